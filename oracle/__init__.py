@@ -1,0 +1,37 @@
+"""Plain FP64 CPU oracle for QDWHpartial-EIG and QDWHpartial-SVD.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use it.  It shares no code with the CUDA library; both sides take
+their inputs from ``paper_2104_14186_gb300.inputs`` and each implements the
+SplitMix64 counter generator for the random vectors the method draws.
+
+The oracle follows the paper step by step (Algorithm 1 for EIG, Algorithm 2
+and the ScaLAPACK listing of Section 5 for SVD), with numpy/LAPACK routines
+(matmul, Householder QR, Cholesky, triangular solve, dense symmetric
+eigensolver, dense SVD) as the individual steps.  Every public function names
+the passage it follows.
+
+Parity status per function (what pins it, see tests/test_oracle_*.py):
+  dwh_weights            pinned: closed-form optimality of the (3,2) function,
+                         iteration counts printed in the paper
+  qdwh_chol_step         pinned: spectral-map identity on known spectra
+  qdwh_qr_step           pinned: spectral-map identity; equals the Cholesky step
+  qdwh_polar             pinned: polar factor from the SVD, H symmetric PSD
+  lanczos_extremes       pinned: bounds against the known spectrum
+  threshold_from_count   pinned: Cauchy interlacing (k eigenvalues beyond t)
+  qdwhp_eig / qdwhp_svd  pinned: constructed spectra, brute-force Jacobi (n<=64),
+                         LAPACK eigh/svd, Theorem 1 containment bound
+  subspace size ell      parity unpinned (several ell are correct; only final
+                         outputs are compared)
+"""
+
+from .rng import splitmix64, uniform_pm1  # noqa: F401
+from .qdwh import dwh_weights, dwh_schedule, qdwh_chol_step, qdwh_qr_step, qdwh_polar, rational_map  # noqa: F401
+from .partial import (  # noqa: F401
+    EigOptions, SvdOptions, EigResult, SvdResult,
+    lanczos_extremes, lanczos_extremes_normal, threshold_from_count_eig, threshold_from_count_svd,
+    qdwhp_eig, qdwhp_svd, qdwhp_eig_negative, qdwhp_svd_threshold, index_from_diag,
+)
+from .jacobi import jacobi_eig  # noqa: F401
+from .metrics import eig_metrics, svd_metrics  # noqa: F401

@@ -1,0 +1,325 @@
+"""QDWHpartial-EIG (Algorithm 1) and QDWHpartial-SVD (Algorithm 2), plain FP64.
+
+The steps below follow the paper in its order and notation.  Where the paper
+is silent (how many Lanczos steps, how to turn a requested count into the
+threshold the method needs, the QR/Cholesky switch), the reading taken is
+stated at the step and listed in the design notes:
+
+  * Lanczos: 30 steps with full reorthogonalisation from a SplitMix64 start
+    vector; an extreme eigenvalue is estimated as Ritz value -/+ residual norm,
+    pushed 1 % outwards (Algorithm 1 step 1 asks for "a few steps").
+  * Count -> threshold: the k-th Ritz value of a (k+p)-dimensional subspace is
+    a one-sided bound on the k-th eigenvalue (Cauchy interlacing), so a
+    threshold there captures at least k wanted eigenpairs.  The subspace comes
+    from q power steps on a positive semidefinite shift of the operator.
+  * Threshold placement guard: the wanted interval is kept at least 5 % of the
+    spectral spread wide, so that the unwanted side is never scaled by more
+    than about 20 (a threshold inside a tight cluster would otherwise make the
+    first Cholesky factor ill conditioned).
+  * QR step while c_k > 100, Cholesky step otherwise (Section 4.2 asks for a
+    QR-based first step when s is small).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+
+from .qdwh import dwh_schedule, qdwh_chol_step, qdwh_qr_step
+from .rng import uniform_pm1
+
+# Stream ids of the two random draws of the method (XORed into the user seed).
+STREAM_LANCZOS = 0x4C414E43   # "LANC"
+STREAM_BLOCK = 0x424C4F43     # "BLOC"
+
+
+@dataclass
+class EigOptions:
+    k: int                      # wanted count (>= 1)
+    side: str = "largest"       # "largest" or "smallest"
+    s: float = 0.2              # shift and ell_0 (Algorithm 1 step 2)
+    iters: int = 3              # QDWH iterations (three for s = 0.2, two for s = 0.875)
+    tol: float = 0.01           # index rule tolerance (Algorithm 1 step 4)
+    lanczos_steps: int = 30
+    block_extra: int = 16       # p in the (k+p)-dimensional threshold subspace
+    power_steps: int = 2        # q
+    guard: float = 0.05         # minimum wanted width / spectral spread
+    max_retries: int = 2
+    seed: int = 1234
+
+
+@dataclass
+class SvdOptions:
+    k: int
+    tol: float = 0.01
+    c_qr: float = 100.0         # QR-based step while c_k > c_qr
+    lanczos_steps: int = 30
+    block_extra: int = 16
+    power_steps: int = 2
+    s_min: float = 1e-15
+    max_retries: int = 2
+    seed: int = 1234
+
+
+@dataclass
+class EigResult:
+    lam: np.ndarray
+    V: np.ndarray
+    ell: int
+    t: float
+    mu: float
+    retries: int
+    info: dict = field(default_factory=dict)
+
+
+@dataclass
+class SvdResult:
+    sigma: np.ndarray
+    U: np.ndarray
+    V: np.ndarray
+    ell: int
+    s: float
+    alpha: float
+    retries: int
+    info: dict = field(default_factory=dict)
+
+
+def lanczos_extremes(matvec, n: int, steps: int, seed: int):
+    """Lanczos with full reorthogonalisation (Algorithm 1 step 1).
+
+    Returns (theta_min, res_min, theta_max, res_max): the extreme Ritz values of
+    the tridiagonal T and their residual norms beta_m |s_{m,i}|.
+    """
+    steps = max(1, min(steps, n))
+    q = uniform_pm1(seed ^ STREAM_LANCZOS, n)
+    Q = np.zeros((n, steps), dtype=np.float64)
+    Q[:, 0] = q / np.linalg.norm(q)
+    alpha = np.zeros(steps)
+    beta = np.zeros(steps)
+    m = steps
+    for j in range(steps):
+        w = matvec(Q[:, j])
+        alpha[j] = Q[:, j] @ w
+        Qj = Q[:, : j + 1]
+        # classical Gram-Schmidt against every Lanczos vector, twice
+        w = w - Qj @ (Qj.T @ w)
+        w = w - Qj @ (Qj.T @ w)
+        beta[j] = np.linalg.norm(w)
+        if j + 1 == steps:
+            break
+        if beta[j] <= 1e-14 * max(abs(alpha[j]), 1e-300):
+            m = j + 1
+            beta[j] = 0.0
+            break
+        Q[:, j + 1] = w / beta[j]
+    T = np.diag(alpha[:m]) + np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
+    theta, S = np.linalg.eigh(T)
+    res = abs(beta[m - 1]) * np.abs(S[m - 1, :])
+    return theta[0], res[0], theta[-1], res[-1]
+
+
+def lanczos_extremes_normal(A: np.ndarray, steps: int, seed: int):
+    """Lanczos on A^T A (norm estimate, Algorithm 2 step 1)."""
+    return lanczos_extremes(lambda x: A.T @ (A @ x), A.shape[1], steps, seed)
+
+
+def _block_start(n: int, b: int, seed: int) -> np.ndarray:
+    """n x b block of SplitMix64 uniforms, column-major order."""
+    return uniform_pm1(seed ^ STREAM_BLOCK, n * b).reshape((n, b), order="F")
+
+
+def _orth(Y: np.ndarray) -> np.ndarray:
+    return np.linalg.qr(Y, mode="reduced")[0]
+
+
+def threshold_from_count_eig(A: np.ndarray, eps_side: float, k: int, lam_hi: float,
+                             p: int, q: int, seed: int) -> float:
+    """Threshold t' on A' = eps_side * A with at least k eigenvalues of A' <= t'.
+
+    Power steps on P = lam_hi I - A' (positive semidefinite, dominant part = the
+    wanted small end of A'), then Rayleigh-Ritz of A' on the final basis.  The
+    k-th smallest Ritz value is >= the k-th smallest eigenvalue (Cauchy
+    interlacing), so it is a valid threshold.
+    """
+    n = A.shape[0]
+    b = min(n, k + p)
+    Om = _block_start(n, b, seed)
+    Y = lam_hi * Om - eps_side * (A @ Om)
+    for _ in range(q):
+        Qy = _orth(Y)
+        Y = lam_hi * Qy - eps_side * (A @ Qy)
+    Qy = _orth(Y)
+    H = Qy.T @ (eps_side * (A @ Qy))
+    H = 0.5 * (H + H.T)
+    theta = np.linalg.eigvalsh(H)
+    return float(theta[k - 1])
+
+
+def threshold_from_count_svd(A: np.ndarray, k: int, p: int, q: int, seed: int) -> float:
+    """sigma_hat_k <= sigma_k: square root of the k-th largest Ritz value of A^T A
+    on a (k+p)-dimensional subspace built by q power steps (Cauchy interlacing)."""
+    n = A.shape[1]
+    b = min(n, k + p)
+    Om = _block_start(n, b, seed)
+    Y = A.T @ (A @ Om)
+    for _ in range(q):
+        Y = A.T @ (A @ _orth(Y))
+    Qy = _orth(Y)
+    C = A @ Qy
+    H = C.T @ C
+    H = 0.5 * (H + H.T)
+    theta = np.linalg.eigvalsh(H)[::-1]
+    return math.sqrt(max(theta[k - 1], 0.0))
+
+
+def index_from_diag(R: np.ndarray, tol: float) -> int:
+    """Algorithm 1 step 4 / Algorithm 2 step 4: ind = min(find(|diag(R)| < tol)),
+    0-based; returns n when no diagonal entry is below tol."""
+    d = np.abs(np.diag(R))
+    hits = np.nonzero(d < tol)[0]
+    return int(hits[0]) if hits.size else d.shape[0]
+
+
+def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float, iters: int, tol: float):
+    """Algorithm 1 steps 1-6 for B = A' - t I with A' = eps_side * A, whose
+    wanted eigenvalues lie on [mu, 0], mu = lam_lo - t <= lambda_min(B)."""
+    n = A.shape[0]
+    mu = lam_lo - t
+    absmu = abs(mu)
+    # Step 1 scaling A := A/|mu| and step 2 shift A~ = (1-s) A - s I, applied to B.
+    X = ((1.0 - s) * eps_side / absmu) * A
+    X[np.diag_indices(n)] -= (1.0 - s) * t / absmu + s
+    # Step 2: QDWH iterations from ell_0 = s, Cholesky-based in all iterations (Section 4.1).
+    sched = dwh_schedule(s, fixed_iters=iters)
+    for a, b, c, _, _ in sched:
+        X = qdwh_chol_step(X, a, b, c)
+    # Step 3: QR of (r(A~) + I) / 2.
+    Bq = 0.5 * (X + np.eye(n))
+    Qf, R = np.linalg.qr(Bq, mode="complete")
+    # Steps 4-5: index rule and trailing columns of Q.
+    ind = index_from_diag(R, tol)
+    Q2 = Qf[:, ind:]
+    # Step 6: Rayleigh-Ritz on the original A, so the Ritz values need no rescaling (step 7).
+    M = Q2.T @ (A @ Q2)
+    M = 0.5 * (M + M.T)
+    theta, W = np.linalg.eigh(M)
+    return theta, W, Q2, mu, {"sched": sched, "ind": ind, "B": Bq, "Q": Qf, "R": R}
+
+
+def qdwhp_eig_negative(A: np.ndarray, mu: float, s: float = 0.2, iters: int = 3, tol: float = 0.01):
+    """Algorithm 1 as printed: the negative eigenpairs of A, given a lower bound
+    mu <= lambda_min(A) < 0.  Returns (lam ascending, V, info)."""
+    theta, W, Q2, _, info = _eig_core(A, 1.0, 0.0, mu, s, iters, tol)
+    sel = np.nonzero(theta < 0.0)[0]
+    return theta[sel], Q2 @ W[:, sel], info
+
+
+def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
+    """QDWHpartial-EIG (Algorithm 1) for the k largest or smallest eigenpairs.
+
+    The wanted side is made the negative side by shifting and scaling by -1
+    (Section 4.1, remark after Algorithm 1): with eps = -1 for "largest" and +1
+    for "smallest", A' = eps A has the wanted eigenvalues at its low end, and
+    B = A' - t' I has them on [mu, 0].
+    """
+    n = A.shape[0]
+    k = opts.k
+    if not (1 <= k <= n):
+        raise ValueError("k out of range")
+    eps_side = -1.0 if opts.side == "largest" else 1.0
+
+    # Step 1: Lanczos bounds of A' (Ritz value -/+ residual, 1 % outwards).
+    th_min, r_min, th_max, r_max = lanczos_extremes(lambda x: A @ x, n, opts.lanczos_steps, opts.seed)
+    if eps_side < 0:
+        lo_raw, hi_raw = -(th_max + r_max), -(th_min - r_min)
+    else:
+        lo_raw, hi_raw = th_min - r_min, th_max + r_max
+    spread = max(hi_raw - lo_raw, 1e-300)
+    lam_lo = lo_raw - 0.01 * spread
+    lam_hi = hi_raw + 0.01 * spread
+
+    # Threshold for the requested count (Cauchy interlacing), with the width guard.
+    t = threshold_from_count_eig(A, eps_side, k, lam_hi, opts.block_extra, opts.power_steps, opts.seed)
+    t += 1e-10 * spread
+    t = max(t, lam_lo + opts.guard * (lam_hi - lam_lo))
+
+    retries = 0
+    while True:
+        theta, W, Q2, mu, info = _eig_core(A, eps_side, t, lam_lo, opts.s, opts.iters, opts.tol)
+        lamp = eps_side * theta               # Ritz values of A'
+        sel = np.nonzero(lamp <= t)[0]
+        if sel.size >= k or retries >= opts.max_retries:
+            break
+        retries += 1
+        t = t + 0.25 * (lam_hi - t)
+    if sel.size < k:
+        raise RuntimeError("fewer than k wanted Ritz values after retries")
+    # Step 7: the k wanted Ritz pairs, V = Q2 W.
+    order = sel[np.argsort(lamp[sel], kind="stable")][:k]
+    lam = theta[order]
+    V = Q2 @ W[:, order]
+    info["lanczos"] = (th_min, r_min, th_max, r_max)
+    return EigResult(lam, V, Q2.shape[1], eps_side * t, eps_side * mu, retries, info)
+
+
+def qdwhp_svd_threshold(A: np.ndarray, s: float, alpha: float, tol: float = 0.01, c_qr: float = 100.0):
+    """Algorithm 2 as printed, for m >= n: the singular triplets with sigma >= s alpha,
+    alpha ~ ||A||_2.  Returns (sigma descending, U, V, info)."""
+    n = A.shape[1]
+    # Step 2: QDWH on A/alpha from ell_0 = s until |ell - 1| < 5 eps; QR-based steps
+    # while c_k > c_qr (Section 4.2: the QR form for the first step when s is small).
+    X = A / alpha
+    sched = dwh_schedule(s)
+    n_qr = 0
+    for a, b, c, _, _ in sched:
+        if c > c_qr:
+            X = qdwh_qr_step(X, a, b, c)
+            n_qr += 1
+        else:
+            X = qdwh_chol_step(X, a, b, c)
+    # Step 3: QR of I - r(A~)^T r(A~).
+    Bq = np.eye(n) - X.T @ X
+    Qf, R = np.linalg.qr(Bq, mode="complete")
+    # Steps 4-5.
+    ind = index_from_diag(R, tol)
+    Q2 = Qf[:, ind:]
+    # Step 6: A Q2 with the unscaled A, and its SVD.
+    C = A @ Q2
+    Ut, St, Vtt = np.linalg.svd(C, full_matrices=False)
+    # Step 7: the triplets above s ||A||_2; step 8: V1 = Q2 V~1.
+    sel = np.nonzero(St >= s * alpha)[0]
+    info = {"sched": sched, "n_qr": n_qr, "ind": ind, "B": Bq, "Q": Qf, "R": R}
+    return St[sel], Ut[:, sel], Q2 @ Vtt[sel, :].T, info
+
+
+def qdwhp_svd(A: np.ndarray, opts: SvdOptions) -> SvdResult:
+    """QDWHpartial-SVD (Algorithm 2 and the Section 5 listing) for the k largest
+    singular triplets.  For m < n it works on A^T and swaps U and V (Section 4.2)."""
+    m, n = A.shape
+    if m < n:
+        r = qdwhp_svd(np.asfortranarray(A.T), opts)
+        return SvdResult(r.sigma, r.V, r.U, r.ell, r.s, r.alpha, r.retries, r.info)
+    k = opts.k
+    if not (1 <= k <= n):
+        raise ValueError("k out of range")
+    # Step 1: alpha ~ ||A||_2 (Lanczos on A^T A, Ritz value + residual).
+    _, _, th_max, r_max = lanczos_extremes_normal(A, opts.lanczos_steps, opts.seed)
+    alpha = math.sqrt(max(th_max + r_max, 0.0))
+    if alpha == 0.0:
+        raise RuntimeError("zero matrix")
+    # Relative threshold s from the requested count.
+    sig_hat = threshold_from_count_svd(A, k, opts.block_extra, opts.power_steps, opts.seed)
+    s = max(sig_hat / alpha * (1.0 - 1e-10), opts.s_min)
+    retries = 0
+    while True:
+        sigma, U, V, info = qdwhp_svd_threshold(A, s, alpha, opts.tol, opts.c_qr)
+        if sigma.shape[0] >= k or retries >= opts.max_retries:
+            break
+        retries += 1
+        s = max(0.5 * s, opts.s_min)
+    if sigma.shape[0] < k:
+        raise RuntimeError("fewer than k singular values above the threshold after retries")
+    return SvdResult(sigma[:k], U[:, :k], V[:, :k], n - info["ind"], s, alpha, retries, info)

@@ -1,0 +1,114 @@
+"""Seeded synthetic test matrices with known spectra.
+
+These generators build the inputs that the solver, its tests and the benchmark
+share.  They hold none of the solver's arithmetic: each matrix is assembled as
+``Q1 diag(d) Q2^T`` from Haar-distributed orthogonal factors, the construction
+the paper's experiments use (Section 6.2: matrices from PDLATMS, mode 0, with
+orthogonal factors taken from the QR factorization of random matrices; Q1 = Q2
+for the symmetric case).  The spectra follow the workload definitions below.
+
+Every draw comes from ``numpy.random.default_rng(seed)`` (PCG64), so a seed
+fixes the matrix on every machine.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def haar_orthogonal(n: int, rng: np.random.Generator, m: int | None = None) -> np.ndarray:
+    """m x n matrix with orthonormal columns, Haar distributed.
+
+    Householder QR of an m x n N(0,1) matrix, with the columns of Q multiplied by
+    sign(diag(R)) so that the distribution is exactly Haar (Mezzadri 2007).
+    """
+    m = n if m is None else m
+    G = rng.standard_normal((m, n))
+    Q, R = np.linalg.qr(G)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return np.asfortranarray(Q * d[None, :])
+
+
+def symmetric_with_spectrum(lam: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    """A = Q diag(lam) Q^T with Haar Q, symmetrised exactly."""
+    n = lam.shape[0]
+    Q = haar_orthogonal(n, rng)
+    A = (Q * lam[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    return np.asfortranarray(A)
+
+
+def general_with_singular_values(m: int, sigma: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    """A = U diag(sigma) V^T, U m x n and V n x n Haar, m >= n = len(sigma)."""
+    n = sigma.shape[0]
+    U = haar_orthogonal(n, rng, m)
+    V = haar_orthogonal(n, rng)
+    return np.asfortranarray((U * sigma[None, :]) @ V.T)
+
+
+@dataclass
+class EigProblem:
+    A: np.ndarray          # n x n symmetric, column-major
+    lam: np.ndarray        # exact eigenvalues (unsorted, as drawn)
+    k: int                 # wanted count
+    side: str              # "largest" or "smallest"
+
+
+@dataclass
+class SvdProblem:
+    A: np.ndarray          # m x n, column-major
+    sigma: np.ndarray      # exact singular values, descending
+    k: int
+
+
+def k_from_fraction(n: int, fraction: float) -> int:
+    """k = ceil(fraction * n), clamped to [1, n] (the library uses the same rule)."""
+    k = int(math.ceil(fraction * n - 1e-9))
+    return max(1, min(n, k))
+
+
+def eig_uniform(n: int, seed: int, fraction: float = 0.10, side: str = "largest") -> EigProblem:
+    """Symmetric n x n, eigenvalues uniform in [-1, 1] (EIG workload, n = 512, 10 % largest)."""
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(-1.0, 1.0, n)
+    A = symmetric_with_spectrum(lam, rng)
+    return EigProblem(A, lam, k_from_fraction(n, fraction), side)
+
+
+def eig_clustered(n: int, seed: int, fraction: float, cluster_frac: float = 0.02) -> EigProblem:
+    """Symmetric n x n: cluster_frac of the eigenvalues uniform in 1 +- 1e-6, the rest
+    uniform in [-1, 0.9] (EIG workload n = 16384 with a tight cluster at the top)."""
+    rng = np.random.default_rng(seed)
+    nc = int(round(cluster_frac * n))
+    lam = np.concatenate([rng.uniform(1.0 - 1e-6, 1.0 + 1e-6, nc), rng.uniform(-1.0, 0.9, n - nc)])
+    A = symmetric_with_spectrum(lam, rng)
+    return EigProblem(A, lam, k_from_fraction(n, fraction), "largest")
+
+
+def svd_logspaced(m: int, n: int, seed: int, fraction: float = 0.05, decades: float = 12.0) -> SvdProblem:
+    """m x n with sigma_i = 10^(-decades * i / (n - 1)), i = 0..n-1 (SVD workload:
+    4096 x 4096, singular values log-spaced from 1 to 1e-12, top 5 %)."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n, dtype=np.float64)
+    sigma = 10.0 ** (-decades * i / max(n - 1, 1))
+    A = general_with_singular_values(m, sigma, rng)
+    return SvdProblem(A, sigma, k_from_fraction(n, fraction))
+
+
+def svd_geometric_half(n: int, seed: int) -> SvdProblem:
+    """The paper's SVD test spectrum (Section 6.2): D[i] = 0.5^(100 i / n)."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n, dtype=np.float64)
+    sigma = 0.5 ** (100.0 * i / n)
+    A = general_with_singular_values(n, sigma, rng)
+    return SvdProblem(A, sigma, 1)
+
+
+def batch_sizes(count: int, seed: int, lo: int = 64, hi: int = 1024) -> np.ndarray:
+    """Sizes of the batched workload: `count` sizes drawn uniformly from [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, size=count)
