@@ -1,0 +1,178 @@
+/*
+ * qdwhp: partial symmetric eigensolver and partial SVD by dynamically weighted
+ * Halley (QDWH) iterations, for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Keyes, Ltaief, Nakatsukasa, Sukkari, "High-Performance Partial Spectrum
+ * Computation for Symmetric eigenvalue problems and the SVD" (arXiv 2104.14186):
+ * Algorithm 1 (QDWHpartial-EIG), Algorithm 2 (QDWHpartial-SVD), the QDWH steps of
+ * Section 2.1 (eqs. practical-polar-qr and practical-polar-chol) and the index rule
+ * of Section 4.1.
+ *
+ * Conventions for every entry point below:
+ *   - Matrices are FP64, column-major, with a leading dimension >= the row count.
+ *   - Matrix and vector arguments are DEVICE pointers unless the name ends in
+ *     `_host`; the caller owns all memory and the library frees nothing it did
+ *     not allocate (it allocates nothing: scratch comes from `workspace`).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; entry points that need a scalar from the device
+ *     (subspace size, thresholds) synchronise that stream before they return.
+ *   - A non-OK status leaves the outputs undefined.  No call falls back to the CPU.
+ *   - Errors: QDWHP_ERR_ARG for bad sizes/pointers (nothing is launched),
+ *     QDWHP_ERR_NOMEM when `ws_bytes` is below the documented size,
+ *     QDWHP_ERR_CUDA for a CUDA runtime error (see qdwhp_last_error_message()).
+ */
+#ifndef QDWHP_H
+#define QDWHP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define QDWHP_API __attribute__((visibility("default")))
+#else
+#define QDWHP_API
+#endif
+
+typedef enum {
+  QDWHP_OK = 0,
+  QDWHP_ERR_ARG = -1,            /* invalid argument */
+  QDWHP_ERR_NOMEM = -2,          /* workspace too small */
+  QDWHP_ERR_NOT_CONVERGED = -3,  /* Jacobi small solver did not converge in its sweep limit */
+  QDWHP_ERR_BREAKDOWN = -4,      /* non-positive pivot in a Cholesky factorisation */
+  QDWHP_ERR_NONFINITE = -5,      /* input or an intermediate holds NaN/Inf */
+  QDWHP_ERR_TIMEOUT = -6,        /* a bounded wait expired */
+  QDWHP_ERR_CUDA = -7,           /* CUDA runtime error */
+  QDWHP_ERR_QUEUE_FULL = -8,     /* request queue has no free slot or budget */
+  QDWHP_ERR_COUNT = -9,          /* fewer than k wanted pairs captured after the retries */
+  QDWHP_PENDING = 1              /* request still running (qdwhp_poll only) */
+} qdwhp_status;
+
+typedef enum { QDWHP_LARGEST = 0, QDWHP_SMALLEST = 1 } qdwhp_side;
+typedef enum { QDWHP_FP64 = 0, QDWHP_MIXED = 1 } qdwhp_precision;
+
+/* Options.  Fill with qdwhp_default_opts() and change what you need. */
+typedef struct {
+  int64_t count;          /* wanted count k; 0 = use `fraction` */
+  double fraction;        /* k = ceil(fraction * n) (clamped to [1, n]) when count == 0 */
+  int32_t side;           /* qdwhp_side (EIG only; SVD always returns the largest) */
+  int32_t precision;      /* qdwhp_precision (QDWHP_FP64; QDWHP_MIXED is rejected with ERR_ARG) */
+  double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
+  int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */
+  int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
+  double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.01) */
+  double c_qr;            /* SVD: QR-based step while c_k > c_qr (default 100) */
+  int32_t block_extra;    /* p: the count-to-threshold subspace has k + p vectors (16) */
+  int32_t power_steps;    /* q: power steps for that subspace (default 2) */
+  double guard;           /* EIG: minimum wanted width / spectral spread (default 0.05) */
+  int32_t max_retries;    /* re-runs with a wider threshold if < k pairs are captured (2) */
+  int32_t jacobi_max_sweeps; /* sweep limit of the reduced-problem Jacobi solver (30) */
+  uint64_t seed;          /* seed of the SplitMix64 start vectors */
+} qdwhp_opts;
+
+/* Per-solve report (host struct, filled when the pointer is non-NULL). */
+typedef struct {
+  int32_t it_qr;          /* QR-based QDWH steps */
+  int32_t it_chol;        /* Cholesky-based QDWH steps */
+  int32_t retries;
+  int32_t jacobi_sweeps;
+  int64_t ell;            /* captured subspace size (n - ind) */
+  int64_t k;              /* returned pairs */
+  double t;               /* EIG: threshold in the units of A */
+  double mu;              /* EIG: lower bound of the shifted matrix (units of A) */
+  double s;               /* SVD: relative threshold s */
+  double alpha;           /* SVD: estimate of ||A||_2 */
+  double ell_k[12];       /* ell_k after each QDWH step */
+  double conv[12];        /* ||X_k - X_{k-1}||_F after each QDWH step */
+  float ms_total;         /* device time of the solve (CUDA events) */
+} qdwhp_info;
+
+QDWHP_API void qdwhp_default_opts(qdwhp_opts* opts);
+QDWHP_API const char* qdwhp_status_string(qdwhp_status s);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+QDWHP_API const char* qdwhp_last_error_message(void);
+/* k = ceil(fraction * n), clamped to [1, n]; 0 if n < 1 or fraction <= 0. */
+QDWHP_API int64_t qdwhp_k_from_fraction(int64_t n, double fraction);
+
+/*
+ * QDWHpartial-EIG (Algorithm 1; arbitrary side by shift and sign, remark after
+ * Algorithm 1): the k largest (side = LARGEST) or smallest eigenpairs of the
+ * symmetric n x n matrix A (both triangles must be stored; A is never modified).
+ *   lambda: k doubles, ordered largest-first (LARGEST) or smallest-first (SMALLEST).
+ *   V:      n x k, leading dimension ldv >= n, orthonormal eigenvectors (signs unspecified).
+ *   workspace/ws_bytes: device scratch of at least qdwhp_eig_workspace_bytes(n, opts).
+ * k comes from opts->count or opts->fraction.  Returns QDWHP_ERR_COUNT if fewer than
+ * k pairs are captured after opts->max_retries widenings of the threshold.
+ */
+QDWHP_API size_t qdwhp_eig_workspace_bytes(int64_t n, const qdwhp_opts* opts);
+QDWHP_API qdwhp_status qdwhp_eig(const double* A, int64_t n, int64_t lda, const qdwhp_opts* opts,
+                                 double* lambda, double* V, int64_t ldv,
+                                 void* workspace, size_t ws_bytes, qdwhp_info* info, void* stream);
+
+/*
+ * QDWHpartial-SVD (Algorithm 2 and the Section 5 listing): the k largest singular
+ * triplets of the m x n matrix A (m < n is solved on A^T, Section 4.2).
+ *   k: wanted count (0 = take it from opts->count / opts->fraction of min(m, n)).
+ *   sigma: k doubles, descending.  U: m x k (ldu >= m).  V: n x k (ldv >= n).
+ *   workspace/ws_bytes: at least qdwhp_svd_workspace_bytes(m, n, opts).
+ */
+QDWHP_API size_t qdwhp_svd_workspace_bytes(int64_t m, int64_t n, const qdwhp_opts* opts);
+QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t lda, int64_t k,
+                                 const qdwhp_opts* opts, double* sigma, double* U, int64_t ldu,
+                                 double* V, int64_t ldv, void* workspace, size_t ws_bytes,
+                                 qdwhp_info* info, void* stream);
+
+/* ---- Building blocks (the dense kernels the solvers are made of) ---- */
+
+/*
+ * C = alpha * op(A) * op(B) + beta * C, FP64 (op = transpose when trans != 0);
+ * C is m x n, the inner dimension k.  beta == 0 never reads C.  The products in
+ * the Cholesky-based QDWH step (eq. practical-polar-chol), the Householder
+ * trailing updates and the Rayleigh-Ritz projections (Algorithms 1-2) are these.
+ */
+QDWHP_API qdwhp_status qdwhp_gemm_f64(int transa, int transb, int64_t m, int64_t n, int64_t k,
+                                      double alpha, const double* A, int64_t lda,
+                                      const double* B, int64_t ldb, double beta,
+                                      double* C, int64_t ldc, void* stream);
+
+/*
+ * Z = L L^T, lower Cholesky factor of the symmetric positive definite n x n Z in
+ * place (lower triangle read and written; the strict upper triangle is left as is).
+ * The factorisation W = chol(Z) of eq. practical-polar-chol with W = L^T.
+ * *info_host = 0 on success, i > 0 if the leading minor of order i is not
+ * positive definite (status QDWHP_ERR_BREAKDOWN).  Synchronises `stream`.
+ */
+QDWHP_API size_t qdwhp_potrf_workspace_bytes(int64_t n);
+QDWHP_API qdwhp_status qdwhp_potrf_f64(int64_t n, double* Z, int64_t ldz, void* workspace, size_t ws_bytes,
+                                       int* info_host, void* stream);
+
+/*
+ * Householder QR (unpivoted, as in Algorithm 1 step 3) of the m x n matrix A,
+ * m >= n: A = Q R with Q m x n orthonormal and R n x n upper triangular, written
+ * to Q (ldq >= m) and R (ldr >= n).  A is overwritten.  diag(R) follows the
+ * Householder convention R_ii = -sign(a_ii) * ||a_i||.
+ */
+QDWHP_API size_t qdwhp_qr_workspace_bytes(int64_t m, int64_t n);
+QDWHP_API qdwhp_status qdwhp_qr_f64(int64_t m, int64_t n, double* A, int64_t lda, double* Q, int64_t ldq,
+                                    double* R, int64_t ldr, void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * QDWH steps in place on the m x n iterate X (m >= n): for step i with weights
+ * (a, b, c) = abc_host[3i .. 3i+2], the QR-based update of eq. practical-polar-qr
+ * if use_qr_host[i] != 0, else the Cholesky-based update of eq. practical-polar-chol.
+ * conv_host (may be NULL) receives ||X_i - X_{i-1}||_F per step.
+ */
+QDWHP_API size_t qdwhp_qdwh_workspace_bytes(int64_t m, int64_t n);
+QDWHP_API qdwhp_status qdwhp_qdwh_steps_f64(int64_t m, int64_t n, double* X, int64_t ldx, int32_t nsteps,
+                                            const double* abc_host, const int32_t* use_qr_host,
+                                            double* conv_host, void* workspace, size_t ws_bytes,
+                                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDWHP_H */

@@ -1,0 +1,154 @@
+// Memory-bound helpers: axpby (the QDWH update's combination step), copies,
+// identity shifts, symmetrisation and reductions.  All are grid-stride loops over
+// column-major matrices with grids sized in multiples of the SM count.
+#include "internal.h"
+
+namespace qdwhp {
+
+namespace {
+
+inline int grid_for(size_t total) {
+  return (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 8 * (size_t)kNumSMs));
+}
+
+__global__ void axpby_kernel(int M, int N, double alpha, const double* X, int64_t ldx, double beta, double* Y,
+                             int64_t ldy, double diag_add) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    double v = alpha * X[i + (int64_t)j * ldx];
+    double* yp = Y + i + (int64_t)j * ldy;
+    if (beta != 0.0) v += beta * (*yp);
+    if (i == j) v += diag_add;
+    *yp = v;
+  }
+}
+
+__global__ void axpby_diff_kernel(int M, int N, double a, double* Y, int64_t ldy, double b, const double* Z,
+                                  int64_t ldz, double* diff_part) {
+  __shared__ double red[32];
+  const size_t total = (size_t)M * N;
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    double* yp = Y + i + (int64_t)j * ldy;
+    const double old = *yp;
+    const double nw = a * old + b * Z[i + (int64_t)j * ldz];
+    *yp = nw;
+    const double d = nw - old;
+    acc += d * d;
+  }
+  acc = block_sum(acc, red);
+  if (diff_part != nullptr && threadIdx.x == 0) diff_part[blockIdx.x] = acc;
+}
+
+__global__ void set_kernel(int M, int N, double off, double diag, double* Y, int64_t ldy) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    Y[i + (int64_t)j * ldy] = (i == j) ? diag : off;
+  }
+}
+
+__global__ void copy_upper_kernel(int N, const double* A, int64_t lda, double* R, int64_t ldr) {
+  const size_t total = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    R[i + (int64_t)j * ldr] = (i <= j) ? A[i + (int64_t)j * lda] : 0.0;
+  }
+}
+
+__global__ void symmetrize_kernel(int N, double* Y, int64_t ldy) {
+  const size_t total = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    if (i < j) Y[i + (int64_t)j * ldy] = Y[j + (int64_t)i * ldy];
+  }
+}
+
+__global__ void reduce_parts_kernel(const double* parts, int nparts, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += parts[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+__global__ void nonfinite_kernel(int M, int N, const double* X, int64_t ldx, unsigned* count) {
+  const size_t total = (size_t)M * N;
+  unsigned c = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    if (!isfinite(X[i + (int64_t)j * ldx])) ++c;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+}  // namespace
+
+qdwhp_status axpby(cudaStream_t st, int64_t m, int64_t n, double alpha, const double* X, int64_t ldx, double beta,
+                   double* Y, int64_t ldy, double diag_add) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  axpby_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, alpha, X, ldx, beta, Y, ldy, diag_add);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status axpby_diff(cudaStream_t st, int64_t m, int64_t n, double a, double* Y, int64_t ldy, double b,
+                        const double* Z, int64_t ldz, double* diff_part) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  // Exactly kDiffParts blocks so that every partial slot is written.
+  axpby_diff_kernel<<<kDiffParts, 256, 0, st>>>((int)m, (int)n, a, Y, ldy, b, Z, ldz, diff_part);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status copy_matrix(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx, double* Y,
+                         int64_t ldy) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  if (ldx == m && ldy == m) {
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(Y, X, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, st));
+    return QDWHP_OK;
+  }
+  QDWHP_CUDA_TRY(cudaMemcpy2DAsync(Y, sizeof(double) * ldy, X, sizeof(double) * ldx, sizeof(double) * m, n,
+                                   cudaMemcpyDeviceToDevice, st));
+  return QDWHP_OK;
+}
+
+qdwhp_status set_matrix(cudaStream_t st, int64_t m, int64_t n, double off, double diag, double* Y, int64_t ldy) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  set_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, off, diag, Y, ldy);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr) {
+  if (n <= 0) return QDWHP_OK;
+  copy_upper_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>((int)n, A, lda, R, ldr);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status symmetrize_from_lower(cudaStream_t st, int64_t n, double* Y, int64_t ldy) {
+  if (n <= 1) return QDWHP_OK;
+  symmetrize_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>((int)n, Y, ldy);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status reduce_parts(cudaStream_t st, const double* parts, int nparts, double* out) {
+  reduce_parts_kernel<<<1, 1024, 0, st>>>(parts, nparts, out);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status count_nonfinite(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx,
+                             unsigned* count_dev) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  nonfinite_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, X, ldx, count_dev);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+}  // namespace qdwhp

@@ -1,0 +1,218 @@
+// FP64 GEMM on the GB300 FP64 tensor path (mma.sync m8n8k4 .f64, "DMMA").
+//
+// tcgen05 has no f64 kind, so FP64 contractions run on DMMA.  Measured on this
+// part, DMMA peaks at ~1.05 TFLOP/s (DFMA ~1.01): one SM does only a few FP64
+// flops per clock, so the kernel needs no deep pipelining to stay compute bound
+// (a 64x64x16 tile step is ~36k clocks of DMMA work against ~1k clocks of load
+// latency).  What matters is covering all 152 SMs: small outputs use 32x32 tiles
+// and split-K.  Split-K writes per-slice partial sums that a second kernel adds
+// in a fixed order, so results do not depend on scheduling.
+#include "internal.h"
+
+namespace qdwhp {
+
+namespace {
+
+constexpr int kBK = 16;
+constexpr int kThreads = 128;   // 2 x 2 warps
+
+__device__ __forceinline__ void dmma884(double (&c)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(c[0]), "+d"(c[1])
+               : "d"(a), "d"(b));
+}
+
+template <int BM, int BN, bool TA, bool TB>
+__global__ void __launch_bounds__(kThreads) dgemm_kernel(int M, int N, int K, int kchunk, double alpha,
+                                                         const double* A, int64_t lda, const double* B,
+                                                         int64_t ldb, double beta, double* C, int64_t ldc,
+                                                         int uplo, double diag_add, double* partial) {
+  constexpr int WM = BM / 2, WN = BN / 2;
+  constexpr int MT = WM / 8, NT = WN / 8;
+  constexpr int A_LD = BM * kBK / kThreads, B_LD = BN * kBK / kThreads;
+  // Row strides of 8 mod 16 doubles keep a warp's fragment reads at two wavefronts.
+  __shared__ double As[kBK][BM + 8];
+  __shared__ double Bs[kBK][BN + 8];
+
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  if (uplo == LOWER && m0 + BM <= n0) return;   // tile strictly above the diagonal
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp & 1, wn = warp >> 1;
+  const int g = lane >> 2, t4 = lane & 3;
+
+  double acc[MT][NT][2];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+  double ra[A_LD], rb[B_LD];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < A_LD; ++r) {
+      const int e = tid + kThreads * r;
+      const int i = TA ? e / kBK : e % BM;
+      const int kk = TA ? e % kBK : e / BM;
+      const int gi = m0 + i, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < M && gk < kend) v = TA ? A[gk + (int64_t)gi * lda] : A[gi + (int64_t)gk * lda];
+      ra[r] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < B_LD; ++r) {
+      const int e = tid + kThreads * r;
+      const int j = TB ? e % BN : e / kBK;
+      const int kk = TB ? e / BN : e % kBK;
+      const int gj = n0 + j, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < N && gk < kend) v = TB ? B[gj + (int64_t)gk * ldb] : B[gk + (int64_t)gj * ldb];
+      rb[r] = v;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int r = 0; r < A_LD; ++r) {
+      const int e = tid + kThreads * r;
+      const int i = TA ? e / kBK : e % BM;
+      const int kk = TA ? e % kBK : e / BM;
+      As[kk][i] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < B_LD; ++r) {
+      const int e = tid + kThreads * r;
+      const int j = TB ? e % BN : e / kBK;
+      const int kk = TB ? e / BN : e % kBK;
+      Bs[kk][j] = rb[r];
+    }
+  };
+
+  if (kbeg < kend) load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+    __syncthreads();
+    store();
+    __syncthreads();
+    if (k0 + kBK < kend) load(k0 + kBK);
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 4) {
+      double af[MT], bf[NT];
+#pragma unroll
+      for (int i = 0; i < MT; ++i) af[i] = As[kk + t4][wm * WM + i * 8 + g];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) bf[j] = Bs[kk + t4][wn * WN + j * 8 + g];
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) dmma884(acc[i][j], af[i], bf[j]);
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int row = m0 + wm * WM + i * 8 + g;
+        const int col = n0 + wn * WN + j * 8 + 2 * t4 + e;
+        if (row >= M || col >= N) continue;
+        if (uplo == LOWER && row < col) continue;
+        if (partial != nullptr) {
+          partial[(size_t)blockIdx.z * M * N + row + (size_t)col * M] = acc[i][j][e];
+        } else {
+          double v = alpha * acc[i][j][e];
+          double* cp = C + row + (int64_t)col * ldc;
+          if (beta != 0.0) v += beta * (*cp);
+          if (row == col) v += diag_add;
+          *cp = v;
+        }
+      }
+    }
+  }
+}
+
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const double* partial, double alpha,
+                                     double beta, double* C, int64_t ldc, int uplo, double diag_add) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e % M), col = (int)(e / M);
+    if (uplo == LOWER && row < col) continue;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += partial[(size_t)z * total + e];
+    double v = alpha * s;
+    double* cp = C + row + (int64_t)col * ldc;
+    if (beta != 0.0) v += beta * (*cp);
+    if (row == col) v += diag_add;
+    *cp = v;
+  }
+}
+
+template <int BM, int BN>
+void launch(cudaStream_t st, bool ta, bool tb, dim3 grid, int M, int N, int K, int kchunk, double alpha,
+            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+            int uplo, double diag_add, double* partial) {
+  if (!ta && !tb)
+    dgemm_kernel<BM, BN, false, false><<<grid, kThreads, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C,
+                                                                ldc, uplo, diag_add, partial);
+  else if (!ta && tb)
+    dgemm_kernel<BM, BN, false, true><<<grid, kThreads, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C,
+                                                               ldc, uplo, diag_add, partial);
+  else if (ta && !tb)
+    dgemm_kernel<BM, BN, true, false><<<grid, kThreads, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C,
+                                                               ldc, uplo, diag_add, partial);
+  else
+    dgemm_kernel<BM, BN, true, true><<<grid, kThreads, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C,
+                                                              ldc, uplo, diag_add, partial);
+}
+
+constexpr int kMaxSplit = 16;
+constexpr size_t kSplitMaxElems = size_t(1) << 22;   // split-K only for outputs up to 4M entries
+
+}  // namespace
+
+size_t gemm_splitk_ws_elems(int64_t m, int64_t n) {
+  size_t mn = (size_t)m * (size_t)n;
+  if (mn > kSplitMaxElems) return 0;
+  return mn * kMaxSplit;
+}
+
+qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                  int64_t ldc, Uplo uplo, double diag_add, double* splitk_ws, size_t splitk_ws_elems) {
+  if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
+  if (m == 0 || n == 0) return QDWHP_OK;
+  if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return QDWHP_ERR_ARG;
+  const int M = (int)m, N = (int)n, K = (int)k;
+  const int64_t tiles64 = (int64_t)ceil_div(M, 64) * ceil_div(N, 64);
+  const bool big = tiles64 >= 2 * kNumSMs;
+  const int BM = big ? 64 : 32, BN = big ? 64 : 32;
+  const int64_t tiles = (int64_t)ceil_div(M, BM) * ceil_div(N, BN) / (uplo == LOWER ? 2 : 1);
+  int split = 1;
+  const size_t mn = (size_t)M * N;
+  if (splitk_ws != nullptr && tiles < kNumSMs && K >= 512 && mn <= kSplitMaxElems) {
+    split = (int)std::min<int64_t>((2 * kNumSMs + tiles - 1) / std::max<int64_t>(tiles, 1), K / 256);
+    split = std::min(split, kMaxSplit);
+    while (split > 1 && (size_t)split * mn > splitk_ws_elems) --split;
+    if (split < 1) split = 1;
+  }
+  int kchunk = (K + split - 1) / split;
+  kchunk = ((kchunk + kBK - 1) / kBK) * kBK;
+  if (split > 1) split = (K + kchunk - 1) / kchunk;
+  dim3 grid(ceil_div(M, BM), ceil_div(N, BN), split);
+  double* partial = split > 1 ? splitk_ws : nullptr;
+  if (big)
+    launch<64, 64>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
+  else
+    launch<32, 32>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
+  QDWHP_LAUNCH_CHECK();
+  if (split > 1) {
+    const int blocks = (int)std::min<size_t>((mn + 255) / 256, 4 * kNumSMs);
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, split, partial, alpha, beta, C, ldc, uplo, diag_add);
+    QDWHP_LAUNCH_CHECK();
+  }
+  return QDWHP_OK;
+}
+
+}  // namespace qdwhp

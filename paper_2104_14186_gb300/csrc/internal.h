@@ -1,0 +1,76 @@
+// Internal host-side interfaces shared by the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace qdwhp {
+
+enum Uplo { FULL = 0, LOWER = 1 };
+
+// ---- gemm.cu ----
+// C = alpha op(A) op(B) + beta C (+ diag_add on the diagonal), FP64 DMMA tiles.
+// uplo == LOWER computes and writes only the lower triangle of C (SYRK use).
+// `splitk_ws` (may be null) is scratch for split-K partial sums: at least
+// gemm_splitk_ws_elems(m, n) doubles.  Without it no split-K is used.
+qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                  int64_t ldc, Uplo uplo = FULL, double diag_add = 0.0, double* splitk_ws = nullptr,
+                  size_t splitk_ws_elems = 0);
+size_t gemm_splitk_ws_elems(int64_t m, int64_t n);
+
+// ---- elementwise.cu ----
+// Y = alpha X + beta Y (+ diag_add on the diagonal); beta == 0 never reads Y.
+qdwhp_status axpby(cudaStream_t st, int64_t m, int64_t n, double alpha, const double* X, int64_t ldx,
+                   double beta, double* Y, int64_t ldy, double diag_add = 0.0);
+// Y = a Y + b Z, and (optional) partial sums of ||Y_new - Y_old||_F^2 into `diff_part`
+// (kDiffParts doubles, summed by the caller's reduction).
+constexpr int kDiffParts = 1024;
+qdwhp_status axpby_diff(cudaStream_t st, int64_t m, int64_t n, double a, double* Y, int64_t ldy, double b,
+                        const double* Z, int64_t ldz, double* diff_part);
+qdwhp_status copy_matrix(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx, double* Y,
+                         int64_t ldy);
+qdwhp_status set_matrix(cudaStream_t st, int64_t m, int64_t n, double offdiag, double diag, double* Y,
+                        int64_t ldy);
+// R (n x n) = upper triangle of A, zeros below.
+qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr);
+// Fills the lower triangle's mirror: Y(i, j) = Y(j, i) for i < j (n x n).
+qdwhp_status symmetrize_from_lower(cudaStream_t st, int64_t n, double* Y, int64_t ldy);
+// Sum of kDiffParts partials -> out (device scalar); also checks finiteness of the sum.
+qdwhp_status reduce_parts(cudaStream_t st, const double* parts, int nparts, double* out);
+// Count of non-finite entries of X (m x n) added into *count_dev (unsigned).
+qdwhp_status count_nonfinite(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx,
+                             unsigned* count_dev);
+
+// ---- chol.cu ----
+constexpr int kCholNB = 64;
+size_t potrf_linv_elems(int64_t n);
+// Lower Cholesky in place; Linv receives the inverses of the kCholNB diagonal blocks;
+// *fail_dev (int, device) receives the first failing 1-based column; the caller zeroes
+// it beforehand and it is never cleared here, so it accumulates over calls.  Needs a
+// scratch of potrf_scratch_elems(n) doubles.
+size_t potrf_scratch_elems(int64_t n);
+qdwhp_status potrf(cudaStream_t st, int64_t n, double* Z, int64_t ldz, double* Linv, double* scratch,
+                   int* fail_dev);
+// X (m x n) := X L^{-T} (trans) or X L^{-1} (!trans), L from potrf with its Linv blocks.
+size_t trsm_scratch_elems(int64_t m, int64_t n);
+qdwhp_status trsm_right_lower(cudaStream_t st, bool trans, int64_t m, int64_t n, double* X, int64_t ldx,
+                              const double* L, int64_t ldl, const double* Linv, double* scratch);
+
+// ---- qr.cu ----
+constexpr int kQRNB = 32;
+struct QRFactors {
+  double* Vall = nullptr;   // m x n explicit reflectors (unit diagonal, zeros above), ld = m
+  double* T = nullptr;      // nblocks x kQRNB x kQRNB upper-triangular block factors
+  double* tau = nullptr;    // n
+  double* diagR = nullptr;  // n: R_ii
+  int64_t m = 0, n = 0;
+};
+size_t qr_scratch_elems(int64_t m, int64_t n);
+// Householder QR of A (m x n, m >= n) in place: R in the upper triangle of A.
+qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f,
+                   double* scratch);
+// C (m x ncols) := Q [0; I; 0] restricted to columns col0 .. col0+ncols-1 of Q (explicit Q columns).
+qdwhp_status orgqr_columns(cudaStream_t st, const QRFactors& f, int64_t col0, int64_t ncols, double* C,
+                           int64_t ldc, double* scratch);
+
+}  // namespace qdwhp

@@ -1,0 +1,235 @@
+// Reduced problems of the Rayleigh-Ritz step (Algorithm 1 step 6, Algorithm 2 step 6)
+// by one-sided (Hestenes) Jacobi, plus selection, ordering and gathers.
+//
+// A sweep visits every column pair once in the round-robin ("circle method")
+// order: nc - 1 rounds of nc / 2 disjoint pairs (a dummy column pads odd nc).  The
+// pairs of a round are independent, so a round is one launch with one CTA per pair:
+// the CTA forms ||g_p||^2, ||g_q||^2 and g_p^T g_q, and applies the plane rotation
+// that makes the two columns orthogonal to G and to the accumulated Vj.
+//   - SVD: G = A Q2 (m x ell): sigma_i = ||w_i||, U = W Sigma^{-1}, V~ = Vj.
+//   - EIG: G = M + sigma I with M = Q2^T A Q2 and sigma >= ||M||_2, so G is positive
+//     semidefinite and its right singular vectors are eigenvectors of M; the
+//     eigenvalues are then taken as Rayleigh quotients v_i^T M v_i.
+#include "internal.h"
+#include "krylov.h"
+
+namespace qdwhp {
+
+namespace {
+
+__device__ __forceinline__ void pair_of(int r, int h, int N, int& p, int& q) {
+  if (h == 0) {
+    p = N - 1;
+    q = r;
+  } else {
+    p = (r + h) % (N - 1);
+    q = (r - h + N - 1) % (N - 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) jacobi_round_kernel(int mg, int nc, int N, int round, double* G, int64_t ldg,
+                                                           double* Vj, int64_t ldv, double tol, JacobiState* jst) {
+  __shared__ double red[3][32];
+  __shared__ double rot[2];
+  __shared__ int skip;
+  int p, q;
+  pair_of(round, blockIdx.x, N, p, q);
+  if (p >= nc || q >= nc) return;   // dummy column
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+  double* gp = G + (int64_t)p * ldg;
+  double* gq = G + (int64_t)q * ldg;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < mg; i += blockDim.x) {
+    const double x = gp[i], y = gq[i];
+    a += x * x;
+    b += y * y;
+    c += x * y;
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    double sa = 0.0, sb = 0.0, sc = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+      sc += red[2][w];
+    }
+    skip = 1;
+    if (!isfinite(sa) || !isfinite(sb) || !isfinite(sc)) {
+      atomicExch(&jst->nonfinite, 1);
+    } else if (sa > 0.0 && sb > 0.0 && sc != 0.0) {
+      const double off = fabs(sc) / sqrt(sa * sb);
+      atomicMax(&jst->max_off_bits, (unsigned long long)__double_as_longlong(off));
+      if (off > tol) {
+        const double zeta = (sb - sa) / (2.0 * sc);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t);
+        rot[0] = cs;
+        rot[1] = cs * t;
+        skip = 0;
+      }
+    }
+  }
+  __syncthreads();
+  if (skip) return;
+  const double cs = rot[0], sn = rot[1];
+  for (int i = threadIdx.x; i < mg; i += blockDim.x) {
+    const double x = gp[i], y = gq[i];
+    gp[i] = cs * x - sn * y;
+    gq[i] = sn * x + cs * y;
+  }
+  double* vp = Vj + (int64_t)p * ldv;
+  double* vq = Vj + (int64_t)q * ldv;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const double x = vp[i], y = vq[i];
+    vp[i] = cs * x - sn * y;
+    vq[i] = sn * x + cs * y;
+  }
+}
+
+__global__ void column_norms_kernel(int mg, const double* G, int64_t ldg, double* norms) {
+  __shared__ double red[32];
+  const double* g = G + (int64_t)blockIdx.x * ldg;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < mg; i += blockDim.x) acc += g[i] * g[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) norms[blockIdx.x] = sqrt(acc);
+}
+
+__global__ void column_dots_kernel(int mg, const double* V, int64_t ldv, const double* MV, int64_t ldmv, double* d) {
+  __shared__ double red[32];
+  const double* v = V + (int64_t)blockIdx.x * ldv;
+  const double* w = MV + (int64_t)blockIdx.x * ldmv;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < mg; i += blockDim.x) acc += v[i] * w[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) d[blockIdx.x] = acc;
+}
+
+// Rank sort of the selected keys (one CTA; O(n^2) comparisons, n <= a few thousand).
+__global__ void select_sort_kernel(int n, const double* vals, double sign, double thresh, int* order, int* count) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ki = sign * vals[i];
+    if (!(ki <= thresh)) continue;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double kj = sign * vals[j];
+      if (!(kj <= thresh)) continue;
+      if (kj < ki || (kj == ki && j < i)) ++rank;
+    }
+    order[rank] = i;
+    atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *count = cnt;
+}
+
+__global__ void gather_columns_kernel(int rows, int k, const double* in, int64_t ldin, const int* order,
+                                      const double* norms, double* out, int64_t ldout) {
+  const size_t total = (size_t)rows * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % rows), r = (int)(e / rows);
+    const int src = order[r];
+    double v = in[i + (int64_t)src * ldin];
+    if (norms != nullptr) v /= norms[src];
+    out[i + (int64_t)r * ldout] = v;
+  }
+}
+
+__global__ void gather_values_kernel(int k, const double* vals, const int* order, double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < k) out[r] = vals[order[r]];
+}
+
+}  // namespace
+
+qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G, int64_t ldg, double* Vj, int64_t ldv,
+                             int max_sweeps, double tol, JacobiState* jst_dev, JacobiState* jst_host, int* sweeps_out,
+                             int* conv_out) {
+  *sweeps_out = 0;
+  *conv_out = 0;
+  QDWHP_TRY(set_matrix(st, nc, nc, 0.0, 1.0, Vj, ldv));
+  if (nc <= 1) {
+    *conv_out = 1;
+    return QDWHP_OK;
+  }
+  const int N = (int)(nc + (nc & 1));
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    QDWHP_CUDA_TRY(cudaMemsetAsync(jst_dev, 0, sizeof(JacobiState), st));
+    for (int r = 0; r < N - 1; ++r) {
+      jacobi_round_kernel<<<N / 2, 256, 0, st>>>((int)mg, (int)nc, N, r, G, ldg, Vj, ldv, tol, jst_dev);
+    }
+    QDWHP_LAUNCH_CHECK();
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
+    QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+    *sweeps_out = sweep + 1;
+    if (jst_host->nonfinite) return QDWHP_ERR_NONFINITE;
+    double max_off;
+    static_assert(sizeof(double) == sizeof(unsigned long long), "size");
+    memcpy(&max_off, &jst_host->max_off_bits, sizeof(double));
+    if (max_off <= tol) {
+      *conv_out = 1;
+      break;
+    }
+  }
+  return QDWHP_OK;
+}
+
+qdwhp_status column_norms(cudaStream_t st, int64_t mg, int64_t nc, const double* G, int64_t ldg, double* norms) {
+  if (nc <= 0) return QDWHP_OK;
+  column_norms_kernel<<<(int)nc, 256, 0, st>>>((int)mg, G, ldg, norms);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status column_dots(cudaStream_t st, int64_t mg, int64_t nc, const double* V, int64_t ldv, const double* MV,
+                         int64_t ldmv, double* d) {
+  if (nc <= 0) return QDWHP_OK;
+  column_dots_kernel<<<(int)nc, 256, 0, st>>>((int)mg, V, ldv, MV, ldmv, d);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status select_sort(cudaStream_t st, int64_t nvals, const double* vals, double sign, double thresh_key, int* order,
+                         int* count_dev) {
+  // Unselected tail entries stay 0, a valid index, so a later gather never reads out of range.
+  QDWHP_CUDA_TRY(cudaMemsetAsync(order, 0, sizeof(int) * std::max<int64_t>(nvals, 1), st));
+  select_sort_kernel<<<1, 1024, 0, st>>>((int)nvals, vals, sign, thresh_key, order, count_dev);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status gather_columns(cudaStream_t st, int64_t rows, int64_t k, const double* in, int64_t ldin, const int* order,
+                            const double* inv_scale_by, double* out, int64_t ldout) {
+  const size_t total = (size_t)rows * k;
+  if (total == 0) return QDWHP_OK;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 8 * kNumSMs));
+  gather_columns_kernel<<<blocks, 256, 0, st>>>((int)rows, (int)k, in, ldin, order, inv_scale_by, out, ldout);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status gather_values(cudaStream_t st, int64_t k, const double* vals, const int* order, double* out) {
+  if (k <= 0) return QDWHP_OK;
+  gather_values_kernel<<<ceil_div(k, 256), 256, 0, st>>>((int)k, vals, order, out);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+}  // namespace qdwhp

@@ -1,0 +1,235 @@
+// QDWH iteration (Section 2.1): dynamical weights on the device and the two
+// practical step forms.
+//   Cholesky-based (eq. practical-polar-chol):
+//     Z = I + c X^T X (lower SYRK with the identity folded into the epilogue),
+//     L = chol(Z) (W = L^T), Y = (X L^{-T}) L^{-1} = X W^{-1} W^{-T},
+//     X <- (b/c) X + (a - b/c) Y.
+//   QR-based (eq. practical-polar-qr):
+//     [sqrt(c) X; I] = [Q1; Q2] R,  X <- (b/c) X + (1/sqrt(c)) (a - b/c) Q1 Q2^T.
+// Each step also reports ||X_k - X_{k-1}||_F (the Section 5 listing's diagnostic).
+#include "internal.h"
+#include "qdwh.h"
+
+namespace qdwhp {
+
+namespace {
+
+// Weights of every step from ell_0 (Section 2.1 and the weight lines of the Section 5
+// listing): L2 = l^2, d = cbrt(4(1 - L2)/L2^2), a = sqrt(1+d) + sqrt(8 - 4d + 8(2 - L2)/(L2 sqrt(1+d)))/2,
+// b = (a-1)^2/4, c = a + b - 1, l <- l (a + b L2)/(1 + c L2).  Stops when |l - 1| < 5 * 2^-52
+// or after fixed_iters steps when fixed_iters > 0.
+__global__ void dwh_schedule_kernel(const double* ell0_dev, double ell0_host, int fixed_iters, double c_qr,
+                                    Schedule* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double ell = ell0_dev ? *ell0_dev : ell0_host;
+  out->ell0 = ell;
+  int n = 0;
+  while (n < kMaxSteps) {
+    if (fixed_iters > 0) {
+      if (n >= fixed_iters) break;
+    } else if (fabs(ell - 1.0) < 5.0 * 0x1.0p-52) {
+      break;
+    }
+    double a, b, c, nxt;
+    if (ell >= 1.0) {
+      a = 3.0;
+      b = 1.0;
+      c = 3.0;
+      nxt = 1.0;
+    } else {
+      const double L2 = ell * ell;
+      const double d = cbrt(4.0 * (1.0 - L2) / (L2 * L2));
+      const double sqd = sqrt(1.0 + d);
+      a = sqd + 0.5 * sqrt(8.0 - 4.0 * d + 8.0 * (2.0 - L2) / (L2 * sqd));
+      b = (a - 1.0) * (a - 1.0) / 4.0;
+      c = a + b - 1.0;
+      nxt = fmin(ell * (a + b * L2) / (1.0 + c * L2), 1.0);
+    }
+    out->abc[3 * n + 0] = a;
+    out->abc[3 * n + 1] = b;
+    out->abc[3 * n + 2] = c;
+    out->ell_after[n] = nxt;
+    out->use_qr[n] = (c > c_qr) ? 1 : 0;
+    ell = nxt;
+    ++n;
+  }
+  out->nsteps = n;
+}
+
+}  // namespace
+
+qdwhp_status dwh_schedule(cudaStream_t st, const double* ell0_dev, double ell0_host, int fixed_iters, double c_qr,
+                          Schedule* out_dev) {
+  dwh_schedule_kernel<<<1, 32, 0, st>>>(ell0_dev, ell0_host, fixed_iters, c_qr, out_dev);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w) {
+  w.m = m;
+  w.n = n;
+  w.Z = ar.take<double>((size_t)n * n);
+  w.Linv = ar.take<double>(potrf_linv_elems(n));
+  w.Y = ar.take<double>((size_t)m * n);
+  w.scratch = ar.take<double>(std::max(potrf_scratch_elems(n), trsm_scratch_elems(m, n)));
+  w.fail = ar.take<int>(4);
+  w.diff_parts = ar.take<double>(kDiffParts);
+  w.diff = ar.take<double>(kMaxSteps);
+  w.has_qr = need_qr;
+  if (need_qr) {
+    const int64_t mm = m + n;
+    w.S = ar.take<double>((size_t)mm * n);
+    w.qf.Vall = ar.take<double>((size_t)mm * n);
+    w.qf.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+    w.qf.tau = ar.take<double>(n);
+    w.qf.diagR = ar.take<double>(n);
+    w.qr_scratch = ar.take<double>(qr_scratch_elems(mm, n));
+  }
+}
+
+qdwhp_status chol_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, double a, double b, double c,
+                       QdwhWs& w, int step) {
+  // Z = I + c X^T X (lower)
+  QDWHP_TRY(gemm(st, true, false, n, n, m, c, X, ldx, X, ldx, 0.0, w.Z, n, LOWER, 1.0));
+  QDWHP_TRY(potrf(st, n, w.Z, n, w.Linv, w.scratch, w.fail));
+  QDWHP_TRY(copy_matrix(st, m, n, X, ldx, w.Y, m));
+  QDWHP_TRY(trsm_right_lower(st, true, m, n, w.Y, m, w.Z, n, w.Linv, w.scratch));    // X W^{-1}
+  QDWHP_TRY(trsm_right_lower(st, false, m, n, w.Y, m, w.Z, n, w.Linv, w.scratch));   // (X W^{-1}) W^{-T}
+  QDWHP_TRY(axpby_diff(st, m, n, b / c, X, ldx, a - b / c, w.Y, m, w.diff_parts));
+  return reduce_parts(st, w.diff_parts, kDiffParts, w.diff + step);
+}
+
+qdwhp_status qr_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, double a, double b, double c,
+                     QdwhWs& w, int step) {
+  if (!w.has_qr) return QDWHP_ERR_ARG;
+  const int64_t mm = m + n;
+  const double sc = sqrt(c);
+  // S = [sqrt(c) X; I]
+  QDWHP_TRY(axpby(st, m, n, sc, X, ldx, 0.0, w.S, mm));
+  QDWHP_TRY(set_matrix(st, n, n, 0.0, 1.0, w.S + m, mm));
+  QDWHP_TRY(geqrf(st, mm, n, w.S, mm, w.qf, w.qr_scratch));
+  // explicit [Q1; Q2] (the compact factors live in qf, so S can be overwritten)
+  QDWHP_TRY(orgqr_columns(st, w.qf, 0, n, w.S, mm, w.qr_scratch));
+  // Y = Q1 Q2^T
+  QDWHP_TRY(gemm(st, false, true, m, n, n, 1.0, w.S, mm, w.S + m, mm, 0.0, w.Y, m));
+  QDWHP_TRY(axpby_diff(st, m, n, b / c, X, ldx, (a - b / c) / sc, w.Y, m, w.diff_parts));
+  return reduce_parts(st, w.diff_parts, kDiffParts, w.diff + step);
+}
+
+}  // namespace qdwhp
+
+// ---------------------------------------------------------------------------------------
+// C-ABI building blocks.
+
+using namespace qdwhp;
+
+extern "C" {
+
+QDWHP_API qdwhp_status qdwhp_gemm_f64(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                                      double* C, int64_t ldc, void* stream) {
+  if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
+  if (m == 0 || n == 0) return QDWHP_OK;
+  const int64_t rowsA = transa ? k : m, rowsB = transb ? n : k;
+  if (C == nullptr || ldc < m || lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB))
+    return QDWHP_ERR_ARG;
+  if (k > 0 && (A == nullptr || B == nullptr)) return QDWHP_ERR_ARG;
+  return gemm((cudaStream_t)stream, transa != 0, transb != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+QDWHP_API size_t qdwhp_potrf_workspace_bytes(int64_t n) {
+  Arena ar;
+  ar.dry = true;
+  ar.take<double>(potrf_linv_elems(n));
+  ar.take<double>(potrf_scratch_elems(n));
+  ar.take<int>(4);
+  return ar.used;
+}
+
+QDWHP_API qdwhp_status qdwhp_potrf_f64(int64_t n, double* Z, int64_t ldz, void* workspace, size_t ws_bytes,
+                                       int* info_host, void* stream) {
+  if (n < 0 || (n > 0 && (Z == nullptr || ldz < n))) return QDWHP_ERR_ARG;
+  if (info_host) *info_host = 0;
+  if (n == 0) return QDWHP_OK;
+  if (workspace == nullptr || ws_bytes < qdwhp_potrf_workspace_bytes(n)) return QDWHP_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar{(char*)workspace, ws_bytes};
+  double* Linv = ar.take<double>(potrf_linv_elems(n));
+  double* scratch = ar.take<double>(potrf_scratch_elems(n));
+  int* fail = ar.take<int>(4);
+  QDWHP_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
+  QDWHP_TRY(potrf(st, n, Z, ldz, Linv, scratch, fail));
+  int h = 0;
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(&h, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info_host) *info_host = h;
+  return h ? QDWHP_ERR_BREAKDOWN : QDWHP_OK;
+}
+
+QDWHP_API size_t qdwhp_qr_workspace_bytes(int64_t m, int64_t n) {
+  Arena ar;
+  ar.dry = true;
+  ar.take<double>((size_t)m * n);
+  ar.take<double>((size_t)ceil_div(std::max<int64_t>(n, 1), kQRNB) * kQRNB * kQRNB);
+  ar.take<double>(n);
+  ar.take<double>(n);
+  ar.take<double>(qr_scratch_elems(m, n));
+  return ar.used;
+}
+
+QDWHP_API qdwhp_status qdwhp_qr_f64(int64_t m, int64_t n, double* A, int64_t lda, double* Q, int64_t ldq, double* R,
+                                    int64_t ldr, void* workspace, size_t ws_bytes, void* stream) {
+  if (m < n || n < 0) return QDWHP_ERR_ARG;
+  if (n == 0) return QDWHP_OK;
+  if (!A || !Q || !R || lda < m || ldq < m || ldr < n) return QDWHP_ERR_ARG;
+  if (workspace == nullptr || ws_bytes < qdwhp_qr_workspace_bytes(m, n)) return QDWHP_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar{(char*)workspace, ws_bytes};
+  QRFactors f;
+  f.Vall = ar.take<double>((size_t)m * n);
+  f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+  f.tau = ar.take<double>(n);
+  f.diagR = ar.take<double>(n);
+  double* scratch = ar.take<double>(qr_scratch_elems(m, n));
+  QDWHP_TRY(geqrf(st, m, n, A, lda, f, scratch));
+  QDWHP_TRY(copy_upper(st, n, A, lda, R, ldr));
+  return orgqr_columns(st, f, 0, n, Q, ldq, scratch);
+}
+
+QDWHP_API size_t qdwhp_qdwh_workspace_bytes(int64_t m, int64_t n) {
+  Arena ar;
+  ar.dry = true;
+  QdwhWs w;
+  carve_qdwh(ar, m, n, true, w);
+  return ar.used;
+}
+
+QDWHP_API qdwhp_status qdwhp_qdwh_steps_f64(int64_t m, int64_t n, double* X, int64_t ldx, int32_t nsteps,
+                                            const double* abc_host, const int32_t* use_qr_host, double* conv_host,
+                                            void* workspace, size_t ws_bytes, void* stream) {
+  if (m < n || n < 1 || X == nullptr || ldx < m || nsteps < 0 || nsteps > kMaxSteps) return QDWHP_ERR_ARG;
+  if (nsteps > 0 && (abc_host == nullptr || use_qr_host == nullptr)) return QDWHP_ERR_ARG;
+  if (workspace == nullptr || ws_bytes < qdwhp_qdwh_workspace_bytes(m, n)) return QDWHP_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar{(char*)workspace, ws_bytes};
+  QdwhWs w;
+  carve_qdwh(ar, m, n, true, w);
+  QDWHP_CUDA_TRY(cudaMemsetAsync(w.fail, 0, sizeof(int), st));
+  for (int i = 0; i < nsteps; ++i) {
+    const double a = abc_host[3 * i], b = abc_host[3 * i + 1], c = abc_host[3 * i + 2];
+    if (use_qr_host[i])
+      QDWHP_TRY(qr_step(st, m, n, X, ldx, a, b, c, w, i));
+    else
+      QDWHP_TRY(chol_step(st, m, n, X, ldx, a, b, c, w, i));
+  }
+  double diffs[kMaxSteps];
+  int fail = 0;
+  if (nsteps > 0) QDWHP_CUDA_TRY(cudaMemcpyAsync(diffs, w.diff, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, st));
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(&fail, w.fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (conv_host)
+    for (int i = 0; i < nsteps; ++i) conv_host[i] = sqrt(diffs[i]);
+  return fail ? QDWHP_ERR_BREAKDOWN : QDWHP_OK;
+}
+
+}  // extern "C"

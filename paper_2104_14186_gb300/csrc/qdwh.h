@@ -1,0 +1,43 @@
+// Internal interfaces of qdwh.cu (QDWH steps and the device weight schedule).
+#pragma once
+
+#include "internal.h"
+
+namespace qdwhp {
+
+constexpr int kMaxSteps = 12;
+
+struct Schedule {
+  double ell0;
+  double abc[3 * kMaxSteps];
+  double ell_after[kMaxSteps];
+  int use_qr[kMaxSteps];
+  int nsteps;
+};
+
+struct QdwhWs {
+  int64_t m = 0, n = 0;
+  double* Z = nullptr;        // n x n: Z, then its Cholesky factor L (lower)
+  double* Linv = nullptr;     // inverses of the diagonal leaves of L
+  double* Y = nullptr;        // m x n solve / product buffer
+  double* scratch = nullptr;
+  int* fail = nullptr;        // first failing Cholesky column (0 = none), reset by the caller
+  double* diff_parts = nullptr;
+  double* diff = nullptr;     // ||X_k - X_{k-1}||_F^2 per step
+  bool has_qr = false;
+  double* S = nullptr;        // (m+n) x n stacked matrix, then its explicit Q
+  QRFactors qf;
+  double* qr_scratch = nullptr;
+};
+
+void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w);
+// Weights from ell_0 (device scalar if ell0_dev != null, else ell0_host); fixed_iters > 0
+// runs exactly that many steps, otherwise until |ell - 1| < 5 eps.
+qdwhp_status dwh_schedule(cudaStream_t st, const double* ell0_dev, double ell0_host, int fixed_iters, double c_qr,
+                          Schedule* out_dev);
+qdwhp_status chol_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, double a, double b, double c,
+                       QdwhWs& w, int step);
+qdwhp_status qr_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, double a, double b, double c,
+                     QdwhWs& w, int step);
+
+}  // namespace qdwhp

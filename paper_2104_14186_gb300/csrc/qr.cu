@@ -1,0 +1,309 @@
+// Blocked Householder QR (unpivoted) and explicit columns of Q.
+//
+// Used for the extraction step (Algorithm 1 step 3, Algorithm 2 step 3), the
+// QR-based QDWH step (eq. practical-polar-qr) and the orthonormalisation of the
+// count-to-threshold subspace.  Reflectors follow the LAPACK convention
+// H = I - tau v v^T with v_1 = 1, and each kCholNB-wide... (kQRNB-wide) panel is
+// accumulated into the compact WY form Q_p = I - V T V^T (T upper triangular).
+//
+// One SM does only a few FP64 flops per clock on this part, so a panel factored by
+// a single CTA would be ~100x slower than the chip.  The panel kernel is therefore
+// a cooperative launch over up to kPanelCTAs CTAs: each CTA keeps its slice of
+// rows in shared memory, and the column norms and the reflector-application dot
+// products are reduced across CTAs through global partials with two grid-wide
+// barriers per column.  Partials are summed in CTA order, so the factorisation is
+// reproducible run to run.  The trailing update and the formation of Q are GEMMs.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace qdwhp {
+
+namespace {
+
+constexpr int NB = kQRNB;          // panel width (32)
+constexpr int kPanelThreads = 256;
+constexpr int kPanelCTAs = 120;
+constexpr int kMinRowsPerCTA = 32;
+constexpr int kPartStride = NB + 1;
+
+struct PanelArgs {
+  int R;            // rows of the panel (from its diagonal down)
+  int jb;           // width
+  double* P;        // A(j, j)
+  int64_t lda;
+  double* V;        // explicit reflectors, R x jb, ld ldv
+  int64_t ldv;
+  double* T;        // jb x jb (ld NB)
+  double* tau;      // jb
+  double* diagR;    // jb
+  double* part;     // gridDim.x * kPartStride
+  double* gram;     // gridDim.x * NB * NB
+  double* alpha_slot;
+};
+
+__global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double s[];          // local rows: s[r + c * rpc]
+  __shared__ double red[32];
+  __shared__ double red8[8][NB];
+  __shared__ double wsh[NB];
+  __shared__ double taus[NB], betas[NB];
+
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int R = a.R, jb = a.jb;
+  const int rpc = (R + G - 1) / G;
+  const int r0 = b * rpc;
+  const int nr = max(0, min(R, r0 + rpc) - r0);
+
+  for (int e = tid; e < rpc * NB; e += blockDim.x) {
+    const int r = e % rpc, c = e / rpc;
+    s[e] = (r < nr && c < jb) ? a.P[(r0 + r) + (int64_t)c * a.lda] : 0.0;
+  }
+  __syncthreads();
+
+  for (int i = 0; i < jb; ++i) {
+    // Phase A: partial ||x(i+1:)||^2 of column i; the owner of row i publishes alpha.
+    double acc = 0.0;
+    for (int r = tid; r < nr; r += blockDim.x) {
+      if (r0 + r > i) {
+        const double v = s[r + i * rpc];
+        acc += v * v;
+      }
+    }
+    acc = block_sum(acc, red);
+    if (tid == 0) {
+      a.part[b * kPartStride] = acc;
+      if (i >= r0 && i < r0 + nr) *a.alpha_slot = s[(i - r0) + i * rpc];
+    }
+    grid.sync();
+
+    // Phase B: every CTA forms the same reflector (sums in CTA order).
+    double ss = 0.0;
+    for (int g = tid; g < G; g += blockDim.x) ss += a.part[g * kPartStride];
+    ss = block_sum(ss, red);
+    const double alpha = *a.alpha_slot;
+    double beta, tau_i, scale;
+    if (ss == 0.0) {
+      beta = alpha;
+      tau_i = 0.0;
+      scale = 0.0;
+    } else {
+      beta = -copysign(sqrt(alpha * alpha + ss), alpha);
+      tau_i = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    if (tid == 0) {
+      taus[i] = tau_i;
+      betas[i] = beta;
+    }
+    for (int r = tid; r < nr; r += blockDim.x) {
+      const int rg = r0 + r;
+      if (rg > i) s[r + i * rpc] *= scale;
+      else if (rg == i) s[r + i * rpc] = 1.0;
+    }
+    __syncthreads();
+    // partial w_c = sum_{rows >= i} v_r x_r,c for c > i
+    {
+      const int c = tid % NB, grp = tid / NB;   // 8 row groups x 32 columns
+      double p = 0.0;
+      if (c > i && c < jb) {
+        for (int r = grp; r < nr; r += 8) {
+          if (r0 + r >= i) p += s[r + i * rpc] * s[r + c * rpc];
+        }
+      }
+      red8[grp][c] = p;
+    }
+    __syncthreads();
+    if (tid < NB) {
+      double p = 0.0;
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8) p += red8[g8][tid];
+      if (tid > i && tid < jb) a.part[b * kPartStride + tid] = p;
+    }
+    grid.sync();
+
+    // Phase C: sum the partials and update the remaining panel columns.
+    if (tid < NB) {
+      double w = 0.0;
+      if (tid > i && tid < jb)
+        for (int g = 0; g < G; ++g) w += a.part[g * kPartStride + tid];
+      wsh[tid] = w;
+    }
+    __syncthreads();
+    if (tau_i != 0.0) {
+      for (int e = tid; e < nr * NB; e += blockDim.x) {
+        const int r = e % nr, c = e / nr;
+        if (c > i && c < jb && r0 + r >= i) s[r + c * rpc] -= tau_i * wsh[c] * s[r + i * rpc];
+      }
+    }
+    __syncthreads();
+  }
+
+  // Gram matrix V^T V of the explicit reflectors (for T), partial per CTA.
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int p = e % NB, q = e / NB;
+    double acc = 0.0;
+    if (p < jb && q < jb) {
+      for (int r = 0; r < nr; ++r) {
+        const int rg = r0 + r;
+        const double vp = (rg > p) ? s[r + p * rpc] : (rg == p ? 1.0 : 0.0);
+        const double vq = (rg > q) ? s[r + q * rpc] : (rg == q ? 1.0 : 0.0);
+        acc += vp * vq;
+      }
+    }
+    a.gram[(size_t)b * NB * NB + e] = acc;
+  }
+  // Write back: R above the diagonal and beta on it, compact v below; explicit V.
+  for (int e = tid; e < nr * jb; e += blockDim.x) {
+    const int r = e % nr, c = e / nr;
+    const int rg = r0 + r;
+    const double v = s[r + c * rpc];
+    double* ap = a.P + rg + (int64_t)c * a.lda;
+    double* vp = a.V + rg + (int64_t)c * a.ldv;
+    if (rg < c) {
+      *ap = v;
+      *vp = 0.0;
+    } else if (rg == c) {
+      *ap = betas[c];
+      *vp = 1.0;
+    } else {
+      *ap = v;
+      *vp = v;
+    }
+  }
+  grid.sync();
+
+  if (b == 0) {
+    // T (forward, columnwise): T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T v_i)(0:i).
+    __shared__ double gsum[NB][NB + 1];
+    __shared__ double Ts[NB][NB + 1];
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      double acc = 0.0;
+      for (int g = 0; g < G; ++g) acc += a.gram[(size_t)g * NB * NB + e];
+      gsum[e % NB][e / NB] = acc;
+      Ts[e % NB][e / NB] = 0.0;
+    }
+    __syncthreads();
+    for (int i = 0; i < jb; ++i) {
+      if (tid < i) {
+        double acc = 0.0;
+        for (int q = tid; q < i; ++q) acc += Ts[tid][q] * gsum[q][i];
+        Ts[tid][i] = -taus[i] * acc;
+      }
+      if (tid == 0) Ts[i][i] = taus[i];
+      __syncthreads();
+    }
+    for (int e = tid; e < NB * NB; e += blockDim.x) a.T[e] = Ts[e % NB][e / NB];
+    if (tid < jb) {
+      a.tau[tid] = taus[tid];
+      a.diagR[tid] = betas[tid];
+    }
+  }
+}
+
+int panel_ctas(int R) {
+  int g = (R + kMinRowsPerCTA - 1) / kMinRowsPerCTA;
+  return std::max(1, std::min(g, kPanelCTAs));
+}
+
+size_t panel_smem_bytes(int R, int G) {
+  const int rpc = (R + G - 1) / G;
+  return (size_t)rpc * NB * sizeof(double);
+}
+
+qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
+  const int G = panel_ctas(pa.R);
+  const size_t smem = panel_smem_bytes(pa.R, G);
+  static bool attr_set = false;
+  if (!attr_set) {
+    QDWHP_CUDA_TRY(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr_set = true;
+  }
+  if (smem > 160 * 1024) return QDWHP_ERR_ARG;
+  void* args[] = {&pa};
+  QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, st));
+  return QDWHP_OK;
+}
+
+}  // namespace
+
+size_t qr_scratch_elems(int64_t m, int64_t n) {
+  const size_t wn = (size_t)NB * std::max<int64_t>(n, 1);
+  size_t splitk = gemm_splitk_ws_elems(NB, std::max<int64_t>(n, 1));
+  return 2 * wn + splitk + (size_t)kPanelCTAs * kPartStride + (size_t)kPanelCTAs * NB * NB + 64;
+  (void)m;
+}
+
+qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f, double* scratch) {
+  if (m < n || n < 0) return QDWHP_ERR_ARG;
+  f.m = m;
+  f.n = n;
+  if (n == 0) return QDWHP_OK;
+  double* W = scratch;
+  double* W2 = W + (size_t)NB * n;
+  const size_t splitk_elems = gemm_splitk_ws_elems(NB, n);
+  double* splitk = W2 + (size_t)NB * n;
+  double* part = splitk + splitk_elems;
+  double* gram = part + (size_t)kPanelCTAs * kPartStride;
+  double* alpha_slot = gram + (size_t)kPanelCTAs * NB * NB;
+  for (int64_t j = 0; j < n; j += NB) {
+    const int jb = (int)std::min<int64_t>(NB, n - j);
+    const int64_t R = m - j;
+    PanelArgs pa;
+    pa.R = (int)R;
+    pa.jb = jb;
+    pa.P = A + j + j * lda;
+    pa.lda = lda;
+    pa.V = f.Vall + j + j * m;
+    pa.ldv = m;
+    pa.T = f.T + (size_t)(j / NB) * NB * NB;
+    pa.tau = f.tau + j;
+    pa.diagR = f.diagR + j;
+    pa.part = part;
+    pa.gram = gram;
+    pa.alpha_slot = alpha_slot;
+    QDWHP_TRY(launch_panel(st, pa));
+    const int64_t nc = n - j - jb;
+    if (nc > 0) {
+      double* C = A + j + (j + jb) * lda;
+      // W = V^T C ; W2 = T^T W ; C -= V W2
+      QDWHP_TRY(gemm(st, true, false, jb, nc, R, 1.0, pa.V, m, C, lda, 0.0, W, jb, FULL, 0.0, splitk, splitk_elems));
+      QDWHP_TRY(gemm(st, true, false, jb, nc, jb, 1.0, pa.T, NB, W, jb, 0.0, W2, jb));
+      QDWHP_TRY(gemm(st, false, false, R, nc, jb, -1.0, pa.V, m, W2, jb, 1.0, C, lda));
+    }
+  }
+  return QDWHP_OK;
+}
+
+qdwhp_status orgqr_columns(cudaStream_t st, const QRFactors& f, int64_t col0, int64_t ncols, double* C, int64_t ldc,
+                           double* scratch) {
+  const int64_t m = f.m, n = f.n;
+  if (col0 < 0 || ncols < 0 || col0 + ncols > n) return QDWHP_ERR_ARG;
+  if (ncols == 0) return QDWHP_OK;
+  QDWHP_TRY(set_matrix(st, m, ncols, 0.0, 0.0, C, ldc));
+  QDWHP_TRY(set_matrix(st, ncols, ncols, 0.0, 1.0, C + col0, ldc));
+  double* W = scratch;
+  double* W2 = W + (size_t)NB * ncols;
+  const size_t splitk_elems = gemm_splitk_ws_elems(NB, ncols);
+  double* splitk = W2 + (size_t)NB * ncols;
+  // Blocks whose first column is past the selected range act on zero rows: skip them.
+  const int64_t last_block = (col0 + ncols - 1) / NB;
+  for (int64_t p = last_block; p >= 0; --p) {
+    const int64_t j = p * NB;
+    const int jb = (int)std::min<int64_t>(NB, n - j);
+    const int64_t R = m - j;
+    const double* V = f.Vall + j + j * m;
+    const double* T = f.T + (size_t)p * NB * NB;
+    double* Cj = C + j;
+    // C(j:, :) -= V (T (V^T C(j:, :)))
+    QDWHP_TRY(gemm(st, true, false, jb, ncols, R, 1.0, V, m, Cj, ldc, 0.0, W, jb, FULL, 0.0, splitk, splitk_elems));
+    QDWHP_TRY(gemm(st, false, false, jb, ncols, jb, 1.0, T, NB, W, jb, 0.0, W2, jb));
+    QDWHP_TRY(gemm(st, false, false, R, ncols, jb, -1.0, V, m, W2, jb, 1.0, Cj, ldc));
+  }
+  return QDWHP_OK;
+}
+
+}  // namespace qdwhp

@@ -1,0 +1,598 @@
+// QDWHpartial-EIG (Algorithm 1) and QDWHpartial-SVD (Algorithm 2) drivers and the
+// solver entry points of the C ABI.
+//
+// Every step runs in this library's kernels; the host enqueues them on the caller's
+// stream and reads back a handful of scalars at stage boundaries (spectral bounds,
+// the threshold, the subspace size ell, the count of captured pairs, Jacobi
+// convergence) because they decide launch shapes and control flow.
+//
+// Readings where the paper is silent (also stated in the oracle):
+//   * the wanted side is made negative by A' = eps A (eps = -1 for LARGEST) and the
+//     threshold t' by a shift, B = A' - t' I (remark after Algorithm 1);
+//   * mu = lam_lo - t', lam_lo = Lanczos lower bound (Ritz value - residual, pushed
+//     1 % of the spread outwards); Algorithm 1 step 1 scales by |mu|;
+//   * a requested count k becomes a threshold through the k-th Ritz value of a
+//     (k+p)-dimensional subspace (Cauchy interlacing guarantees >= k pairs beyond it);
+//   * the wanted width is kept >= guard * spread (default 5 %);
+//   * QR-based QDWH steps while c_k > c_qr (default 100), Section 4.2.
+#include <cstdio>
+
+#include "internal.h"
+#include "krylov.h"
+#include "qdwh.h"
+
+namespace qdwhp {
+
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_err, sizeof(g_err), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line,
+           cudaGetErrorString(e));
+}
+
+namespace {
+
+__global__ void index_scan_kernel(int n, const double* diagR, double tol, int* ind) {
+  __shared__ int best;
+  if (threadIdx.x == 0) best = n;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (fabs(diagR[i]) < tol) atomicMin(&best, i);
+  __syncthreads();
+  if (threadIdx.x == 0) *ind = best;
+}
+
+__global__ void symmetrize_avg_kernel(int n, double* H, int64_t ldh) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) {
+      const double v = 0.5 * (H[i + (int64_t)j * ldh] + H[j + (int64_t)i * ldh]);
+      H[i + (int64_t)j * ldh] = v;
+      H[j + (int64_t)i * ldh] = v;
+    }
+  }
+}
+
+__global__ void transpose_kernel(int rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb) {
+  // B (cols x rows) = A^T
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = bx + threadIdx.x, j = by + k;
+    if (i < rows && j < cols) tile[k][threadIdx.x] = A[i + (int64_t)j * lda];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = by + threadIdx.x, j = bx + k;   // B(i, j) = A(j, i)
+    if (i < cols && j < rows) B[i + (int64_t)j * ldb] = tile[threadIdx.x][k];
+  }
+}
+
+qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh) {
+  if (n <= 1) return QDWHP_OK;
+  const size_t total = (size_t)n * n;
+  symmetrize_avg_kernel<<<(int)std::min<size_t>((total + 255) / 256, 8 * kNumSMs), 256, 0, st>>>((int)n, H, ldh);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+constexpr double kEps = 0x1.0p-52;
+
+struct Common {
+  // small-problem and control buffers shared by both drivers
+  LanczosState* lst = nullptr;
+  JacobiState* jst = nullptr;
+  Schedule* sched = nullptr;
+  int* ints = nullptr;        // [0] ind, [1] count, [2..] spare
+  unsigned* nonfinite = nullptr;
+  double* vals = nullptr;     // n
+  int* order = nullptr;       // n
+  double* lws = nullptr;      // Lanczos workspace
+  double* splitk = nullptr;
+  size_t splitk_elems = 0;
+};
+
+// Pinned host staging for scalars read back from the device.
+struct HostScalars {
+  LanczosState lst;
+  JacobiState jst;
+  Schedule sched;
+  int ints[4];
+  unsigned nonfinite;
+};
+
+void carve_common(Arena& ar, int64_t m, int64_t n, int steps, Common& c) {
+  c.lst = ar.take<LanczosState>(1);
+  c.jst = ar.take<JacobiState>(1);
+  c.sched = ar.take<Schedule>(1);
+  c.ints = ar.take<int>(8);
+  c.nonfinite = ar.take<unsigned>(4);
+  c.vals = ar.take<double>(std::max<int64_t>(n, 1));
+  c.order = ar.take<int>(std::max<int64_t>(n, 1));
+  c.lws = ar.take<double>(lanczos_ws_elems(m, n, std::max(1, std::min(steps, 48))));
+  c.splitk_elems = std::min<size_t>(gemm_splitk_ws_elems(std::min<int64_t>(n, 2048), std::min<int64_t>(n, 2048)),
+                                    size_t(8) << 20);
+  c.splitk = ar.take<double>(c.splitk_elems);
+}
+
+int64_t resolve_k(int64_t n, const qdwhp_opts& o, int64_t k_arg) {
+  if (k_arg > 0) return k_arg;
+  if (o.count > 0) return o.count;
+  return qdwhp_k_from_fraction(n, o.fraction);
+}
+
+struct Timer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) cudaEventRecord(e0, st);
+  }
+  float stop() {
+    float ms = 0.f;
+    if (e0 && e1) {
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return ms;
+  }
+  ~Timer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+qdwhp_status sync_read(cudaStream_t st, void* host, const void* dev, size_t bytes) {
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st));
+  QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+  return QDWHP_OK;
+}
+
+// Orthonormal basis of the columns of Y (rows x b): Householder QR then explicit Q.
+qdwhp_status orth(cudaStream_t st, int64_t rows, int64_t b, double* Y, double* Qout, QRFactors& f, double* scratch) {
+  QDWHP_TRY(geqrf(st, rows, b, Y, rows, f, scratch));
+  return orgqr_columns(st, f, 0, b, Qout, rows, scratch);
+}
+
+// ---------------------------------------------------------------------------------------
+struct EigWs {
+  Common c;
+  QdwhWs q;
+  QRFactors f;
+  double* qr_scratch = nullptr;
+  double* X = nullptr;   // n x n iterate
+  double* S1 = nullptr;  // n x n capacity: M (Rayleigh-Ritz matrix) / H
+  double* S2 = nullptr;  // n x n capacity: G, then M V, then gathered W
+  double* S3 = nullptr;  // n x n capacity: Vj
+};
+
+void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
+  carve_common(ar, n, n, o.lanczos_steps, w.c);
+  carve_qdwh(ar, n, n, false, w.q);
+  w.X = ar.take<double>((size_t)n * n);
+  w.f.Vall = ar.take<double>((size_t)n * n);
+  w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+  w.f.tau = ar.take<double>(n);
+  w.f.diagR = ar.take<double>(n);
+  w.qr_scratch = ar.take<double>(qr_scratch_elems(n, n));
+  w.S1 = ar.take<double>((size_t)n * n);
+  w.S2 = ar.take<double>((size_t)n * n);
+  w.S3 = ar.take<double>((size_t)n * n);
+}
+
+// Eigenvalues (Rayleigh quotients, into w.c.vals) and eigenvectors (S3) of the
+// symmetric ell x ell matrix in S1, whose spectrum lies above `lower`.
+qdwhp_status small_sym_eig(cudaStream_t st, int64_t ell, double lower, EigWs& w, int max_sweeps, HostScalars& hs,
+                           int* sweeps) {
+  QDWHP_TRY(symmetrize_avg(st, ell, w.S1, ell));
+  // G = M - lower I is positive semidefinite; its right singular vectors are M's eigenvectors.
+  QDWHP_TRY(axpby(st, ell, ell, 1.0, w.S1, ell, 0.0, w.S2, ell, -lower));
+  int conv = 0;
+  const double tol = kEps * std::sqrt((double)std::max<int64_t>(ell, 1));
+  QDWHP_TRY(jacobi_onesided(st, ell, ell, w.S2, ell, w.S3, ell, max_sweeps, tol, w.c.jst, &hs.jst, sweeps, &conv));
+  if (!conv) return QDWHP_ERR_NOT_CONVERGED;
+  // Rayleigh quotients v_i^T M v_i
+  QDWHP_TRY(gemm(st, false, false, ell, ell, ell, 1.0, w.S1, ell, w.S3, ell, 0.0, w.S2, ell));
+  return column_dots(st, ell, ell, w.S3, ell, w.S2, ell, w.c.vals);
+}
+
+qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts& o, double* lambda, double* V,
+                      int64_t ldv, void* workspace, size_t ws_bytes, qdwhp_info* info, cudaStream_t st) {
+  const int64_t k = resolve_k(n, o, 0);
+  if (k < 1 || k > n) return QDWHP_ERR_ARG;
+  Arena ar{(char*)workspace, ws_bytes};
+  EigWs w;
+  carve_eig(ar, n, o, w);
+  if (!ar.ok()) return QDWHP_ERR_NOMEM;
+  Timer timer(st);
+  HostScalars hs;
+  qdwhp_info inf;
+  memset(&inf, 0, sizeof(inf));
+  const double eps_side = (o.side == QDWHP_SMALLEST) ? 1.0 : -1.0;
+
+  QDWHP_CUDA_TRY(cudaMemsetAsync(w.c.nonfinite, 0, sizeof(unsigned), st));
+  QDWHP_TRY(count_nonfinite(st, n, n, A, lda, w.c.nonfinite));
+  // Step 1: Lanczos bounds.
+  QDWHP_TRY(lanczos(st, false, n, n, A, lda, o.lanczos_steps, o.seed, w.c.lws, w.c.lst));
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.nonfinite, w.c.nonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  QDWHP_TRY(sync_read(st, &hs.lst, w.c.lst, sizeof(LanczosState)));
+  if (hs.nonfinite || hs.lst.nonfinite) return QDWHP_ERR_NONFINITE;
+  const double th_min = hs.lst.out[0], r_min = hs.lst.out[1], th_max = hs.lst.out[2], r_max = hs.lst.out[3];
+  double lo_raw, hi_raw;
+  if (eps_side < 0) {
+    lo_raw = -(th_max + r_max);
+    hi_raw = -(th_min - r_min);
+  } else {
+    lo_raw = th_min - r_min;
+    hi_raw = th_max + r_max;
+  }
+  const double spread = std::max(hi_raw - lo_raw, 1e-300);
+  const double lam_lo = lo_raw - 0.01 * spread, lam_hi = hi_raw + 0.01 * spread;
+
+  // Threshold for the requested count: q power steps on lam_hi I - A', Rayleigh-Ritz of A'.
+  const int64_t b = std::min<int64_t>(n, k + o.block_extra);
+  double* Om = w.X;          // n x b
+  double* Yb = w.q.Y;        // n x b
+  double* Qb = w.q.Z;        // n x b
+  double* AQ = w.S2;         // n x b
+  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Om, n));
+  QDWHP_TRY(axpby(st, n, b, lam_hi, Om, n, 0.0, Yb, n));
+  QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Om, n, 1.0, Yb, n));
+  for (int it = 0; it < o.power_steps; ++it) {
+    QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
+    QDWHP_TRY(axpby(st, n, b, lam_hi, Qb, n, 0.0, Yb, n));
+    QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Qb, n, 1.0, Yb, n));
+  }
+  QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
+  QDWHP_TRY(gemm(st, false, false, n, b, n, eps_side, A, lda, Qb, n, 0.0, AQ, n));
+  QDWHP_TRY(gemm(st, true, false, b, b, n, 1.0, Qb, n, AQ, n, 0.0, w.S1, b, FULL, 0.0, w.c.splitk, w.c.splitk_elems));
+  int sweeps = 0;
+  QDWHP_TRY(small_sym_eig(st, b, lam_lo, w, o.jacobi_max_sweeps, hs, &sweeps));
+  QDWHP_TRY(select_sort(st, b, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
+  QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
+  QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
+  double theta_k = 0.0;
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.sched, w.c.sched, sizeof(Schedule), cudaMemcpyDeviceToHost, st));
+  QDWHP_TRY(sync_read(st, &theta_k, w.S1, sizeof(double)));
+  double t = theta_k + 1e-10 * spread;
+  t = std::max(t, lam_lo + o.guard * (lam_hi - lam_lo));
+  const double s = o.s_eig;
+
+  int retries = 0;
+  int64_t ell = 0;
+  double mu = 0.0;
+  int count = 0;
+  for (;;) {
+    mu = lam_lo - t;
+    const double absmu = std::fabs(mu);
+    // Steps 1-2: X0 = (1-s) B / |mu| - s I with B = eps A - t I.
+    QDWHP_TRY(axpby(st, n, n, (1.0 - s) * eps_side / absmu, A, lda, 0.0, w.X, n, -((1.0 - s) * t / absmu + s)));
+    QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
+    for (int i = 0; i < hs.sched.nsteps; ++i)
+      QDWHP_TRY(chol_step(st, n, n, w.X, n, hs.sched.abc[3 * i], hs.sched.abc[3 * i + 1], hs.sched.abc[3 * i + 2],
+                          w.q, i));
+    // Step 3: QR of (r(A~) + I) / 2.
+    QDWHP_TRY(axpby(st, n, n, 0.5, w.X, n, 0.0, w.X, n, 0.5));
+    QDWHP_TRY(geqrf(st, n, n, w.X, n, w.f, w.qr_scratch));
+    // Step 4: index rule.
+    index_scan_kernel<<<1, 1024, 0, st>>>((int)n, w.f.diagR, o.tol, w.c.ints);
+    QDWHP_LAUNCH_CHECK();
+    int fail = 0;
+    double diffs[kMaxSteps];
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(&fail, w.q.fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(diffs, w.q.diff, sizeof(double) * kMaxSteps, cudaMemcpyDeviceToHost, st));
+    QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
+    if (fail) return QDWHP_ERR_BREAKDOWN;
+    for (int i = 0; i < hs.sched.nsteps && i < 12; ++i) {
+      inf.conv[i] = std::sqrt(diffs[i]);
+      inf.ell_k[i] = hs.sched.ell_after[i];
+    }
+    const int ind = hs.ints[0];
+    ell = n - ind;
+    count = 0;
+    if (ell > 0) {
+      // Step 5: Q2 = trailing ell columns of Q.
+      double* Q2 = w.q.Y;
+      QDWHP_TRY(orgqr_columns(st, w.f, ind, ell, Q2, n, w.qr_scratch));
+      // Step 6: Rayleigh-Ritz on the original A.
+      double* AQ2 = w.q.Z;
+      QDWHP_TRY(gemm(st, false, false, n, ell, n, 1.0, A, lda, Q2, n, 0.0, AQ2, n));
+      QDWHP_TRY(gemm(st, true, false, ell, ell, n, 1.0, Q2, n, AQ2, n, 0.0, w.S1, ell, FULL, 0.0, w.c.splitk,
+                     w.c.splitk_elems));
+      const double a_lo = th_min - r_min - 0.01 * spread;   // lower bound of A's spectrum
+      QDWHP_TRY(small_sym_eig(st, ell, a_lo, w, o.jacobi_max_sweeps, hs, &sweeps));
+      inf.jacobi_sweeps = sweeps;
+      // wanted: eps * theta <= t, ordered ascending in eps * theta
+      QDWHP_TRY(select_sort(st, ell, w.c.vals, eps_side, t, w.c.order, w.c.ints + 1));
+      QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
+      count = hs.ints[1];
+    }
+    if (count >= k || retries >= o.max_retries) break;
+    ++retries;
+    t = t + 0.25 * (lam_hi - t);
+  }
+  if (count < k) return QDWHP_ERR_COUNT;
+  // Step 7: the k wanted pairs, V = Q2 W.
+  QDWHP_TRY(gather_values(st, k, w.c.vals, w.c.order, lambda));
+  QDWHP_TRY(gather_columns(st, ell, k, w.S3, ell, w.c.order, nullptr, w.S2, ell));
+  QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, w.S2, ell, 0.0, V, ldv));
+  inf.ms_total = timer.stop();
+  inf.it_chol = hs.sched.nsteps;
+  inf.it_qr = 0;
+  inf.retries = retries;
+  inf.ell = ell;
+  inf.k = k;
+  inf.t = eps_side * t;
+  inf.mu = eps_side * mu;
+  if (info) *info = inf;
+  return QDWHP_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+struct SvdWs {
+  Common c;
+  QdwhWs q;
+  QRFactors f;
+  double* qr_scratch = nullptr;
+  double* X = nullptr;    // m x n iterate
+  double* C = nullptr;    // m x n capacity: A Q2 (and A Qb)
+  double* Vj = nullptr;   // n x n capacity
+  double* W = nullptr;    // n x n capacity: gathered V~
+  double* At = nullptr;   // transposed input when m < n
+};
+
+void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
+  carve_common(ar, m, n, o.lanczos_steps, w.c);
+  carve_qdwh(ar, m, n, true, w.q);
+  w.X = ar.take<double>((size_t)m * n);
+  w.f.Vall = ar.take<double>((size_t)n * n);
+  w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+  w.f.tau = ar.take<double>(n);
+  w.f.diagR = ar.take<double>(n);
+  w.qr_scratch = ar.take<double>(qr_scratch_elems(n, n));
+  w.C = ar.take<double>((size_t)m * n);
+  w.Vj = ar.take<double>((size_t)n * n);
+  w.W = ar.take<double>((size_t)n * n);
+  if (need_transpose) w.At = ar.take<double>((size_t)m * n);
+}
+
+qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_t k, const qdwhp_opts& o,
+                      double* sigma, double* U, int64_t ldu, double* V, int64_t ldv, SvdWs& w, qdwhp_info* info,
+                      cudaStream_t st) {
+  Timer timer(st);
+  HostScalars hs;
+  qdwhp_info inf;
+  memset(&inf, 0, sizeof(inf));
+  QDWHP_CUDA_TRY(cudaMemsetAsync(w.c.nonfinite, 0, sizeof(unsigned), st));
+  QDWHP_TRY(count_nonfinite(st, m, n, A, lda, w.c.nonfinite));
+  // Step 1: alpha ~ ||A||_2 from Lanczos on A^T A.
+  QDWHP_TRY(lanczos(st, true, m, n, A, lda, o.lanczos_steps, o.seed, w.c.lws, w.c.lst));
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.nonfinite, w.c.nonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  QDWHP_TRY(sync_read(st, &hs.lst, w.c.lst, sizeof(LanczosState)));
+  if (hs.nonfinite || hs.lst.nonfinite) return QDWHP_ERR_NONFINITE;
+  const double alpha = std::sqrt(std::max(hs.lst.out[2] + hs.lst.out[3], 0.0));
+  if (!(alpha > 0.0)) return QDWHP_ERR_ARG;
+
+  // Relative threshold s from the k-th Ritz value of A^T A on a (k+p)-dim subspace.
+  const int64_t b = std::min<int64_t>(n, k + o.block_extra);
+  double* Om = w.q.Z;    // n x b
+  double* T1 = w.X;      // m x b
+  double* Yb = w.q.Y;    // n x b
+  double* Qb = w.Vj;     // n x b
+  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Om, n));
+  QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Om, n, 0.0, T1, m));
+  QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Yb, n));
+  for (int it = 0; it < o.power_steps; ++it) {
+    QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
+    QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qb, n, 0.0, T1, m));
+    QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Yb, n));
+  }
+  QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
+  QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qb, n, 0.0, w.C, m));
+  int sweeps = 0, conv = 0;
+  const double tol_b = kEps * std::sqrt((double)m);
+  QDWHP_TRY(jacobi_onesided(st, m, b, w.C, m, w.W, b, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst, &sweeps, &conv));
+  if (!conv) return QDWHP_ERR_NOT_CONVERGED;
+  QDWHP_TRY(column_norms(st, m, b, w.C, m, w.c.vals));
+  QDWHP_TRY(select_sort(st, b, w.c.vals, -1.0, INFINITY, w.c.order, w.c.ints + 1));
+  QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.q.Z));
+  double sig_hat = 0.0;
+  QDWHP_TRY(sync_read(st, &sig_hat, w.q.Z, sizeof(double)));
+  double s = std::max(sig_hat / alpha * (1.0 - 1e-10), 1e-15);
+
+  int retries = 0;
+  int64_t ell = 0;
+  int count = 0;
+  for (;;) {
+    QDWHP_TRY(dwh_schedule(st, nullptr, s, 0, o.c_qr, w.c.sched));
+    QDWHP_TRY(sync_read(st, &hs.sched, w.c.sched, sizeof(Schedule)));
+    // Step 2: QDWH on A / alpha from ell_0 = s.
+    QDWHP_TRY(axpby(st, m, n, 1.0 / alpha, A, lda, 0.0, w.X, m));
+    QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
+    inf.it_qr = inf.it_chol = 0;
+    for (int i = 0; i < hs.sched.nsteps; ++i) {
+      const double a = hs.sched.abc[3 * i], bb = hs.sched.abc[3 * i + 1], c = hs.sched.abc[3 * i + 2];
+      if (hs.sched.use_qr[i]) {
+        QDWHP_TRY(qr_step(st, m, n, w.X, m, a, bb, c, w.q, i));
+        ++inf.it_qr;
+      } else {
+        QDWHP_TRY(chol_step(st, m, n, w.X, m, a, bb, c, w.q, i));
+        ++inf.it_chol;
+      }
+    }
+    // Step 3: QR of I - X^T X.
+    double* B = w.q.Z;
+    QDWHP_TRY(gemm(st, true, false, n, n, m, -1.0, w.X, m, w.X, m, 0.0, B, n, LOWER, 1.0));
+    QDWHP_TRY(symmetrize_from_lower(st, n, B, n));
+    QDWHP_TRY(geqrf(st, n, n, B, n, w.f, w.qr_scratch));
+    index_scan_kernel<<<1, 1024, 0, st>>>((int)n, w.f.diagR, o.tol, w.c.ints);
+    QDWHP_LAUNCH_CHECK();
+    int fail = 0;
+    double diffs[kMaxSteps];
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(&fail, w.q.fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(diffs, w.q.diff, sizeof(double) * kMaxSteps, cudaMemcpyDeviceToHost, st));
+    QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
+    if (fail) return QDWHP_ERR_BREAKDOWN;
+    for (int i = 0; i < hs.sched.nsteps && i < 12; ++i) {
+      inf.conv[i] = std::sqrt(diffs[i]);
+      inf.ell_k[i] = hs.sched.ell_after[i];
+    }
+    const int ind = hs.ints[0];
+    ell = n - ind;
+    count = 0;
+    if (ell > 0) {
+      // Steps 5-6: Q2, A Q2 and its SVD by one-sided Jacobi.
+      double* Q2 = w.q.Y;
+      QDWHP_TRY(orgqr_columns(st, w.f, ind, ell, Q2, n, w.qr_scratch));
+      QDWHP_TRY(gemm(st, false, false, m, ell, n, 1.0, A, lda, Q2, n, 0.0, w.C, m));
+      const double tol = kEps * std::sqrt((double)m);
+      QDWHP_TRY(jacobi_onesided(st, m, ell, w.C, m, w.Vj, ell, o.jacobi_max_sweeps, tol, w.c.jst, &hs.jst, &sweeps,
+                                &conv));
+      if (!conv) return QDWHP_ERR_NOT_CONVERGED;
+      inf.jacobi_sweeps = sweeps;
+      QDWHP_TRY(column_norms(st, m, ell, w.C, m, w.c.vals));
+      // Step 7: sigma >= s alpha, descending.
+      QDWHP_TRY(select_sort(st, ell, w.c.vals, -1.0, -s * alpha, w.c.order, w.c.ints + 1));
+      QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
+      count = hs.ints[1];
+    }
+    if (count >= k || retries >= o.max_retries) break;
+    ++retries;
+    s = std::max(0.5 * s, 1e-15);
+  }
+  if (count < k) return QDWHP_ERR_COUNT;
+  // Step 8: U1 = U~1, V1 = Q2 V~1.
+  QDWHP_TRY(gather_values(st, k, w.c.vals, w.c.order, sigma));
+  QDWHP_TRY(gather_columns(st, m, k, w.C, m, w.c.order, w.c.vals, U, ldu));
+  QDWHP_TRY(gather_columns(st, ell, k, w.Vj, ell, w.c.order, nullptr, w.W, ell));
+  QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, w.W, ell, 0.0, V, ldv));
+  inf.ms_total = timer.stop();
+  inf.retries = retries;
+  inf.ell = ell;
+  inf.k = k;
+  inf.s = s;
+  inf.alpha = alpha;
+  if (info) *info = inf;
+  return QDWHP_OK;
+}
+
+bool opts_valid(const qdwhp_opts& o) {
+  return o.s_eig > 0.0 && o.s_eig < 1.0 && o.iters_eig >= 1 && o.iters_eig <= kMaxSteps && o.tol > 0.0 &&
+         o.c_qr > 0.0 && o.block_extra >= 0 && o.power_steps >= 0 && o.power_steps <= 16 && o.lanczos_steps >= 1 &&
+         o.guard >= 0.0 && o.guard < 1.0 && o.max_retries >= 0 && o.jacobi_max_sweeps >= 1 &&
+         (o.side == QDWHP_LARGEST || o.side == QDWHP_SMALLEST) &&
+         o.precision == QDWHP_FP64;
+}
+
+}  // namespace
+}  // namespace qdwhp
+
+using namespace qdwhp;
+
+extern "C" {
+
+QDWHP_API void qdwhp_default_opts(qdwhp_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->count = 0;
+  o->fraction = 0.1;
+  o->side = QDWHP_LARGEST;
+  o->precision = QDWHP_FP64;
+  o->s_eig = 0.2;
+  o->iters_eig = 3;
+  o->lanczos_steps = 30;
+  o->tol = 0.01;
+  o->c_qr = 100.0;
+  o->block_extra = 16;
+  o->power_steps = 2;
+  o->guard = 0.05;
+  o->max_retries = 2;
+  o->jacobi_max_sweeps = 30;
+  o->seed = 1234;
+}
+
+QDWHP_API const char* qdwhp_status_string(qdwhp_status s) {
+  switch (s) {
+    case QDWHP_OK: return "ok";
+    case QDWHP_ERR_ARG: return "invalid argument";
+    case QDWHP_ERR_NOMEM: return "workspace too small";
+    case QDWHP_ERR_NOT_CONVERGED: return "reduced-problem Jacobi solver did not converge";
+    case QDWHP_ERR_BREAKDOWN: return "Cholesky breakdown (non-positive pivot)";
+    case QDWHP_ERR_NONFINITE: return "non-finite input or intermediate";
+    case QDWHP_ERR_TIMEOUT: return "bounded wait expired";
+    case QDWHP_ERR_CUDA: return "CUDA runtime error";
+    case QDWHP_ERR_QUEUE_FULL: return "request queue full";
+    case QDWHP_ERR_COUNT: return "fewer than k wanted pairs captured";
+    case QDWHP_PENDING: return "pending";
+  }
+  return "unknown status";
+}
+
+QDWHP_API const char* qdwhp_last_error_message(void) { return g_err; }
+
+QDWHP_API int64_t qdwhp_k_from_fraction(int64_t n, double fraction) {
+  if (n < 1 || !(fraction > 0.0)) return 0;
+  double kf = std::ceil(fraction * (double)n - 1e-9);
+  int64_t k = (int64_t)kf;
+  return std::max<int64_t>(1, std::min<int64_t>(n, k));
+}
+
+QDWHP_API size_t qdwhp_eig_workspace_bytes(int64_t n, const qdwhp_opts* opts) {
+  qdwhp_opts o;
+  if (opts) o = *opts; else qdwhp_default_opts(&o);
+  if (n < 1) return 0;
+  Arena ar;
+  ar.dry = true;
+  EigWs w;
+  carve_eig(ar, n, o, w);
+  return ar.used;
+}
+
+QDWHP_API qdwhp_status qdwhp_eig(const double* A, int64_t n, int64_t lda, const qdwhp_opts* opts, double* lambda,
+                                 double* V, int64_t ldv, void* workspace, size_t ws_bytes, qdwhp_info* info,
+                                 void* stream) {
+  if (!opts || !A || !lambda || !V || n < 1 || lda < n || ldv < n) return QDWHP_ERR_ARG;
+  if (!opts_valid(*opts)) return QDWHP_ERR_ARG;
+  if (n > (1 << 20)) return QDWHP_ERR_ARG;
+  if (!workspace || ws_bytes < qdwhp_eig_workspace_bytes(n, opts)) return QDWHP_ERR_NOMEM;
+  return eig_impl(A, n, lda, *opts, lambda, V, ldv, workspace, ws_bytes, info, (cudaStream_t)stream);
+}
+
+QDWHP_API size_t qdwhp_svd_workspace_bytes(int64_t m, int64_t n, const qdwhp_opts* opts) {
+  qdwhp_opts o;
+  if (opts) o = *opts; else qdwhp_default_opts(&o);
+  if (m < 1 || n < 1) return 0;
+  Arena ar;
+  ar.dry = true;
+  SvdWs w;
+  carve_svd(ar, std::max(m, n), std::min(m, n), o, w, m < n);
+  return ar.used;
+}
+
+QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t lda, int64_t k,
+                                 const qdwhp_opts* opts, double* sigma, double* U, int64_t ldu, double* V,
+                                 int64_t ldv, void* workspace, size_t ws_bytes, qdwhp_info* info, void* stream) {
+  if (!opts || !A || !sigma || !U || !V || m < 1 || n < 1 || lda < m || ldu < m || ldv < n) return QDWHP_ERR_ARG;
+  if (!opts_valid(*opts) || k < 0) return QDWHP_ERR_ARG;
+  const int64_t mm = std::max(m, n), nn = std::min(m, n);
+  const int64_t kk = resolve_k(nn, *opts, k);
+  if (kk < 1 || kk > nn) return QDWHP_ERR_ARG;
+  if (mm > (1 << 20)) return QDWHP_ERR_ARG;
+  if (!workspace || ws_bytes < qdwhp_svd_workspace_bytes(m, n, opts)) return QDWHP_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar{(char*)workspace, ws_bytes};
+  SvdWs w;
+  carve_svd(ar, mm, nn, *opts, w, m < n);
+  if (!ar.ok()) return QDWHP_ERR_NOMEM;
+  if (m >= n) return svd_impl(A, m, n, lda, kk, *opts, sigma, U, ldu, V, ldv, w, info, st);
+  // m < n: solve on A^T (n x m) and swap the roles of U and V (Section 4.2).
+  dim3 grid(ceil_div(m, 32), ceil_div(n, 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>((int)m, (int)n, A, lda, w.At, n);
+  QDWHP_LAUNCH_CHECK();
+  return svd_impl(w.At, n, m, n, kk, *opts, sigma, V, ldv, U, ldu, w, info, st);
+}
+
+}  // extern "C"

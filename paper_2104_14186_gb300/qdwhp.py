@@ -1,0 +1,269 @@
+"""Python binding of the qdwhp C ABI (include/qdwhp.h).
+
+Argument marshalling only: every step of a solve runs in libqdwhp.so's CUDA
+kernels.  PyTorch supplies device memory (inputs, outputs and the workspace the
+library asks for) and the current CUDA stream.  Matrices cross the boundary in
+column-major order: a logical torch matrix ``A`` is passed as the storage of
+``A.t().contiguous()``, and outputs are allocated transposed and returned as
+``.t()`` views.
+
+If the compiled library is missing the import of this module fails: there is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libqdwhp.so")
+
+QDWHP_OK = 0
+QDWHP_PENDING = 1
+STATUS_NAMES = {
+    0: "OK", -1: "ERR_ARG", -2: "ERR_NOMEM", -3: "ERR_NOT_CONVERGED", -4: "ERR_BREAKDOWN",
+    -5: "ERR_NONFINITE", -6: "ERR_TIMEOUT", -7: "ERR_CUDA", -8: "ERR_QUEUE_FULL", -9: "ERR_COUNT", 1: "PENDING",
+}
+LARGEST, SMALLEST = 0, 1
+FP64, MIXED = 0, 1
+
+
+class Opts(C.Structure):
+    _fields_ = [
+        ("count", C.c_int64), ("fraction", C.c_double), ("side", C.c_int32), ("precision", C.c_int32),
+        ("s_eig", C.c_double), ("iters_eig", C.c_int32), ("lanczos_steps", C.c_int32), ("tol", C.c_double),
+        ("c_qr", C.c_double), ("block_extra", C.c_int32), ("power_steps", C.c_int32), ("guard", C.c_double),
+        ("max_retries", C.c_int32), ("jacobi_max_sweeps", C.c_int32), ("seed", C.c_uint64),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("it_qr", C.c_int32), ("it_chol", C.c_int32), ("retries", C.c_int32), ("jacobi_sweeps", C.c_int32),
+        ("ell", C.c_int64), ("k", C.c_int64), ("t", C.c_double), ("mu", C.c_double), ("s", C.c_double),
+        ("alpha", C.c_double), ("ell_k", C.c_double * 12), ("conv", C.c_double * 12), ("ms_total", C.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("ell_k", "conv")}
+        n = self.it_qr + self.it_chol
+        d["ell_k"] = list(self.ell_k)[:n]
+        d["conv"] = list(self.conv)[:n]
+        return d
+
+
+class QdwhpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        if status == -7:
+            msg += " (" + lib().qdwhp_last_error_message().decode() + ")"
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+P = C.c_void_p
+I64 = C.c_int64
+D = C.c_double
+SIGNATURES = {
+    "qdwhp_default_opts": (None, [C.POINTER(Opts)]),
+    "qdwhp_status_string": (C.c_char_p, [C.c_int]),
+    "qdwhp_last_error_message": (C.c_char_p, []),
+    "qdwhp_k_from_fraction": (I64, [I64, D]),
+    "qdwhp_eig_workspace_bytes": (C.c_size_t, [I64, C.POINTER(Opts)]),
+    "qdwhp_eig": (C.c_int, [P, I64, I64, C.POINTER(Opts), P, P, I64, P, C.c_size_t, C.POINTER(Info), P]),
+    "qdwhp_svd_workspace_bytes": (C.c_size_t, [I64, I64, C.POINTER(Opts)]),
+    "qdwhp_svd": (C.c_int, [P, I64, I64, I64, I64, C.POINTER(Opts), P, P, I64, P, I64, P, C.c_size_t,
+                            C.POINTER(Info), P]),
+    "qdwhp_gemm_f64": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P]),
+    "qdwhp_potrf_workspace_bytes": (C.c_size_t, [I64]),
+    "qdwhp_potrf_f64": (C.c_int, [I64, P, I64, P, C.c_size_t, C.POINTER(C.c_int), P]),
+    "qdwhp_qr_workspace_bytes": (C.c_size_t, [I64, I64]),
+    "qdwhp_qr_f64": (C.c_int, [I64, I64, P, I64, P, I64, P, I64, P, C.c_size_t, P]),
+    "qdwhp_qdwh_workspace_bytes": (C.c_size_t, [I64, I64]),
+    "qdwhp_qdwh_steps_f64": (C.c_int, [I64, I64, P, I64, C.c_int32, C.POINTER(D), C.POINTER(C.c_int32),
+                                       C.POINTER(D), P, C.c_size_t, P]),
+}
+
+
+def lib():
+    """The loaded libqdwhp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2104_14186_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != QDWHP_OK:
+        raise QdwhpError(status, where)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _colmajor(A: torch.Tensor) -> torch.Tensor:
+    """Storage holding the logical matrix A in column-major order (ld = rows)."""
+    if A.dtype != torch.float64 or not A.is_cuda or A.dim() != 2:
+        raise ValueError("expected a 2-D float64 CUDA tensor")
+    return A.t().contiguous()
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().qdwhp_default_opts(C.byref(o))
+    side = kw.pop("side", None)
+    if side is not None:
+        o.side = SMALLEST if str(side).lower().startswith("s") else LARGEST
+    for key, val in kw.items():
+        if not hasattr(o, key):
+            raise TypeError(f"unknown option {key}")
+        setattr(o, key, val)
+    return o
+
+
+def k_from_fraction(n: int, fraction: float) -> int:
+    return int(lib().qdwhp_k_from_fraction(n, fraction))
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+@dataclass
+class EigResult:
+    lam: torch.Tensor      # (k,)
+    V: torch.Tensor        # (n, k)
+    info: dict
+
+
+@dataclass
+class SvdResult:
+    sigma: torch.Tensor    # (k,)
+    U: torch.Tensor        # (m, k)
+    V: torch.Tensor        # (n, k)
+    info: dict
+
+
+def eig(A: torch.Tensor, k: int | None = None, fraction: float | None = None, side: str = "largest",
+        ws: torch.Tensor | None = None, stream=None, **opts) -> EigResult:
+    """qdwhp_eig: k largest (or smallest) eigenpairs of the symmetric CUDA float64 matrix A."""
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("A must be square")
+    o = default_opts(side=side, **opts)
+    if k is not None:
+        o.count = int(k)
+    elif fraction is not None:
+        o.count = 0
+        o.fraction = float(fraction)
+    kk = int(o.count) if o.count > 0 else k_from_fraction(n, o.fraction)
+    Ac = _colmajor(A)
+    lam = torch.empty(max(kk, 1), dtype=torch.float64, device=A.device)
+    Vt = torch.empty(max(kk, 1), n, dtype=torch.float64, device=A.device)
+    need = lib().qdwhp_eig_workspace_bytes(n, C.byref(o))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    info = Info()
+    st = lib().qdwhp_eig(_ptr(Ac), n, n, C.byref(o), _ptr(lam), _ptr(Vt), n, _ptr(ws), ws.numel(), C.byref(info),
+                         _stream(stream))
+    _check(st, "qdwhp_eig")
+    return EigResult(lam[:kk], Vt[:kk].t(), info.as_dict())
+
+
+def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws: torch.Tensor | None = None,
+        stream=None, **opts) -> SvdResult:
+    """qdwhp_svd: k largest singular triplets of the CUDA float64 matrix A (m x n)."""
+    m, n = A.shape
+    o = default_opts(**opts)
+    kk = 0
+    if k is not None:
+        kk = int(k)
+    elif fraction is not None:
+        o.fraction = float(fraction)
+    kres = kk if kk > 0 else (int(o.count) if o.count > 0 else k_from_fraction(min(m, n), o.fraction))
+    Ac = _colmajor(A)
+    sigma = torch.empty(max(kres, 1), dtype=torch.float64, device=A.device)
+    Ut = torch.empty(max(kres, 1), m, dtype=torch.float64, device=A.device)
+    Vt = torch.empty(max(kres, 1), n, dtype=torch.float64, device=A.device)
+    need = lib().qdwhp_svd_workspace_bytes(m, n, C.byref(o))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    info = Info()
+    st = lib().qdwhp_svd(_ptr(Ac), m, n, m, kk, C.byref(o), _ptr(sigma), _ptr(Ut), m, _ptr(Vt), n, _ptr(ws),
+                         ws.numel(), C.byref(info), _stream(stream))
+    _check(st, "qdwhp_svd")
+    return SvdResult(sigma[:kres], Ut[:kres].t(), Vt[:kres].t(), info.as_dict())
+
+
+# ---- building blocks ----
+
+def gemm_f64(A: torch.Tensor, B: torch.Tensor, transa=False, transb=False, alpha=1.0, beta=0.0,
+             Cmat: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C through qdwhp_gemm_f64 (logical row-major tensors in/out)."""
+    Ac, Bc = _colmajor(A), _colmajor(B)
+    m = A.shape[1] if transa else A.shape[0]
+    k = A.shape[0] if transa else A.shape[1]
+    n = B.shape[0] if transb else B.shape[1]
+    Ct = (torch.zeros(n, m, dtype=torch.float64, device=A.device) if Cmat is None else _colmajor(Cmat))
+    st = lib().qdwhp_gemm_f64(int(transa), int(transb), m, n, k, alpha, _ptr(Ac), A.shape[0], _ptr(Bc), B.shape[0],
+                              beta, _ptr(Ct), m, _stream(stream))
+    _check(st, "qdwhp_gemm_f64")
+    return Ct.t()
+
+
+def potrf_f64(Z: torch.Tensor, stream=None):
+    """Lower Cholesky factor L (Z = L L^T) through qdwhp_potrf_f64; returns (L, info)."""
+    n = Z.shape[0]
+    Zc = _colmajor(Z)
+    ws = workspace(lib().qdwhp_potrf_workspace_bytes(n), Z.device)
+    info = C.c_int(0)
+    st = lib().qdwhp_potrf_f64(n, _ptr(Zc), n, _ptr(ws), ws.numel(), C.byref(info), _stream(stream))
+    if st not in (QDWHP_OK, -4):
+        _check(st, "qdwhp_potrf_f64")
+    return torch.tril(Zc.t()), info.value
+
+
+def qr_f64(A: torch.Tensor, stream=None):
+    """Householder QR A = Q R (m >= n) through qdwhp_qr_f64; returns (Q, R)."""
+    m, n = A.shape
+    Ac = _colmajor(A)
+    Qt = torch.empty(n, m, dtype=torch.float64, device=A.device)
+    Rt = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    ws = workspace(lib().qdwhp_qr_workspace_bytes(m, n), A.device)
+    st = lib().qdwhp_qr_f64(m, n, _ptr(Ac), m, _ptr(Qt), m, _ptr(Rt), n, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "qdwhp_qr_f64")
+    return Qt.t(), Rt.t()
+
+
+def qdwh_steps_f64(X: torch.Tensor, weights, use_qr, stream=None):
+    """Apply QDWH steps with the given (a, b, c) weights in place; returns (X_new, conv)."""
+    m, n = X.shape
+    Xc = _colmajor(X)
+    ns = len(weights)
+    abc = (C.c_double * (3 * max(ns, 1)))(*[float(v) for w in weights for v in w[:3]])
+    uq = (C.c_int32 * max(ns, 1))(*[int(u) for u in use_qr])
+    conv = (C.c_double * max(ns, 1))()
+    ws = workspace(lib().qdwhp_qdwh_workspace_bytes(m, n), X.device)
+    st = lib().qdwhp_qdwh_steps_f64(m, n, _ptr(Xc), m, ns, abc, uq, conv, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "qdwhp_qdwh_steps_f64")
+    return Xc.t(), [conv[i] for i in range(ns)]

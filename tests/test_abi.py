@@ -1,0 +1,96 @@
+"""The C-ABI library builds, loads and exports every symbol include/qdwhp.h declares;
+host-only entry points behave (no GPU needed)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp as Q
+    return Q.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qdwhp.h")).read()
+    return sorted(set(re.findall(r"QDWHP_API\s+[\w\s\*]+?\b(qdwhp_\w+)\s*\(", text)))
+
+
+def test_header_declares_solvers_and_blocks():
+    syms = declared_symbols()
+    for name in ("qdwhp_eig", "qdwhp_svd", "qdwhp_gemm_f64", "qdwhp_potrf_f64", "qdwhp_qr_f64",
+                 "qdwhp_qdwh_steps_f64", "qdwhp_default_opts"):
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_header(lib):
+    from paper_2104_14186_gb300 import qdwhp as Q
+    assert set(declared_symbols()) <= set(Q.SIGNATURES), set(declared_symbols()) - set(Q.SIGNATURES)
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_2104_14186_gb300 import qdwhp as Q
+    o = Q.default_opts()
+    assert o.s_eig == 0.2 and o.iters_eig == 3 and o.tol == 0.01 and o.c_qr == 100.0
+    assert o.lanczos_steps == 30 and o.block_extra == 16 and o.power_steps == 2 and o.seed == 1234
+    assert o.max_retries == 2 and o.jacobi_max_sweeps == 30 and o.side == Q.LARGEST
+
+
+def test_k_from_fraction(lib):
+    from paper_2104_14186_gb300 import inputs as I
+    from paper_2104_14186_gb300 import qdwhp as Q
+    for n, f in [(512, 0.10), (4096, 0.05), (16384, 0.01), (16384, 0.20), (10, 0.01), (7, 1.0)]:
+        assert Q.k_from_fraction(n, f) == I.k_from_fraction(n, f)
+    assert Q.k_from_fraction(512, 0.10) == 52
+    assert Q.k_from_fraction(4096, 0.05) == 205
+    assert Q.k_from_fraction(0, 0.1) == 0
+
+
+def test_workspace_sizes_grow(lib):
+    from paper_2104_14186_gb300 import qdwhp as Q
+    o = Q.default_opts()
+    a = lib.qdwhp_eig_workspace_bytes(512, C.byref(o))
+    b = lib.qdwhp_eig_workspace_bytes(1024, C.byref(o))
+    assert 0 < a < b
+    assert lib.qdwhp_svd_workspace_bytes(300, 200, C.byref(o)) > 0
+    # wide problems are solved transposed and need room for A^T
+    assert lib.qdwhp_svd_workspace_bytes(200, 300, C.byref(o)) > lib.qdwhp_svd_workspace_bytes(300, 200, C.byref(o))
+
+
+def test_argument_errors_return_before_any_launch(lib):
+    from paper_2104_14186_gb300 import qdwhp as Q
+    o = Q.default_opts()
+    info = Q.Info()
+    fake = C.c_void_p(0x1000)
+    # null A, n < 1, k > n, bad options: ERR_ARG without touching the device
+    assert lib.qdwhp_eig(None, 10, 10, C.byref(o), fake, fake, 10, fake, 1 << 30, C.byref(info), None) == -1
+    assert lib.qdwhp_eig(fake, 0, 10, C.byref(o), fake, fake, 10, fake, 1 << 30, C.byref(info), None) == -1
+    o2 = Q.default_opts(count=11)
+    assert lib.qdwhp_eig(fake, 10, 10, C.byref(o2), fake, fake, 10, fake, 1 << 30, C.byref(info), None) == -1
+    o3 = Q.default_opts(s_eig=1.5)
+    assert lib.qdwhp_eig(fake, 10, 10, C.byref(o3), fake, fake, 10, fake, 1 << 30, C.byref(info), None) == -1
+    o4 = Q.default_opts(precision=Q.MIXED + 5)
+    assert lib.qdwhp_eig(fake, 10, 10, C.byref(o4), fake, fake, 10, fake, 1 << 30, C.byref(info), None) == -1
+    # workspace too small: ERR_NOMEM
+    assert lib.qdwhp_eig(fake, 10, 10, C.byref(o), fake, fake, 10, fake, 16, C.byref(info), None) == -2
+    assert lib.qdwhp_svd(fake, 10, 8, 10, 20, C.byref(o), fake, fake, 10, fake, 8, fake, 1 << 30,
+                         C.byref(info), None) == -1
+    assert lib.qdwhp_gemm_f64(0, 0, 4, 4, 4, 1.0, fake, 2, fake, 4, 0.0, fake, 4, None) == -1
+    assert lib.qdwhp_qr_f64(3, 4, fake, 3, fake, 3, fake, 4, fake, 1 << 20, None) == -1
+
+
+def test_status_strings(lib):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9, 1):
+        assert lib.qdwhp_status_string(s)

@@ -1,0 +1,130 @@
+"""GPU parity of qdwhp_eig / qdwhp_svd (through the C ABI) against the FP64 oracle and
+the constructed spectra, at the plain-FP64 tolerances:
+    |lambda - lambda*| <= 1e-12 ||A||_2,  ||V^T V - I||_F <= 5e-15 n,
+    ||A V - V Lambda||_F / ||A||_F <= 1e-13  (and the SVD analogues)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2104_14186_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+LAM_TOL = 1e-12
+ORTH_TOL = 5e-15
+RES_TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def Q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp
+    return qdwhp
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def check_eig(p, r, ref=None):
+    n = p.A.shape[0]
+    lam, V = r.lam.cpu().numpy(), r.V.cpu().numpy()
+    true = np.sort(p.lam)[::-1][: p.k] if p.side == "largest" else np.sort(p.lam)[: p.k]
+    m = O.eig_metrics(p.A, lam, V, true)
+    assert lam.shape == (p.k,) and V.shape == (n, p.k)
+    assert m["lam_err"] <= LAM_TOL, m
+    assert m["orth"] <= ORTH_TOL * n, m
+    assert m["resid"] <= RES_TOL, m
+    if ref is not None:
+        assert np.max(np.abs(lam - ref.lam)) <= LAM_TOL * np.max(np.abs(p.lam))
+        # same invariant subspace as the oracle (eigenvectors are unique up to sign here)
+        assert np.linalg.norm(np.abs(V.T @ ref.V) - np.eye(p.k), 2) <= 1e-9
+    return m
+
+
+@pytest.mark.parametrize("n,frac,side,seed", [
+    (512, 0.10, "largest", 1000),      # the EIG workload: n = 512, 10 % largest
+    (512, 0.10, "smallest", 1001),
+    (700, 0.02, "largest", 5),         # ragged size (not a multiple of any tile)
+    (333, 0.30, "smallest", 6),
+    (96, 0.05, "largest", 7),
+])
+def test_eig_vs_oracle(Q, n, frac, side, seed):
+    p = I.eig_uniform(n, seed, frac, side)
+    r = Q.eig(dev(p.A), k=p.k, side=side)
+    ref = O.qdwhp_eig(p.A, O.EigOptions(k=p.k, side=side))
+    check_eig(p, r, ref)
+    assert r.info["ell"] >= p.k and r.info["it_chol"] == 3
+
+
+def test_eig_single_pair_and_fraction(Q):
+    p = I.eig_uniform(257, 12, 0.0, "largest")
+    p.k = 1
+    r = Q.eig(dev(p.A), k=1)
+    check_eig(p, r)
+    p2 = I.eig_uniform(257, 13, 0.07, "smallest")
+    r2 = Q.eig(dev(p2.A), fraction=0.07, side="smallest")
+    assert r2.lam.shape[0] == p2.k
+    check_eig(p2, r2)
+
+
+def test_eig_repeatable(Q):
+    p = I.eig_uniform(300, 21, 0.1, "largest")
+    A = dev(p.A)
+    r1 = Q.eig(A, k=p.k)
+    r2 = Q.eig(A, k=p.k)
+    assert torch.equal(r1.lam, r2.lam) and torch.equal(r1.V, r2.V)
+
+
+def check_svd(q, r, ref=None):
+    m_, n_ = q.A.shape
+    sig, U, V = r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy()
+    mt = O.svd_metrics(q.A, sig, U, V, q.sigma[: q.k])
+    assert sig.shape == (q.k,) and U.shape == (m_, q.k) and V.shape == (n_, q.k)
+    assert mt["sigma_err"] <= LAM_TOL, mt
+    assert mt["orthU"] <= ORTH_TOL * max(m_, n_) and mt["orthV"] <= ORTH_TOL * max(m_, n_), mt
+    assert mt["residV"] <= RES_TOL and mt["residU"] <= RES_TOL, mt
+    if ref is not None:
+        assert np.max(np.abs(sig - ref.sigma)) <= LAM_TOL * q.sigma[0]
+    return mt
+
+
+@pytest.mark.parametrize("m,n,frac,seed", [(700, 500, 0.05, 2000), (512, 512, 0.10, 2001), (401, 257, 0.2, 3)])
+def test_svd_vs_oracle(Q, m, n, frac, seed):
+    q = I.svd_logspaced(m, n, seed, frac)
+    r = Q.svd(dev(q.A), k=q.k)
+    ref = O.qdwhp_svd(q.A, O.SvdOptions(k=q.k))
+    check_svd(q, r, ref)
+
+
+def test_svd_wide(Q):
+    q = I.svd_logspaced(300, 240, 31, 0.1)
+    At = np.asfortranarray(q.A.T)
+    r = Q.svd(dev(At), k=q.k)
+    sig, U, V = r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy()
+    assert U.shape == (240, q.k) and V.shape == (300, q.k)
+    mt = O.svd_metrics(At, sig, U, V, q.sigma[: q.k])
+    assert mt["sigma_err"] <= LAM_TOL and mt["residV"] <= RES_TOL and mt["residU"] <= RES_TOL
+
+
+def test_svd_small_threshold_takes_qr_step(Q):
+    """k deep into a log-spaced spectrum puts s near 1e-4: the first QDWH step is QR-based."""
+    q = I.svd_logspaced(360, 300, 77, 0.35, decades=12.0)
+    r = Q.svd(dev(q.A), k=q.k)
+    assert r.info["it_qr"] >= 1
+    check_svd(q, r)
+
+
+def test_nonfinite_input_is_reported(Q):
+    p = I.eig_uniform(64, 1, 0.1)
+    A = p.A.copy()
+    A[3, 5] = np.nan
+    with pytest.raises(Q.QdwhpError) as e:
+        Q.eig(dev(A), k=3)
+    assert e.value.status == -5
