@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Throughput of QDWHpartial-SVD on one GB300 (and replicas on N GPUs).
+
+Workload (one step = one full solve): A = U diag(sigma) V^T, 4096 x 4096, FP64,
+Haar U and V, sigma_i = 10^(-12 i / 4095); the 5 % largest singular triplets
+(k = 205).  Every step runs the whole hot path: Lanczos norm estimate,
+count-to-threshold subspace, QDWH iterations, extraction QR, index rule, Q2,
+A Q2 and its SVD, back-transform.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle on the host cores (the method's
+plain CPU implementation, test infrastructure) on the same workload.
+For N > 1 (launched by torchrun) every rank solves its own independent problem
+(replicas, no collective on the data path); the value is all ranks' solves over
+the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "partial EIG/SVD solves/sec and TFLOP/s vs FP64/TF32 peak; p50/p99 latency, mixed vs FP64"
+UNIT = "solves/s"
+M = N = 4096
+FRACTION = 0.05
+SEED = 2000
+L2_FLUSH_BYTES = 256 << 20
+
+# Roofline denominator for FP64 DMMA: no FP64 figure is in the measured-peaks file, so it is the
+# measured BF16 dense burst peak times the nominal FP64 / BF16 ratio (1.25 TFLOP/s / 2250 TFLOP/s).
+NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
+
+
+def workload_config(k):
+    return {"workload": f"QDWHpartial-SVD {M}x{N} FP64, sigma log-spaced 1..1e-12, top 5% (k={k})",
+            "m": M, "n": N, "k": k, "seed": SEED,
+            "l2": "L2 flushed (256 MB write) between timed steps; A alone is 134 MB > L2"}
+
+
+def svd_flops(m, n, ell, k, it_qr, it_chol):
+    """Algorithmic flops of one solve: QDWH steps (Cholesky: 3mn^2 + n^3/3; QR: 2(2(m+n)n^2 - 2n^3/3) + 2mn^2),
+    I - X^T X (mn^2), Householder QR (4/3 n^3), Q2 (2 n^2 ell), A Q2 (2 m n ell), reduced SVD (4 m ell^2 +
+    17 ell^3) and V = Q2 V~ (2 n ell k)."""
+    f = it_chol * (3.0 * m * n * n + n ** 3 / 3.0)
+    f += it_qr * (2.0 * (2.0 * (m + n) * n * n - 2.0 * n ** 3 / 3.0) + 2.0 * m * n * n)
+    f += m * n * n + 4.0 / 3.0 * n ** 3 + 2.0 * n * n * ell + 2.0 * m * n * ell + 4.0 * m * ell ** 2
+    f += 17.0 * ell ** 3 + 2.0 * n * ell * k
+    return f
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = []
+        smax = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_problem(seed):
+    from paper_2104_14186_gb300 import inputs as I
+    return I.svd_logspaced(M, N, seed, FRACTION)
+
+
+def oracle_solve(A, k):
+    import oracle as O
+    return O.qdwhp_svd(A, O.SvdOptions(k=k))
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    p = make_problem(SEED)
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_solve(p.A, p.k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_solve(p.A, p.k)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(p.k),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full solves of the {M}x{N} workload (numpy/LAPACK FP64 oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp as Q
+
+    p = make_problem(SEED + rank)
+    A_host = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()
+    A = A_host.to(dev)
+    k = p.k
+    o = Q.default_opts()
+    ws = Q.workspace(Q.lib().qdwhp_svd_workspace_bytes(M, N, __import__("ctypes").byref(o)), dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        r = Q.svd(A, k=k, ws=ws)
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM ----
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = Q.launch_count()
+    Q.profile_begin()
+    infos = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        r = Q.svd(A, k=k, ws=ws)
+        ev[i][1].record(stream)
+        infos.append(r.info)
+    torch.cuda.synchronize()
+    barrier()
+    prof = Q.profile_end()
+    launches = Q.launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the host-buffer API (H2D of A and D2H of sigma, U, V in the region) ----
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        rh = Q.svd(A_host, k=k, ws=ws, device=dev)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = A_host.numel() * 8
+    d2h = (rh.sigma.numel() + rh.U.numel() + rh.V.numel()) * 8
+
+    info = infos[-1]
+    fl = svd_flops(M, N, info["ell"], k, info["it_qr"], info["it_chol"])
+    peaks = load_peaks()
+    bf16 = peaks.get("bf16_tflops")
+    peak = bf16 * NOMINAL_FP64_OVER_BF16 if bf16 else 1.9e3 * NOMINAL_FP64_OVER_BF16
+    achieved = prof["gemm_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(k),
+        "tflops": fl / (total_ms / args.steps / 1e3) / 1e12,
+        "tflops_frac_of_fp64_peak": fl / (total_ms / args.steps / 1e3) / 1e12 / peak,
+        "solve": {"ell": info["ell"], "it_qr": info["it_qr"], "it_chol": info["it_chol"], "s": info["s"],
+                  "alpha": info["alpha"], "jacobi_sweeps": info["jacobi_sweeps"], "alg_flops": fl,
+                  "step_ms": step_ms},
+        "roofline": {
+            "kernel": "dgemm_kernel (FP64 DMMA mma.sync m8n8k4 tiles, all GEMM/SYRK/TRSM/QR-update launches)",
+            "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": "measured bf16 dense burst x nominal FP64/BF16 ratio (1.25/2250), of measured",
+            "gemm_share_of_step": prof["gemm_ms"] / total_ms if total_ms > 0 else None,
+            "gemm_launches": prof["gemm_launches"],
+        },
+        "e2e": {"value": world * args.steps / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        oracle_solve(p.A, k)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"1 full solve of the {M}x{N} workload (numpy/LAPACK FP64 oracle)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,20 @@ QDWHP_API qdwhp_status qdwhp_qdwh_steps_f64(int64_t m, int64_t n, double* X, int
                                             double* conv_host, void* workspace, size_t ws_bytes,
                                             void* stream);
 
+/* ---- Instrumentation (not part of the method) ---- */
+
+/* Kernels launched by this library since it was loaded (all threads). */
+QDWHP_API unsigned long long qdwhp_launch_count(void);
+/*
+ * Opt-in timing of the FP64 GEMM launches: between qdwhp_profile_begin() and
+ * qdwhp_profile_end(), every GEMM the library launches is bracketed by CUDA events on
+ * its stream; qdwhp_profile_end() waits for them and returns the summed device time
+ * (ms), the summed algorithmic flops (2mnk, or n(n+1)k for a lower-triangular
+ * product) and the number of GEMMs.  Process-wide; use from one host thread.
+ */
+QDWHP_API qdwhp_status qdwhp_profile_begin(void);
+QDWHP_API qdwhp_status qdwhp_profile_end(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches);
+
 #ifdef __cplusplus
 }
 #endif

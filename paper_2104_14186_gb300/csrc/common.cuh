@@ -29,9 +29,22 @@ constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs (queried at run 
     if (_s != QDWHP_OK) return _s;             \
   } while (0)
 
-#define QDWHP_LAUNCH_CHECK() QDWHP_CUDA_TRY(cudaGetLastError())
+// Every kernel launch is followed by exactly one QDWHP_LAUNCH_CHECK(), which also
+// counts it (qdwhp_launch_count()).
+#define QDWHP_LAUNCH_CHECK()                 \
+  do {                                       \
+    ::qdwhp::note_launch();                  \
+    QDWHP_CUDA_TRY(cudaGetLastError());      \
+  } while (0)
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+void note_launch();
+
+// Opt-in timing of the DMMA GEMM launches (CUDA events around each launch on its stream).
+bool gemm_prof_enabled();
+// Records the start event; returns a slot id for gemm_prof_end (or -1 when disabled).
+int gemm_prof_start(cudaStream_t st, double flops);
+void gemm_prof_stop(cudaStream_t st, int slot);
 
 // Device-side error flags written by kernels (bitwise OR into ws->flags).
 enum DeviceFlag : unsigned {

@@ -202,6 +202,9 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   if (split > 1) split = (K + kchunk - 1) / kchunk;
   dim3 grid(ceil_div(M, BM), ceil_div(N, BN), split);
   double* partial = split > 1 ? splitk_ws : nullptr;
+  // algorithmic flops: 2 m n k, or n (n + 1) k for the lower triangle only
+  const double flops = (uplo == LOWER) ? (double)N * (N + 1) * K : 2.0 * M * N * K;
+  const int prof_slot = gemm_prof_enabled() ? gemm_prof_start(st, flops) : -1;
   if (big)
     launch<64, 64>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
   else
@@ -212,6 +215,7 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
     splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, split, partial, alpha, beta, C, ldc, uplo, diag_add);
     QDWHP_LAUNCH_CHECK();
   }
+  if (prof_slot >= 0) gemm_prof_stop(st, prof_slot);
   return QDWHP_OK;
 }
 

@@ -174,8 +174,8 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     QDWHP_CUDA_TRY(cudaMemsetAsync(jst_dev, 0, sizeof(JacobiState), st));
     for (int r = 0; r < N - 1; ++r) {
       jacobi_round_kernel<<<N / 2, 256, 0, st>>>((int)mg, (int)nc, N, r, G, ldg, Vj, ldv, tol, jst_dev);
+      QDWHP_LAUNCH_CHECK();
     }
-    QDWHP_LAUNCH_CHECK();
     QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
     QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
     *sweeps_out = sweep + 1;

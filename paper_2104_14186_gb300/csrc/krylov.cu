@@ -249,9 +249,13 @@ qdwhp_status lanczos(cudaStream_t st, bool normal, int64_t m, int64_t n, const d
       QDWHP_TRY(gemv_t(st, n, n, A, lda, qj, w));         // symmetric: A q = A^T q
     }
     dots_t_kernel<<<j + 1, 256, 0, st>>>((int)n, Q, n, w, h0);
+    QDWHP_LAUNCH_CHECK();
     sub_qh_kernel<<<rows_blocks, 256, 0, st>>>((int)n, j + 1, Q, n, h0, w);
+    QDWHP_LAUNCH_CHECK();
     dots_t_kernel<<<j + 1, 256, 0, st>>>((int)n, Q, n, w, h1);
+    QDWHP_LAUNCH_CHECK();
     sub_qh_kernel<<<rows_blocks, 256, 0, st>>>((int)n, j + 1, Q, n, h1, w);
+    QDWHP_LAUNCH_CHECK();
     lanczos_finish_kernel<<<1, 1024, 0, st>>>((int)n, j, steps, h0, w, Q + (size_t)(j + 1) * n * (j + 1 < steps),
                                                stt);
     QDWHP_LAUNCH_CHECK();

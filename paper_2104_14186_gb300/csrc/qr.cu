@@ -3,7 +3,7 @@
 // Used for the extraction step (Algorithm 1 step 3, Algorithm 2 step 3), the
 // QR-based QDWH step (eq. practical-polar-qr) and the orthonormalisation of the
 // count-to-threshold subspace.  Reflectors follow the LAPACK convention
-// H = I - tau v v^T with v_1 = 1, and each kCholNB-wide... (kQRNB-wide) panel is
+// H = I - tau v v^T with v_1 = 1, and each kQRNB-wide panel is
 // accumulated into the compact WY form Q_p = I - V T V^T (T upper triangular).
 //
 // One SM does only a few FP64 flops per clock on this part, so a panel factored by
@@ -225,6 +225,7 @@ qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
   if (smem > 160 * 1024) return QDWHP_ERR_ARG;
   void* args[] = {&pa};
   QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, st));
+  QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }
 

@@ -88,6 +88,9 @@ SIGNATURES = {
     "qdwhp_qdwh_workspace_bytes": (C.c_size_t, [I64, I64]),
     "qdwhp_qdwh_steps_f64": (C.c_int, [I64, I64, P, I64, C.c_int32, C.POINTER(D), C.POINTER(C.c_int32),
                                        C.POINTER(D), P, C.c_size_t, P]),
+    "qdwhp_launch_count": (C.c_ulonglong, []),
+    "qdwhp_profile_begin": (C.c_int, []),
+    "qdwhp_profile_end": (C.c_int, [C.POINTER(D), C.POINTER(D), C.POINTER(I64)]),
 }
 
 
@@ -191,8 +194,25 @@ def eig(A: torch.Tensor, k: int | None = None, fraction: float | None = None, si
 
 
 def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws: torch.Tensor | None = None,
-        stream=None, **opts) -> SvdResult:
-    """qdwhp_svd: k largest singular triplets of the CUDA float64 matrix A (m x n)."""
+        stream=None, device=None, **opts) -> SvdResult:
+    """qdwhp_svd: k largest singular triplets of the float64 matrix A (m x n).
+
+    A CUDA tensor is solved in place on its device.  A host tensor (pinned for
+    asynchronous copies) is copied to `device` (default cuda:0) on the stream, solved,
+    and sigma, U and V are copied back into host tensors before returning.
+    """
+    host_in = not A.is_cuda
+    if host_in:
+        dev = torch.device(device or "cuda")
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        with torch.cuda.stream(st):
+            Ad = A.to(dev, non_blocking=True)
+            r = svd(Ad, k=k, fraction=fraction, ws=ws, stream=st, **opts)
+            out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (r.sigma, r.U, r.V)]
+            for o_, t in zip(out, (r.sigma, r.U, r.V)):
+                o_.copy_(t, non_blocking=True)
+        st.synchronize()
+        return SvdResult(out[0], out[1], out[2], r.info)
     m, n = A.shape
     o = default_opts(**opts)
     kk = 0
@@ -201,18 +221,41 @@ def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws
     elif fraction is not None:
         o.fraction = float(fraction)
     kres = kk if kk > 0 else (int(o.count) if o.count > 0 else k_from_fraction(min(m, n), o.fraction))
-    Ac = _colmajor(A)
-    sigma = torch.empty(max(kres, 1), dtype=torch.float64, device=A.device)
-    Ut = torch.empty(max(kres, 1), m, dtype=torch.float64, device=A.device)
-    Vt = torch.empty(max(kres, 1), n, dtype=torch.float64, device=A.device)
-    need = lib().qdwhp_svd_workspace_bytes(m, n, C.byref(o))
-    if ws is None or ws.numel() < need:
-        ws = workspace(need, A.device)
-    info = Info()
-    st = lib().qdwhp_svd(_ptr(Ac), m, n, m, kk, C.byref(o), _ptr(sigma), _ptr(Ut), m, _ptr(Vt), n, _ptr(ws),
-                         ws.numel(), C.byref(info), _stream(stream))
+    with torch.cuda.stream(stream) if stream is not None else _nullctx():
+        Ac = _colmajor(A)
+        sigma = torch.empty(max(kres, 1), dtype=torch.float64, device=A.device)
+        Ut = torch.empty(max(kres, 1), m, dtype=torch.float64, device=A.device)
+        Vt = torch.empty(max(kres, 1), n, dtype=torch.float64, device=A.device)
+        need = lib().qdwhp_svd_workspace_bytes(m, n, C.byref(o))
+        if ws is None or ws.numel() < need:
+            ws = workspace(need, A.device)
+        info = Info()
+        st = lib().qdwhp_svd(_ptr(Ac), m, n, m, kk, C.byref(o), _ptr(sigma), _ptr(Ut), m, _ptr(Vt), n, _ptr(ws),
+                             ws.numel(), C.byref(info), _stream(stream))
     _check(st, "qdwhp_svd")
     return SvdResult(sigma[:kres], Ut[:kres].t(), Vt[:kres].t(), info.as_dict())
+
+
+class _nullctx:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def launch_count() -> int:
+    return int(lib().qdwhp_launch_count())
+
+
+def profile_begin():
+    _check(lib().qdwhp_profile_begin(), "qdwhp_profile_begin")
+
+
+def profile_end() -> dict:
+    ms, fl, n = D(0.0), D(0.0), I64(0)
+    _check(lib().qdwhp_profile_end(C.byref(ms), C.byref(fl), C.byref(n)), "qdwhp_profile_end")
+    return {"gemm_ms": ms.value, "gemm_flops": fl.value, "gemm_launches": n.value}
 
 
 # ---- building blocks ----
