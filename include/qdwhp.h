@@ -171,6 +171,26 @@ QDWHP_API qdwhp_status qdwhp_qdwh_steps_f64(int64_t m, int64_t n, double* X, int
                                             double* conv_host, void* workspace, size_t ws_bytes,
                                             void* stream);
 
+/*
+ * Cholesky factorisation with no workspace argument; it allocates no memory.
+ * The paper has no counterpart: this is a convenience for callers that cannot give
+ * the library device scratch, e.g. a program whose device memory belongs to another
+ * allocator (a framework's caching pool, a server's fixed memory plan) and must not
+ * call cudaMalloc behind its back, or code that cannot afford the device-wide
+ * synchronisation a cudaMalloc/cudaFree may cause.
+ *   Same result as qdwhp_potrf_f64 (same arguments minus the workspace).
+ *   n <= QDWHP_POTRF_NOALLOC_MAX_N, else QDWHP_ERR_ARG with a message in
+ *   qdwhp_last_error_message() and nothing launched.
+ *   Scratch: a 4 MB array in the library's own device memory, held by every GPU that
+ *   loads the library until the process exits.  The first call on a device looks up
+ *   that array's device address (with the device current); make that first call
+ *   before any stream capture.  All calls share the one array, so calls that
+ *   overlap on the GPU (other streams, other host threads) race: serialise them.
+ *   Synchronises `stream` to read the result flag.
+ */
+#define QDWHP_POTRF_NOALLOC_MAX_N 4096
+QDWHP_API qdwhp_status qdwhp_potrf_f64_noalloc(int64_t n, double* Z, int64_t ldz, int* info_host, void* stream);
+
 /* ---- Instrumentation (not part of the method) ---- */
 
 /* Kernels launched by this library since it was loaded (all threads). */

@@ -38,6 +38,8 @@ constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs (queried at run 
   } while (0)
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+// Sets the text returned by qdwhp_last_error_message() for a non-CUDA error.
+void set_error_message(const char* msg);
 void note_launch();
 
 // Opt-in timing of the DMMA GEMM launches (CUDA events around each launch on its stream).

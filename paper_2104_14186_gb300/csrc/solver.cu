@@ -32,6 +32,8 @@ void set_last_error(cudaError_t e, const char* what, const char* file, int line)
            cudaGetErrorString(e));
 }
 
+void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 namespace {
 
 __global__ void index_scan_kernel(int n, const double* diagR, double tol, int* ind) {

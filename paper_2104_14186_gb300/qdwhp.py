@@ -88,6 +88,7 @@ SIGNATURES = {
     "qdwhp_qdwh_workspace_bytes": (C.c_size_t, [I64, I64]),
     "qdwhp_qdwh_steps_f64": (C.c_int, [I64, I64, P, I64, C.c_int32, C.POINTER(D), C.POINTER(C.c_int32),
                                        C.POINTER(D), P, C.c_size_t, P]),
+    "qdwhp_potrf_f64_noalloc": (C.c_int, [I64, P, I64, C.POINTER(C.c_int), P]),
     "qdwhp_launch_count": (C.c_ulonglong, []),
     "qdwhp_profile_begin": (C.c_int, []),
     "qdwhp_profile_end": (C.c_int, [C.POINTER(D), C.POINTER(D), C.POINTER(I64)]),
