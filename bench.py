@@ -288,6 +288,48 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel_gemm(args):
+    """Isolated DMMA GEMM C = A B (4096^3, FP64) through qdwhp_gemm_f64, one launch per step."""
+    import torch
+
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp as Q
+
+    n = 4096
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+    Cm = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    lib = Q.lib()
+
+    def step():
+        rc = lib.qdwhp_gemm_f64(0, 0, n, n, n, 1.0, A.data_ptr(), n, B.data_ptr(), n, 0.0, Cm.data_ptr(), n,
+                                st.cuda_stream)
+        assert rc == 0
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    peaks = load_peaks()
+    peak = peaks.get("bf16_tflops", 1.9e3) * NOMINAL_FP64_OVER_BF16
+    tf = 2.0 * n ** 3 / (statistics.median(ms) / 1e3) / 1e12
+    print(json.dumps({"kernel": "dgemm_kernel<64,64,N,N> via qdwhp_gemm_f64", "m": n, "n": n, "k": n,
+                      "ms_median": statistics.median(ms), "tflops": tf, "peak": peak, "frac": tf / peak,
+                      "alg_bytes": 3 * n * n * 8}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -295,7 +337,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["gemm"], default=None,
+                    help="time one building block in isolation instead of the full solve")
     args = ap.parse_args()
+    if args.kernel == "gemm":
+        run_kernel_gemm(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
