@@ -330,6 +330,24 @@ def run_kernel_gemm(args):
                       "alg_bytes": 3 * n * n * 8}), flush=True)
 
 
+def run_single(args):
+    """One untimed solve of the workload: the command the ncu launch-list capture runs."""
+    import numpy as np
+    import torch
+
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp as Q
+
+    p = make_problem(SEED)
+    A = torch.from_numpy(np.ascontiguousarray(p.A)).cuda()
+    launches0 = Q.launch_count()
+    r = Q.svd(A, k=p.k)
+    torch.cuda.synchronize()
+    print(json.dumps({"single_solve": True, "launches": Q.launch_count() - launches0, "ell": r.info["ell"],
+                      "ms": r.info["ms_total"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,7 +357,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["gemm"], default=None,
                     help="time one building block in isolation instead of the full solve")
+    ap.add_argument("--single", action="store_true", help="one untimed solve (for profiler launch lists)")
     args = ap.parse_args()
+    if args.single:
+        run_single(args)
+        return
     if args.kernel == "gemm":
         run_kernel_gemm(args)
         return

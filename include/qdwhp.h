@@ -204,6 +204,9 @@ QDWHP_API unsigned long long qdwhp_launch_count(void);
  */
 QDWHP_API qdwhp_status qdwhp_profile_begin(void);
 QDWHP_API qdwhp_status qdwhp_profile_end(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches);
+/* Per-GEMM records of the last profile: 6 doubles each (m, n, k, lower-triangle flag,
+ * split-K slices, ms), up to `capacity` records into `out` (host); returns the count. */
+QDWHP_API int64_t qdwhp_profile_records(double* out, int64_t capacity);
 
 #ifdef __cplusplus
 }

@@ -16,14 +16,22 @@ namespace {
 constexpr int NB = kCholNB;
 
 // One diagonal leaf: Z (nb x nb, lower) -> L with Z = L L^T, plus inv(L) (lower) into Linv (ld NB).
+// Right-looking in shared memory; each pivot's reciprocal is formed once so the column
+// scaling and the inverse use multiplies.  inv(L) is formed by the same right-looking
+// substitution applied to all columns of the identity at once (parallel over entries).
+constexpr size_t kLeafSmem = 2 * sizeof(double) * NB * (NB + 1) + sizeof(double) * NB;
+
 __global__ void __launch_bounds__(256) potrf_leaf_kernel(int nb, double* Z, int64_t ldz, double* Linv, int* fail,
                                                          int col_offset) {
-  __shared__ double a[NB][NB + 1];
+  extern __shared__ double sm[];
+  double (*a)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(sm);
+  double (*x)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(sm + NB * (NB + 1));
+  double* dinv = sm + 2 * NB * (NB + 1);
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     const int i = e % NB, j = e / NB;
     a[i][j] = (i < nb && j < nb && i >= j) ? Z[i + (int64_t)j * ldz] : 0.0;
-    Linv[e] = 0.0;   // e = i + j * NB
+    x[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
@@ -33,11 +41,13 @@ __global__ void __launch_bounds__(256) potrf_leaf_kernel(int nb, double* Z, int6
         atomicCAS(fail, 0, col_offset + j + 1);
         d = 1.0;
       }
-      a[j][j] = sqrt(d);
+      const double piv = sqrt(d);
+      a[j][j] = piv;
+      dinv[j] = 1.0 / piv;
     }
     __syncthreads();
-    const double piv = a[j][j];
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] /= piv;
+    const double r = dinv[j];
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] *= r;
     __syncthreads();
     const int rem = nb - j - 1;
     for (int e = tid; e < rem * rem; e += blockDim.x) {
@@ -50,17 +60,21 @@ __global__ void __launch_bounds__(256) potrf_leaf_kernel(int nb, double* Z, int6
     const int i = e % nb, j = e / nb;
     if (i >= j) Z[i + (int64_t)j * ldz] = a[i][j];
   }
-  __syncthreads();
-  // inv(L) (lower): column c by forward substitution, one thread per column; each thread
-  // reads back only the entries of its own column it has written.
-  if (tid < nb) {
-    const int c = tid;
-    double* xc = Linv + (int64_t)c * NB;
-    for (int i = c; i < nb; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int j = c; j < i; ++j) s -= a[i][j] * xc[j];
-      xc[i] = s / a[i][i];
+  // Solve L X = I: for each j, row j of X is scaled by 1/L_jj, then eliminated from rows below.
+  for (int j = 0; j < nb; ++j) {
+    const double r = dinv[j];
+    for (int c = tid; c <= j; c += blockDim.x) x[j][c] *= r;
+    __syncthreads();
+    const int rem = nb - j - 1;
+    for (int e = tid; e < rem * (j + 1); e += blockDim.x) {
+      const int i = j + 1 + e % rem, c = e / rem;
+      x[i][c] -= a[i][j] * x[j][c];
     }
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int i = e % NB, j = e / NB;
+    Linv[i + (int64_t)j * NB] = (i < nb && j < nb) ? x[i][j] : 0.0;
   }
 }
 
@@ -97,7 +111,12 @@ qdwhp_status trsm_rec(cudaStream_t st, bool trans, int64_t m, int64_t n, double*
 qdwhp_status potrf_rec(cudaStream_t st, int64_t n, double* Z, int64_t ldz, double* Linv, double* scratch,
                        int* fail, int64_t off) {
   if (n <= NB) {
-    potrf_leaf_kernel<<<1, 256, 0, st>>>((int)n, Z, ldz, Linv, fail, (int)off);
+    static bool attr_set = false;
+    if (!attr_set) {
+      QDWHP_CUDA_TRY(cudaFuncSetAttribute(potrf_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmem));
+      attr_set = true;
+    }
+    potrf_leaf_kernel<<<1, 256, kLeafSmem, st>>>((int)n, Z, ldz, Linv, fail, (int)off);
     QDWHP_LAUNCH_CHECK();
     return QDWHP_OK;
   }

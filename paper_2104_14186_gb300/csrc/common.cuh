@@ -45,7 +45,7 @@ void note_launch();
 // Opt-in timing of the DMMA GEMM launches (CUDA events around each launch on its stream).
 bool gemm_prof_enabled();
 // Records the start event; returns a slot id for gemm_prof_end (or -1 when disabled).
-int gemm_prof_start(cudaStream_t st, double flops);
+int gemm_prof_start(cudaStream_t st, double flops, const double* shape);
 void gemm_prof_stop(cudaStream_t st, int slot);
 
 // Device-side error flags written by kernels (bitwise OR into ws->flags).

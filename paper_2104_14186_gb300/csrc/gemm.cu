@@ -204,7 +204,11 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   double* partial = split > 1 ? splitk_ws : nullptr;
   // algorithmic flops: 2 m n k, or n (n + 1) k for the lower triangle only
   const double flops = (uplo == LOWER) ? (double)N * (N + 1) * K : 2.0 * M * N * K;
-  const int prof_slot = gemm_prof_enabled() ? gemm_prof_start(st, flops) : -1;
+  int prof_slot = -1;
+  if (gemm_prof_enabled()) {
+    const double shape[5] = {(double)M, (double)N, (double)K, (double)(uplo == LOWER), (double)split};
+    prof_slot = gemm_prof_start(st, flops, shape);
+  }
   if (big)
     launch<64, 64>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
   else

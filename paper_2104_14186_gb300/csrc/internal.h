@@ -72,5 +72,7 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
 // C (m x ncols) := Q [0; I; 0] restricted to columns col0 .. col0+ncols-1 of Q (explicit Q columns).
 qdwhp_status orgqr_columns(cudaStream_t st, const QRFactors& f, int64_t col0, int64_t ncols, double* C,
                            int64_t ldc, double* scratch);
+// C (m x ncols) := Q C with the full Q of the factorisation (scratch as for orgqr_columns).
+qdwhp_status ormqr_left(cudaStream_t st, const QRFactors& f, double* C, int64_t ncols, int64_t ldc, double* scratch);
 
 }  // namespace qdwhp

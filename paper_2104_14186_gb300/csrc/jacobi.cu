@@ -3,15 +3,20 @@
 //
 // A sweep visits every column pair once in the round-robin ("circle method")
 // order: nc - 1 rounds of nc / 2 disjoint pairs (a dummy column pads odd nc).  The
-// pairs of a round are independent, so a round is one launch with one CTA per pair:
-// the CTA forms ||g_p||^2, ||g_q||^2 and g_p^T g_q, and applies the plane rotation
-// that makes the two columns orthogonal to G and to the accumulated Vj.
+// pairs of a round are independent: a CTA takes a pair, forms ||g_p||^2, ||g_q||^2
+// and g_p^T g_q, and applies the plane rotation that makes the two columns
+// orthogonal to G and to the accumulated Vj.  A whole sweep is one cooperative
+// launch with a grid barrier between rounds.
 //   - SVD: G = A Q2 (m x ell): sigma_i = ||w_i||, U = W Sigma^{-1}, V~ = Vj.
 //   - EIG: G = M + sigma I with M = Q2^T A Q2 and sigma >= ||M||_2, so G is positive
 //     semidefinite and its right singular vectors are eigenvectors of M; the
 //     eigenvalues are then taken as Rayleigh quotients v_i^T M v_i.
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "krylov.h"
+
+namespace cg = cooperative_groups;
 
 namespace qdwhp {
 
@@ -27,14 +32,11 @@ __device__ __forceinline__ void pair_of(int r, int h, int N, int& p, int& q) {
   }
 }
 
-__global__ void __launch_bounds__(256) jacobi_round_kernel(int mg, int nc, int N, int round, double* G, int64_t ldg,
-                                                           double* Vj, int64_t ldv, double tol, JacobiState* jst) {
-  __shared__ double red[3][32];
-  __shared__ double rot[2];
-  __shared__ int skip;
-  int p, q;
-  pair_of(round, blockIdx.x, N, p, q);
-  if (p >= nc || q >= nc) return;   // dummy column
+// Orthogonalise columns p and q of G (length mg) and rotate the same columns of Vj
+// (length nc).  `red`, `rot` and `flag` are shared scratch of the calling CTA; all
+// threads of the CTA call this together.
+__device__ void rotate_pair(int p, int q, int mg, int nc, double* G, int64_t ldg, double* Vj, int64_t ldv, double tol,
+                            JacobiState* jst, double (*red)[32], double* rot, int* flag) {
   if (p > q) {
     const int t = p;
     p = q;
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(int mg, int nc, int N
       sb += red[1][w];
       sc += red[2][w];
     }
-    skip = 1;
+    *flag = 1;   // skip
     if (!isfinite(sa) || !isfinite(sb) || !isfinite(sc)) {
       atomicExch(&jst->nonfinite, 1);
     } else if (sa > 0.0 && sb > 0.0 && sc != 0.0) {
@@ -79,25 +81,58 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(int mg, int nc, int N
         const double cs = 1.0 / sqrt(1.0 + t * t);
         rot[0] = cs;
         rot[1] = cs * t;
-        skip = 0;
+        *flag = 0;
       }
     }
   }
   __syncthreads();
-  if (skip) return;
-  const double cs = rot[0], sn = rot[1];
-  for (int i = threadIdx.x; i < mg; i += blockDim.x) {
-    const double x = gp[i], y = gq[i];
-    gp[i] = cs * x - sn * y;
-    gq[i] = sn * x + cs * y;
+  if (*flag == 0) {
+    const double cs = rot[0], sn = rot[1];
+    for (int i = threadIdx.x; i < mg; i += blockDim.x) {
+      const double x = gp[i], y = gq[i];
+      gp[i] = cs * x - sn * y;
+      gq[i] = sn * x + cs * y;
+    }
+    double* vp = Vj + (int64_t)p * ldv;
+    double* vq = Vj + (int64_t)q * ldv;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+      const double x = vp[i], y = vq[i];
+      vp[i] = cs * x - sn * y;
+      vq[i] = sn * x + cs * y;
+    }
   }
-  double* vp = Vj + (int64_t)p * ldv;
-  double* vq = Vj + (int64_t)q * ldv;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    const double x = vp[i], y = vq[i];
-    vp[i] = cs * x - sn * y;
-    vq[i] = sn * x + cs * y;
+  __syncthreads();
+}
+
+// One full sweep (N - 1 rounds) in one cooperative launch: the CTAs share the pairs of
+// a round and meet at a grid barrier between rounds.
+__global__ void __launch_bounds__(256) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg, double* Vj,
+                                                           int64_t ldv, double tol, JacobiState* jst) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[3][32];
+  __shared__ double rot[2];
+  __shared__ int flag;
+  for (int r = 0; r < N - 1; ++r) {
+    for (int h = blockIdx.x; h < N / 2; h += gridDim.x) {
+      int p, q;
+      pair_of(r, h, N, p, q);
+      if (p < nc && q < nc) rotate_pair(p, q, mg, nc, G, ldg, Vj, ldv, tol, jst, red, rot, &flag);
+    }
+    grid.sync();
   }
+}
+
+int sweep_grid(int pairs) {
+  static int max_blocks = 0;
+  if (max_blocks == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, 256, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    int dev = 0, sms = kNumSMs;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    max_blocks = std::min(per_sm, 2) * sms;
+  }
+  return std::max(1, std::min(pairs, max_blocks));
 }
 
 __global__ void column_norms_kernel(int mg, const double* G, int64_t ldg, double* norms) {
@@ -170,12 +205,13 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     return QDWHP_OK;
   }
   const int N = (int)(nc + (nc & 1));
+  const int grid = sweep_grid(N / 2);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     QDWHP_CUDA_TRY(cudaMemsetAsync(jst_dev, 0, sizeof(JacobiState), st));
-    for (int r = 0; r < N - 1; ++r) {
-      jacobi_round_kernel<<<N / 2, 256, 0, st>>>((int)mg, (int)nc, N, r, G, ldg, Vj, ldv, tol, jst_dev);
-      QDWHP_LAUNCH_CHECK();
-    }
+    int mg_i = (int)mg, nc_i = (int)nc, N_i = N;
+    void* args[] = {&mg_i, &nc_i, &N_i, &G, &ldg, &Vj, &ldv, &tol, &jst_dev};
+    QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(256), args, 0, st));
+    QDWHP_LAUNCH_CHECK();
     QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
     QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
     *sweeps_out = sweep + 1;

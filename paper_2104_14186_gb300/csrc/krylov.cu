@@ -3,9 +3,9 @@
 // and the SplitMix64 start vectors.
 //
 // Lanczos runs with full reorthogonalisation (classical Gram-Schmidt, twice) and
-// keeps every scalar on the device: the host only enqueues the steps.  The
-// tridiagonal T (at most 64 x 64) is diagonalised by cyclic Jacobi in one warp;
-// the extreme Ritz values and their residual norms beta_m |s_{m,i}| are the output.
+// keeps every scalar on the device: the host only enqueues the steps.  Only the
+// extreme eigenpairs of the tridiagonal T (at most 48 x 48) are needed: the extreme
+// Ritz values and their residual norms beta_m |s_{m,i}| are the output.
 #include "internal.h"
 #include "krylov.h"
 
@@ -112,76 +112,108 @@ __global__ void normalize_kernel(int n, double* q) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] *= inv;
 }
 
-// Cyclic Jacobi on the m x m tridiagonal T (one warp); writes the extreme Ritz values
-// and residual norms beta_{m-1} |s_{m-1, i}|.
-constexpr int kMaxT = 48;   // two 48 x 49 double arrays stay under the 48 KB static shared-memory limit
+// Extreme eigenpairs of the m x m Lanczos tridiagonal T (one warp).  Eigenvalues by
+// multisection on Sturm counts (each lane evaluates one of 32 points of the current
+// interval, so every step shrinks it 33-fold); the last component of each eigenvector
+// by two steps of inverse iteration with T - x I factored as L D L^T, x just outside
+// the spectrum so the factorisation is definite.  Writes theta_min, its residual norm
+// beta_{m-1} |s_{m-1}|, theta_max and its residual norm.
+constexpr int kMaxT = 48;
+
+__device__ int sturm_count(const double* al, const double* be, int m, double x, double pivmin) {
+  // number of eigenvalues of T below x: negative pivots of T - x I = L D L^T
+  int cnt = 0;
+  double d = al[0] - x;
+  if (fabs(d) < pivmin) d = -pivmin;
+  cnt += d < 0.0;
+  for (int i = 1; i < m; ++i) {
+    d = (al[i] - x) - be[i - 1] * be[i - 1] / d;
+    if (fabs(d) < pivmin) d = -pivmin;
+    cnt += d < 0.0;
+  }
+  return cnt;
+}
+
+// Find the eigenvalue where the Sturm count steps to `target` (1: smallest, m: largest).
+__device__ double multisect(const double* al, const double* be, int m, double lo, double hi, int target,
+                            double pivmin) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < 64; ++it) {
+    const double w = hi - lo;
+    if (!(w > 2.0 * 0x1.0p-52 * fmax(fabs(lo), fabs(hi)) + pivmin)) break;
+    const double x = lo + w * (double)(lane + 1) / 33.0;
+    const int c = sturm_count(al, be, m, x, pivmin);
+    const unsigned mask = __ballot_sync(0xffffffffu, c >= target);
+    const int first = mask ? __ffs(mask) - 1 : 32;
+    const double xf = __shfl_sync(0xffffffffu, x, first < 32 ? first : 31);
+    const double xp = __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0);
+    if (first == 32) {
+      lo = xf;                       // all 32 points below the eigenvalue
+    } else {
+      hi = xf;
+      lo = first > 0 ? xp : lo;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// |last component| / ||y|| of the eigenvector for the eigenvalue near x (lane 0).
+__device__ double last_component(const double* al, const double* be, int m, double x) {
+  double l[kMaxT], d[kMaxT], y[kMaxT];
+  d[0] = al[0] - x;
+  for (int i = 1; i < m; ++i) {
+    l[i] = be[i - 1] / d[i - 1];
+    d[i] = (al[i] - x) - l[i] * be[i - 1];
+  }
+  for (int i = 0; i < m; ++i) y[i] = 1.0;
+  for (int it = 0; it < 2; ++it) {
+    for (int i = 1; i < m; ++i) y[i] -= l[i] * y[i - 1];          // L z = y
+    y[m - 1] /= d[m - 1];                                          // D L^T y = z
+    for (int i = m - 2; i >= 0; --i) y[i] = y[i] / d[i] - l[i + 1] * y[i + 1];
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < m; ++i) y[i] /= nrm;
+  }
+  return fabs(y[m - 1]);
+}
+
 __global__ void tridiag_extremes_kernel(LanczosState* stt) {
-  __shared__ double a[kMaxT][kMaxT + 1];
-  __shared__ double v[kMaxT][kMaxT + 1];
+  __shared__ double al[kMaxT], be[kMaxT];
   const int lane = threadIdx.x;
   const int m = max(1, min(stt->m, kMaxT));
-  for (int e = lane; e < kMaxT * kMaxT; e += 32) {
-    const int i = e % kMaxT, j = e / kMaxT;
-    double t = 0.0;
-    if (i < m && j < m) {
-      if (i == j) t = stt->alpha[i];
-      else if (i == j + 1) t = stt->beta[j];
-      else if (j == i + 1) t = stt->beta[i];
-    }
-    a[i][j] = t;
-    v[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int i = lane; i < kMaxT; i += 32) {
+    al[i] = i < m ? stt->alpha[i] : 0.0;
+    be[i] = i < m - 1 ? stt->beta[i] : 0.0;
   }
   __syncwarp();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0;
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = e % m, j = e / m;
-      if (i < j) off += a[i][j] * a[i][j];
-    }
-    off = warp_sum(off);
-    double fro = 0.0;
-    for (int e = lane; e < m * m; e += 32) fro += a[e % m][e / m] * a[e % m][e / m];
-    fro = warp_sum(fro);
-    if (off <= 1e-36 * fro || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p) {
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = a[p][q];
-        if (apq == 0.0) continue;
-        const double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
-        const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-        __syncwarp();
-        for (int i = lane; i < m; i += 32) {
-          const double aip = a[i][p], aiq = a[i][q];
-          a[i][p] = c * aip - s * aiq;
-          a[i][q] = s * aip + c * aiq;
-          const double vip = v[i][p], viq = v[i][q];
-          v[i][p] = c * vip - s * viq;
-          v[i][q] = s * vip + c * viq;
-        }
-        __syncwarp();
-        for (int j = lane; j < m; j += 32) {
-          const double apj = a[p][j], aqj = a[q][j];
-          a[p][j] = c * apj - s * aqj;
-          a[q][j] = s * apj + c * aqj;
-        }
-        __syncwarp();
-        if (lane == 0) a[p][q] = a[q][p] = 0.0;
-        __syncwarp();
-      }
-    }
+  // Gershgorin interval
+  double lo = INFINITY, hi = -INFINITY, scale = 0.0;
+  for (int i = lane; i < m; i += 32) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < m - 1 ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+    scale = fmax(scale, fabs(al[i]) + r);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    scale = fmax(scale, __shfl_xor_sync(0xffffffffu, scale, o));
+  }
+  const double pivmin = fmax(scale, 1e-300) * 0x1.0p-100;
+  const double pad = fmax(scale, 1e-300) * 1e-12;
+  lo -= pad;
+  hi += pad;
+  const double tmin = multisect(al, be, m, lo, hi, 1, pivmin);
+  const double tmax = multisect(al, be, m, lo, hi, m, pivmin);
   if (lane == 0) {
-    int imin = 0, imax = 0;
-    for (int i = 1; i < m; ++i) {
-      if (a[i][i] < a[imin][imin]) imin = i;
-      if (a[i][i] > a[imax][imax]) imax = i;
-    }
     const double bm = fabs(stt->beta[m - 1]);
-    stt->out[0] = a[imin][imin];
-    stt->out[1] = bm * fabs(v[m - 1][imin]);
-    stt->out[2] = a[imax][imax];
-    stt->out[3] = bm * fabs(v[m - 1][imax]);
+    const double shift = fmax(scale, 1e-300) * 1e-13;
+    stt->out[0] = tmin;
+    stt->out[1] = bm * last_component(al, be, m, tmin - shift);
+    stt->out[2] = tmax;
+    stt->out[3] = bm * last_component(al, be, m, tmax + shift);
   }
 }
 

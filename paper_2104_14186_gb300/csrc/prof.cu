@@ -17,7 +17,9 @@ std::atomic<unsigned long long> g_launches{0};
 struct ProfSlot {
   cudaEvent_t a = nullptr, b = nullptr;
   double flops = 0.0;
+  double shape[5] = {0, 0, 0, 0, 0};   // m, n, k, lower, split
 };
+std::vector<double> g_records;          // 6 doubles per GEMM of the last profile: m, n, k, lower, split, ms
 std::mutex g_mu;
 bool g_on = false;
 std::vector<ProfSlot> g_slots;
@@ -28,7 +30,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 bool gemm_prof_enabled() { return g_on; }
 
-int gemm_prof_start(cudaStream_t st, double flops) {
+int gemm_prof_start(cudaStream_t st, double flops, const double* shape) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return -1;
   if (g_used == g_slots.size()) {
@@ -38,6 +40,7 @@ int gemm_prof_start(cudaStream_t st, double flops) {
   }
   const int slot = (int)g_used++;
   g_slots[slot].flops = flops;
+  for (int i = 0; i < 5; ++i) g_slots[slot].shape[i] = shape ? shape[i] : 0.0;
   cudaEventRecord(g_slots[slot].a, st);
   return slot;
 }
@@ -66,18 +69,29 @@ QDWHP_API qdwhp_status qdwhp_profile_end(double* gemm_ms, double* gemm_flops, in
   std::lock_guard<std::mutex> lk(g_mu);
   g_on = false;
   double ms_total = 0.0, fl = 0.0;
+  g_records.clear();
   for (size_t i = 0; i < g_used; ++i) {
     QDWHP_CUDA_TRY(cudaEventSynchronize(g_slots[i].b));
     float ms = 0.f;
     QDWHP_CUDA_TRY(cudaEventElapsedTime(&ms, g_slots[i].a, g_slots[i].b));
     ms_total += ms;
     fl += g_slots[i].flops;
+    for (int j = 0; j < 5; ++j) g_records.push_back(g_slots[i].shape[j]);
+    g_records.push_back(ms);
   }
   if (gemm_ms) *gemm_ms = ms_total;
   if (gemm_flops) *gemm_flops = fl;
   if (gemm_launches) *gemm_launches = (int64_t)g_used;
   g_used = 0;
   return QDWHP_OK;
+}
+
+QDWHP_API int64_t qdwhp_profile_records(double* out, int64_t capacity) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const int64_t n = (int64_t)g_records.size() / 6;
+  if (out != nullptr)
+    for (int64_t i = 0; i < std::min(n, capacity) * 6; ++i) out[i] = g_records[i];
+  return n;
 }
 
 }  // extern "C"

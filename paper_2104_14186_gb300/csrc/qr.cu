@@ -25,8 +25,8 @@ namespace {
 
 constexpr int NB = kQRNB;          // panel width (32)
 constexpr int kPanelThreads = 256;
-constexpr int kPanelCTAs = 120;
-constexpr int kMinRowsPerCTA = 32;
+constexpr int kPanelCTAs = 96;
+constexpr int kMinRowsPerCTA = 64;
 constexpr int kPartStride = NB + 1;
 
 struct PanelArgs {
@@ -40,7 +40,7 @@ struct PanelArgs {
   double* tau;      // jb
   double* diagR;    // jb
   double* part;     // gridDim.x * kPartStride
-  double* gram;     // gridDim.x * NB * NB
+  double* gram;     // (gridDim.x + 1) * NB * NB: per-CTA partials, then the totals
   double* alpha_slot;
 };
 
@@ -125,11 +125,22 @@ __global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
     }
     grid.sync();
 
-    // Phase C: sum the partials and update the remaining panel columns.
+    // Phase C: sum the partials (8 groups of CTAs per column, combined in a fixed order)
+    // and update the remaining panel columns.
+    {
+      const int c = tid % NB, grp = tid / NB;
+      double w = 0.0;
+      if (c > i && c < jb) {
+#pragma unroll 4
+        for (int g = grp; g < G; g += 8) w += a.part[g * kPartStride + c];
+      }
+      red8[grp][c] = w;
+    }
+    __syncthreads();
     if (tid < NB) {
       double w = 0.0;
-      if (tid > i && tid < jb)
-        for (int g = 0; g < G; ++g) w += a.part[g * kPartStride + tid];
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8) w += red8[g8][tid];
       wsh[tid] = w;
     }
     __syncthreads();
@@ -176,14 +187,25 @@ __global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
   }
   grid.sync();
 
+  // Sum the per-CTA Gram partials: CTA b owns entries [b*chunk, (b+1)*chunk).
+  {
+    const int chunk = (NB * NB + G - 1) / G;
+    const int e0 = b * chunk, e1 = min(NB * NB, e0 + chunk);
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+      double acc = 0.0;
+#pragma unroll 4
+      for (int g = 0; g < G; ++g) acc += a.gram[(size_t)g * NB * NB + e];
+      a.gram[(size_t)G * NB * NB + e] = acc;
+    }
+  }
+  grid.sync();
+
   if (b == 0) {
     // T (forward, columnwise): T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T v_i)(0:i).
     __shared__ double gsum[NB][NB + 1];
     __shared__ double Ts[NB][NB + 1];
     for (int e = tid; e < NB * NB; e += blockDim.x) {
-      double acc = 0.0;
-      for (int g = 0; g < G; ++g) acc += a.gram[(size_t)g * NB * NB + e];
-      gsum[e % NB][e / NB] = acc;
+      gsum[e % NB][e / NB] = a.gram[(size_t)G * NB * NB + e];
       Ts[e % NB][e / NB] = 0.0;
     }
     __syncthreads();
@@ -234,7 +256,7 @@ qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
 size_t qr_scratch_elems(int64_t m, int64_t n) {
   const size_t wn = (size_t)NB * std::max<int64_t>(n, 1);
   size_t splitk = gemm_splitk_ws_elems(NB, std::max<int64_t>(n, 1));
-  return 2 * wn + splitk + (size_t)kPanelCTAs * kPartStride + (size_t)kPanelCTAs * NB * NB + 64;
+  return 2 * wn + splitk + (size_t)kPanelCTAs * kPartStride + (size_t)(kPanelCTAs + 1) * NB * NB + 64;
   (void)m;
 }
 
@@ -249,7 +271,7 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
   double* splitk = W2 + (size_t)NB * n;
   double* part = splitk + splitk_elems;
   double* gram = part + (size_t)kPanelCTAs * kPartStride;
-  double* alpha_slot = gram + (size_t)kPanelCTAs * NB * NB;
+  double* alpha_slot = gram + (size_t)(kPanelCTAs + 1) * NB * NB;
   for (int64_t j = 0; j < n; j += NB) {
     const int jb = (int)std::min<int64_t>(NB, n - j);
     const int64_t R = m - j;
@@ -279,19 +301,17 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
   return QDWHP_OK;
 }
 
-qdwhp_status orgqr_columns(cudaStream_t st, const QRFactors& f, int64_t col0, int64_t ncols, double* C, int64_t ldc,
-                           double* scratch) {
+namespace {
+
+// C(j:, :) -= V_p (T_p (V_p^T C(j:, :))) for blocks p = last_block .. 0, i.e. C := Q C restricted to
+// the first last_block + 1 block reflectors.
+qdwhp_status apply_blocks(cudaStream_t st, const QRFactors& f, int64_t last_block, double* C, int64_t ncols,
+                          int64_t ldc, double* scratch) {
   const int64_t m = f.m, n = f.n;
-  if (col0 < 0 || ncols < 0 || col0 + ncols > n) return QDWHP_ERR_ARG;
-  if (ncols == 0) return QDWHP_OK;
-  QDWHP_TRY(set_matrix(st, m, ncols, 0.0, 0.0, C, ldc));
-  QDWHP_TRY(set_matrix(st, ncols, ncols, 0.0, 1.0, C + col0, ldc));
   double* W = scratch;
   double* W2 = W + (size_t)NB * ncols;
   const size_t splitk_elems = gemm_splitk_ws_elems(NB, ncols);
   double* splitk = W2 + (size_t)NB * ncols;
-  // Blocks whose first column is past the selected range act on zero rows: skip them.
-  const int64_t last_block = (col0 + ncols - 1) / NB;
   for (int64_t p = last_block; p >= 0; --p) {
     const int64_t j = p * NB;
     const int jb = (int)std::min<int64_t>(NB, n - j);
@@ -299,12 +319,29 @@ qdwhp_status orgqr_columns(cudaStream_t st, const QRFactors& f, int64_t col0, in
     const double* V = f.Vall + j + j * m;
     const double* T = f.T + (size_t)p * NB * NB;
     double* Cj = C + j;
-    // C(j:, :) -= V (T (V^T C(j:, :)))
     QDWHP_TRY(gemm(st, true, false, jb, ncols, R, 1.0, V, m, Cj, ldc, 0.0, W, jb, FULL, 0.0, splitk, splitk_elems));
     QDWHP_TRY(gemm(st, false, false, jb, ncols, jb, 1.0, T, NB, W, jb, 0.0, W2, jb));
     QDWHP_TRY(gemm(st, false, false, R, ncols, jb, -1.0, V, m, W2, jb, 1.0, Cj, ldc));
   }
   return QDWHP_OK;
+}
+
+}  // namespace
+
+qdwhp_status orgqr_columns(cudaStream_t st, const QRFactors& f, int64_t col0, int64_t ncols, double* C, int64_t ldc,
+                           double* scratch) {
+  const int64_t m = f.m, n = f.n;
+  if (col0 < 0 || ncols < 0 || col0 + ncols > n) return QDWHP_ERR_ARG;
+  if (ncols == 0) return QDWHP_OK;
+  QDWHP_TRY(set_matrix(st, m, ncols, 0.0, 0.0, C, ldc));
+  QDWHP_TRY(set_matrix(st, ncols, ncols, 0.0, 1.0, C + col0, ldc));
+  // Blocks whose first column is past the selected range act on zero rows: skip them.
+  return apply_blocks(st, f, (col0 + ncols - 1) / NB, C, ncols, ldc, scratch);
+}
+
+qdwhp_status ormqr_left(cudaStream_t st, const QRFactors& f, double* C, int64_t ncols, int64_t ldc, double* scratch) {
+  if (ncols <= 0 || f.n <= 0) return QDWHP_OK;
+  return apply_blocks(st, f, (f.n - 1) / NB, C, ncols, ldc, scratch);
 }
 
 }  // namespace qdwhp

@@ -394,15 +394,21 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   }
   QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
   QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qb, n, 0.0, w.C, m));
+  // Ritz values of A^T A on span(Qb): eigenvalues of H = C^T C (b x b, positive semidefinite,
+  // so they are its singular values: column norms after one-sided Jacobi).
+  double* H = w.W;
+  QDWHP_TRY(gemm(st, true, false, b, b, m, 1.0, w.C, m, w.C, m, 0.0, H, b, FULL, 0.0, w.c.splitk, w.c.splitk_elems));
+  QDWHP_TRY(symmetrize_avg(st, b, H, b));
   int sweeps = 0, conv = 0;
-  const double tol_b = kEps * std::sqrt((double)m);
-  QDWHP_TRY(jacobi_onesided(st, m, b, w.C, m, w.W, b, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst, &sweeps, &conv));
+  const double tol_b = kEps * std::sqrt((double)b);
+  QDWHP_TRY(jacobi_onesided(st, b, b, H, b, w.Vj, b, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst, &sweeps, &conv));
   if (!conv) return QDWHP_ERR_NOT_CONVERGED;
-  QDWHP_TRY(column_norms(st, m, b, w.C, m, w.c.vals));
+  QDWHP_TRY(column_norms(st, b, b, H, b, w.c.vals));
   QDWHP_TRY(select_sort(st, b, w.c.vals, -1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.q.Z));
-  double sig_hat = 0.0;
-  QDWHP_TRY(sync_read(st, &sig_hat, w.q.Z, sizeof(double)));
+  double theta_k = 0.0;
+  QDWHP_TRY(sync_read(st, &theta_k, w.q.Z, sizeof(double)));
+  const double sig_hat = std::sqrt(std::max(theta_k, 0.0));
   double s = std::max(sig_hat / alpha * (1.0 - 1e-10), 1e-15);
 
   int retries = 0;
@@ -446,16 +452,19 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     ell = n - ind;
     count = 0;
     if (ell > 0) {
-      // Steps 5-6: Q2, A Q2 and its SVD by one-sided Jacobi.
+      // Steps 5-6: Q2, A Q2 and its SVD.  A Q2 = Q_C R (Householder), then one-sided Jacobi
+      // on R: R Vj = W, sigma_i = ||w_i||, so A Q2 = (Q_C W Sigma^{-1}) Sigma Vj^T.
       double* Q2 = w.q.Y;
       QDWHP_TRY(orgqr_columns(st, w.f, ind, ell, Q2, n, w.qr_scratch));
       QDWHP_TRY(gemm(st, false, false, m, ell, n, 1.0, A, lda, Q2, n, 0.0, w.C, m));
-      const double tol = kEps * std::sqrt((double)m);
-      QDWHP_TRY(jacobi_onesided(st, m, ell, w.C, m, w.Vj, ell, o.jacobi_max_sweeps, tol, w.c.jst, &hs.jst, &sweeps,
+      QDWHP_TRY(geqrf(st, m, ell, w.C, m, w.q.qf, w.q.qr_scratch));
+      QDWHP_TRY(copy_upper(st, ell, w.C, m, w.W, ell));
+      const double tol = kEps * std::sqrt((double)ell);
+      QDWHP_TRY(jacobi_onesided(st, ell, ell, w.W, ell, w.Vj, ell, o.jacobi_max_sweeps, tol, w.c.jst, &hs.jst, &sweeps,
                                 &conv));
       if (!conv) return QDWHP_ERR_NOT_CONVERGED;
       inf.jacobi_sweeps = sweeps;
-      QDWHP_TRY(column_norms(st, m, ell, w.C, m, w.c.vals));
+      QDWHP_TRY(column_norms(st, ell, ell, w.W, ell, w.c.vals));
       // Step 7: sigma >= s alpha, descending.
       QDWHP_TRY(select_sort(st, ell, w.c.vals, -1.0, -s * alpha, w.c.order, w.c.ints + 1));
       QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
@@ -466,11 +475,13 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     s = std::max(0.5 * s, 1e-15);
   }
   if (count < k) return QDWHP_ERR_COUNT;
-  // Step 8: U1 = U~1, V1 = Q2 V~1.
+  // Step 8: U1 = Q_C [W_sel Sigma_sel^{-1}; 0], V1 = Q2 Vj_sel.
   QDWHP_TRY(gather_values(st, k, w.c.vals, w.c.order, sigma));
-  QDWHP_TRY(gather_columns(st, m, k, w.C, m, w.c.order, w.c.vals, U, ldu));
-  QDWHP_TRY(gather_columns(st, ell, k, w.Vj, ell, w.c.order, nullptr, w.W, ell));
-  QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, w.W, ell, 0.0, V, ldv));
+  QDWHP_TRY(gather_columns(st, ell, k, w.W, ell, w.c.order, w.c.vals, U, ldu));
+  if (m > ell) QDWHP_TRY(set_matrix(st, m - ell, k, 0.0, 0.0, U + ell, ldu));
+  QDWHP_TRY(ormqr_left(st, w.q.qf, U, k, ldu, w.q.qr_scratch));
+  QDWHP_TRY(gather_columns(st, ell, k, w.Vj, ell, w.c.order, nullptr, w.X, ell));
+  QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, w.X, ell, 0.0, V, ldv));
   inf.ms_total = timer.stop();
   inf.retries = retries;
   inf.ell = ell;

@@ -92,6 +92,7 @@ SIGNATURES = {
     "qdwhp_launch_count": (C.c_ulonglong, []),
     "qdwhp_profile_begin": (C.c_int, []),
     "qdwhp_profile_end": (C.c_int, [C.POINTER(D), C.POINTER(D), C.POINTER(I64)]),
+    "qdwhp_profile_records": (I64, [C.POINTER(D), I64]),
 }
 
 
@@ -257,6 +258,13 @@ def profile_end() -> dict:
     ms, fl, n = D(0.0), D(0.0), I64(0)
     _check(lib().qdwhp_profile_end(C.byref(ms), C.byref(fl), C.byref(n)), "qdwhp_profile_end")
     return {"gemm_ms": ms.value, "gemm_flops": fl.value, "gemm_launches": n.value}
+
+
+def profile_records() -> list:
+    n = int(lib().qdwhp_profile_records(None, 0))
+    buf = (D * (6 * max(n, 1)))()
+    lib().qdwhp_profile_records(buf, n)
+    return [tuple(buf[6 * i:6 * i + 6]) for i in range(n)]
 
 
 # ---- building blocks ----
