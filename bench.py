@@ -325,7 +325,7 @@ def run_kernel_gemm(args):
     peaks = load_peaks()
     peak = peaks.get("bf16_tflops", 1.9e3) * NOMINAL_FP64_OVER_BF16
     tf = 2.0 * n ** 3 / (statistics.median(ms) / 1e3) / 1e12
-    print(json.dumps({"kernel": "dgemm_kernel<64,64,N,N> via qdwhp_gemm_f64", "m": n, "n": n, "k": n,
+    print(json.dumps({"kernel": "dgemm_kernel<32,32,N,N> via qdwhp_gemm_f64", "m": n, "n": n, "k": n,
                       "ms_median": statistics.median(ms), "tflops": tf, "peak": peak, "frac": tf / peak,
                       "alg_bytes": 3 * n * n * 8}), flush=True)
 

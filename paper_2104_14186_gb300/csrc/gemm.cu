@@ -4,8 +4,8 @@
 // part, DMMA peaks at ~1.05 TFLOP/s (DFMA ~1.01): one SM does only a few FP64
 // flops per clock, so the kernel needs no deep pipelining to stay compute bound
 // (a 64x64x16 tile step is ~36k clocks of DMMA work against ~1k clocks of load
-// latency).  What matters is covering all 152 SMs: small outputs use 32x32 tiles
-// and split-K.  Split-K writes per-slice partial sums that a second kernel adds
+// latency).  What matters is covering all 152 SMs and keeping many CTAs resident:
+// 32x32 tiles everywhere, and split-K for outputs with few tiles.  Split-K writes per-slice partial sums that a second kernel adds
 // in a fixed order, so results do not depend on scheduling.
 #include "internal.h"
 
@@ -14,6 +14,7 @@ namespace qdwhp {
 namespace {
 
 constexpr int kBK = 16;
+constexpr int kChunk = 64;      // K slice summed separately before joining the accumulator
 constexpr int kThreads = 128;   // 2 x 2 warps
 
 __device__ __forceinline__ void dmma884(double (&c)[2], double a, double b) {
@@ -43,11 +44,14 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(int M, int N, int K, in
   const int wm = warp & 1, wn = warp >> 1;
   const int g = lane >> 2, t4 = lane & 3;
 
-  double acc[MT][NT][2];
+  // Two-level accumulation: each kChunk-wide slice of K is summed into `part`, which is then
+  // added to `acc`, so the rounding chain per output is K / kChunk + kChunk / 4 long instead
+  // of K / 4 (the dot products here run over up to tens of thousands of terms).
+  double acc[MT][NT][2], part[MT][NT][2];
 #pragma unroll
   for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+    for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = part[i][j][0] = part[i][j][1] = 0.0;
 
   double ra[A_LD], rb[B_LD];
   auto load = [&](int k0) {
@@ -105,7 +109,17 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(int M, int N, int K, in
 #pragma unroll
       for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < NT; ++j) dmma884(acc[i][j], af[i], bf[j]);
+        for (int j = 0; j < NT; ++j) dmma884(part[i][j], af[i], bf[j]);
+    }
+    if (((k0 - kbeg) / kBK) % (kChunk / kBK) == kChunk / kBK - 1 || k0 + kBK >= kend) {
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          acc[i][j][0] += part[i][j][0];
+          acc[i][j][1] += part[i][j][1];
+          part[i][j][0] = part[i][j][1] = 0.0;
+        }
     }
   }
 
@@ -185,9 +199,9 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   if (m == 0 || n == 0) return QDWHP_OK;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return QDWHP_ERR_ARG;
   const int M = (int)m, N = (int)n, K = (int)k;
-  const int64_t tiles64 = (int64_t)ceil_div(M, 64) * ceil_div(N, 64);
-  const bool big = tiles64 >= 2 * kNumSMs;
-  const int BM = big ? 64 : 32, BN = big ? 64 : 32;
+  // 32 x 32 tiles throughout: the DMMA pipe is slow enough that a small tile (96 registers,
+  // many resident CTAs per SM) beats larger tiles (1.07 vs 1.00-1.02 TFLOP/s at 4096^3).
+  constexpr int BM = 32, BN = 32;
   const int64_t tiles = (int64_t)ceil_div(M, BM) * ceil_div(N, BN) / (uplo == LOWER ? 2 : 1);
   int split = 1;
   const size_t mn = (size_t)M * N;
@@ -209,10 +223,7 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
     const double shape[5] = {(double)M, (double)N, (double)K, (double)(uplo == LOWER), (double)split};
     prof_slot = gemm_prof_start(st, flops, shape);
   }
-  if (big)
-    launch<64, 64>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
-  else
-    launch<32, 32>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
+  launch<BM, BN>(st, ta, tb, grid, M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, partial);
   QDWHP_LAUNCH_CHECK();
   if (split > 1) {
     const int blocks = (int)std::min<size_t>((mn + 255) / 256, 4 * kNumSMs);

@@ -44,31 +44,51 @@ __device__ void rotate_pair(int p, int q, int mg, int nc, double* G, int64_t ldg
   }
   double* gp = G + (int64_t)p * ldg;
   double* gq = G + (int64_t)q * ldg;
-  double a = 0.0, b = 0.0, c = 0.0;
+  // ||g_p||^2 and ||g_q||^2 plainly; g_p^T g_q, which decides convergence and goes to
+  // zero, in double-double (TwoProduct and TwoSum) so that it is accurate far below
+  // sqrt(mg) u and the stopping test can ask for orthogonality at the level of u.
+  double a = 0.0, b = 0.0, c = 0.0, ce = 0.0;
   for (int i = threadIdx.x; i < mg; i += blockDim.x) {
     const double x = gp[i], y = gq[i];
     a += x * x;
     b += y * y;
-    c += x * y;
+    const double pr = x * y;
+    const double pe = fma(x, y, -pr);
+    const double t = c + pr;
+    const double z = t - c;
+    ce += ((c - (t - z)) + (pr - z)) + pe;
+    c = t;
   }
   a = warp_sum(a);
   b = warp_sum(b);
-  c = warp_sum(c);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double c2 = __shfl_xor_sync(0xffffffffu, c, o), e2 = __shfl_xor_sync(0xffffffffu, ce, o);
+    const double t = c + c2;
+    const double z = t - c;
+    ce += e2 + ((c - (t - z)) + (c2 - z));
+    c = t;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = a;
     red[1][wid] = b;
     red[2][wid] = c;
+    red[3][wid] = ce;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     const int nw = blockDim.x >> 5;
-    double sa = 0.0, sb = 0.0, sc = 0.0;
+    double sa = 0.0, sb = 0.0, sc = 0.0, se = 0.0;
     for (int w = 0; w < nw; ++w) {
       sa += red[0][w];
       sb += red[1][w];
-      sc += red[2][w];
+      const double t = sc + red[2][w];
+      const double z = t - sc;
+      se += red[3][w] + ((sc - (t - z)) + (red[2][w] - z));
+      sc = t;
     }
+    sc += se;
     *flag = 1;   // skip
     if (!isfinite(sa) || !isfinite(sb) || !isfinite(sc)) {
       atomicExch(&jst->nonfinite, 1);
@@ -109,7 +129,7 @@ __device__ void rotate_pair(int p, int q, int mg, int nc, double* G, int64_t ldg
 __global__ void __launch_bounds__(256) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg, double* Vj,
                                                            int64_t ldv, double tol, JacobiState* jst) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double red[3][32];
+  __shared__ double red[4][32];
   __shared__ double rot[2];
   __shared__ int flag;
   for (int r = 0; r < N - 1; ++r) {
@@ -206,6 +226,11 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
   }
   const int N = (int)(nc + (nc & 1));
   const int grid = sweep_grid(N / 2);
+  // Converged when the largest normalised inner product of a sweep is <= tol, or, once it
+  // is below sqrt(mg) u (the level of a plain dot product's rounding), when a sweep no
+  // longer reduces it by 4x: rotations of that size only stir rounding noise.
+  const double floor_tol = std::max(tol, 2.220446049250313e-16 * std::sqrt((double)std::max<int64_t>(mg, 1)));
+  double prev = INFINITY;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     QDWHP_CUDA_TRY(cudaMemsetAsync(jst_dev, 0, sizeof(JacobiState), st));
     int mg_i = (int)mg, nc_i = (int)nc, N_i = N;
@@ -219,11 +244,31 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     double max_off;
     static_assert(sizeof(double) == sizeof(unsigned long long), "size");
     memcpy(&max_off, &jst_host->max_off_bits, sizeof(double));
-    if (max_off <= tol) {
+    if (max_off <= tol || (max_off <= floor_tol && max_off > 0.25 * prev)) {
       *conv_out = 1;
       break;
     }
+    prev = max_off;
   }
+  return QDWHP_OK;
+}
+
+__global__ void normalize_columns_kernel(int rows, double* X, int64_t ldx, double* norms) {
+  __shared__ double red[32];
+  double* x = X + (int64_t)blockIdx.x * ldx;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) acc += x[i] * x[i];
+  acc = block_sum(acc, red);
+  const double nrm = sqrt(acc);
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) x[i] *= inv;
+  if (norms != nullptr && threadIdx.x == 0) norms[blockIdx.x] = nrm;
+}
+
+qdwhp_status normalize_columns(cudaStream_t st, int64_t rows, int64_t ncols, double* X, int64_t ldx, double* norms) {
+  if (ncols <= 0) return QDWHP_OK;
+  normalize_columns_kernel<<<(int)ncols, 256, 0, st>>>((int)rows, X, ldx, norms);
+  QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }
 

@@ -30,11 +30,14 @@ struct JacobiState {
 };
 // One-sided (Hestenes) Jacobi on the columns of G (mg x nc): G Vj = W with orthogonal
 // columns, Vj (nc x nc) orthogonal.  Runs sweeps until the largest normalised inner
-// product of a sweep is <= tol or max_sweeps; *sweeps_out = sweeps run, *conv_out = 1
-// if converged.  Synchronises the stream once per sweep.
+// product of a sweep is <= tol (or stagnates below sqrt(mg) u) or max_sweeps;
+// *sweeps_out = sweeps run, *conv_out = 1 if converged.  Synchronises the stream once
+// per sweep.
 qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G, int64_t ldg, double* Vj,
                              int64_t ldv, int max_sweeps, double tol, JacobiState* jst_dev, JacobiState* jst_host,
                              int* sweeps_out, int* conv_out);
+// Scales each column of X (rows x ncols) to unit 2-norm; norms (may be null) receives the old norms.
+qdwhp_status normalize_columns(cudaStream_t st, int64_t rows, int64_t ncols, double* X, int64_t ldx, double* norms);
 // norms[i] = ||G(:, i)||_2
 qdwhp_status column_norms(cudaStream_t st, int64_t mg, int64_t nc, const double* G, int64_t ldg, double* norms);
 // d[i] = v_i^T MV(:, i) (Rayleigh quotients from MV = M V)

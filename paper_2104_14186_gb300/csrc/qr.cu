@@ -10,8 +10,9 @@
 // a single CTA would be ~100x slower than the chip.  The panel kernel is therefore
 // a cooperative launch over up to kPanelCTAs CTAs: each CTA keeps its slice of
 // rows in shared memory, and the column norms and the reflector-application dot
-// products are reduced across CTAs through global partials with two grid-wide
-// barriers per column.  Partials are summed in CTA order, so the factorisation is
+// products are reduced across CTAs through global partials with one grid-wide
+// barrier per column (the squared norm and the dot products with the later columns
+// are summed together; the reflector's w_c = v^T x_c follows from them locally).  Partials are summed in CTA order, so the factorisation is
 // reproducible run to run.  The trailing update and the formation of Q are GEMMs.
 #include <cooperative_groups.h>
 
@@ -39,17 +40,17 @@ struct PanelArgs {
   double* T;        // jb x jb (ld NB)
   double* tau;      // jb
   double* diagR;    // jb
-  double* part;     // gridDim.x * kPartStride
+  double* part;     // 2 x kPanelCTAs x kPartStride (double-buffered by column parity)
   double* gram;     // (gridDim.x + 1) * NB * NB: per-CTA partials, then the totals
-  double* alpha_slot;
+  double* row_slot;   // 2 x NB doubles: row i of the panel, published by its owner
 };
 
 __global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double s[];          // local rows: s[r + c * rpc]
-  __shared__ double red[32];
   __shared__ double red8[8][NB];
   __shared__ double wsh[NB];
+  __shared__ double rowv[NB];
   __shared__ double taus[NB], betas[NB];
 
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
@@ -65,26 +66,58 @@ __global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
   __syncthreads();
 
   for (int i = 0; i < jb; ++i) {
-    // Phase A: partial ||x(i+1:)||^2 of column i; the owner of row i publishes alpha.
-    double acc = 0.0;
-    for (int r = tid; r < nr; r += blockDim.x) {
-      if (r0 + r > i) {
-        const double v = s[r + i * rpc];
-        acc += v * v;
+    // Partials and the published row are double-buffered by column parity: with one
+    // barrier per column, a CTA may already write column i+1's partials while another
+    // still reads column i's.
+    double* part = a.part + (i & 1) * (kPanelCTAs * kPartStride);
+    double* row_slot = a.row_slot + (i & 1) * NB;
+    // Phase A (one grid barrier per column): each CTA sums, over its rows below row i,
+    // x_r,i^2 and x_r,i x_r,c for the columns c > i; the owner of row i publishes the
+    // row-i entries (alpha = x_i,i and x_i,c).
+    {
+      const int c = tid % NB, grp = tid / NB;   // 8 row groups x 32 columns
+      double p = 0.0;
+      if (c >= i && c < jb) {
+        for (int r = grp; r < nr; r += 8) {
+          if (r0 + r > i) p += s[r + i * rpc] * s[r + c * rpc];
+        }
       }
+      red8[grp][c] = p;
     }
-    acc = block_sum(acc, red);
-    if (tid == 0) {
-      a.part[b * kPartStride] = acc;
-      if (i >= r0 && i < r0 + nr) *a.alpha_slot = s[(i - r0) + i * rpc];
+    __syncthreads();
+    if (tid < NB) {
+      double p = 0.0;
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8) p += red8[g8][tid];
+      // slot i holds the squared norm, slots c > i the dot products
+      if (tid >= i && tid < jb) part[b * kPartStride + tid] = p;
+      if (i >= r0 && i < r0 + nr && tid >= i && tid < jb) row_slot[tid] = s[(i - r0) + tid * rpc];
     }
     grid.sync();
 
-    // Phase B: every CTA forms the same reflector (sums in CTA order).
-    double ss = 0.0;
-    for (int g = tid; g < G; g += blockDim.x) ss += a.part[g * kPartStride];
-    ss = block_sum(ss, red);
-    const double alpha = *a.alpha_slot;
+    // Phase B: every CTA sums the partials in the same fixed order (8 groups of CTAs per
+    // slot) and forms the reflector: beta = -sign(alpha) sqrt(alpha^2 + ss), tau = (beta -
+    // alpha) / beta, v = [1; x(i+1:) / (alpha - beta)], and w_c = v^T x_c = x_i,c + e_c / (alpha - beta).
+    {
+      const int c = tid % NB, grp = tid / NB;
+      double w = 0.0;
+      if (c >= i && c < jb) {
+#pragma unroll 4
+        for (int g = grp; g < G; g += 8) w += part[g * kPartStride + c];
+      }
+      red8[grp][c] = w;
+    }
+    __syncthreads();
+    if (tid < NB) {
+      double w = 0.0;
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8) w += red8[g8][tid];
+      wsh[tid] = w;                              // wsh[i] = ss, wsh[c > i] = e_c
+      rowv[tid] = (tid >= i && tid < jb) ? row_slot[tid] : 0.0;
+    }
+    __syncthreads();
+    const double ss = wsh[i];
+    const double alpha = rowv[i];
     double beta, tau_i, scale;
     if (ss == 0.0) {
       beta = alpha;
@@ -95,55 +128,19 @@ __global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
       tau_i = (beta - alpha) / beta;
       scale = 1.0 / (alpha - beta);
     }
+    __syncthreads();
     if (tid == 0) {
       taus[i] = tau_i;
       betas[i] = beta;
     }
+    if (tid < NB && tid > i && tid < jb) wsh[tid] = rowv[tid] + scale * wsh[tid];
     for (int r = tid; r < nr; r += blockDim.x) {
       const int rg = r0 + r;
       if (rg > i) s[r + i * rpc] *= scale;
       else if (rg == i) s[r + i * rpc] = 1.0;
     }
     __syncthreads();
-    // partial w_c = sum_{rows >= i} v_r x_r,c for c > i
-    {
-      const int c = tid % NB, grp = tid / NB;   // 8 row groups x 32 columns
-      double p = 0.0;
-      if (c > i && c < jb) {
-        for (int r = grp; r < nr; r += 8) {
-          if (r0 + r >= i) p += s[r + i * rpc] * s[r + c * rpc];
-        }
-      }
-      red8[grp][c] = p;
-    }
-    __syncthreads();
-    if (tid < NB) {
-      double p = 0.0;
-#pragma unroll
-      for (int g8 = 0; g8 < 8; ++g8) p += red8[g8][tid];
-      if (tid > i && tid < jb) a.part[b * kPartStride + tid] = p;
-    }
-    grid.sync();
-
-    // Phase C: sum the partials (8 groups of CTAs per column, combined in a fixed order)
-    // and update the remaining panel columns.
-    {
-      const int c = tid % NB, grp = tid / NB;
-      double w = 0.0;
-      if (c > i && c < jb) {
-#pragma unroll 4
-        for (int g = grp; g < G; g += 8) w += a.part[g * kPartStride + c];
-      }
-      red8[grp][c] = w;
-    }
-    __syncthreads();
-    if (tid < NB) {
-      double w = 0.0;
-#pragma unroll
-      for (int g8 = 0; g8 < 8; ++g8) w += red8[g8][tid];
-      wsh[tid] = w;
-    }
-    __syncthreads();
+    // Phase C: x_c -= tau w_c v on rows >= i for c > i (local rows only).
     if (tau_i != 0.0) {
       for (int e = tid; e < nr * NB; e += blockDim.x) {
         const int r = e % nr, c = e / nr;
@@ -256,7 +253,7 @@ qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
 size_t qr_scratch_elems(int64_t m, int64_t n) {
   const size_t wn = (size_t)NB * std::max<int64_t>(n, 1);
   size_t splitk = gemm_splitk_ws_elems(NB, std::max<int64_t>(n, 1));
-  return 2 * wn + splitk + (size_t)kPanelCTAs * kPartStride + (size_t)(kPanelCTAs + 1) * NB * NB + 64;
+  return 2 * wn + splitk + 2 * (size_t)kPanelCTAs * kPartStride + (size_t)(kPanelCTAs + 1) * NB * NB + 2 * NB + 64;
   (void)m;
 }
 
@@ -270,8 +267,8 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
   const size_t splitk_elems = gemm_splitk_ws_elems(NB, n);
   double* splitk = W2 + (size_t)NB * n;
   double* part = splitk + splitk_elems;
-  double* gram = part + (size_t)kPanelCTAs * kPartStride;
-  double* alpha_slot = gram + (size_t)(kPanelCTAs + 1) * NB * NB;
+  double* gram = part + 2 * (size_t)kPanelCTAs * kPartStride;
+  double* row_slot = gram + (size_t)(kPanelCTAs + 1) * NB * NB;
   for (int64_t j = 0; j < n; j += NB) {
     const int jb = (int)std::min<int64_t>(NB, n - j);
     const int64_t R = m - j;
@@ -287,7 +284,7 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
     pa.diagR = f.diagR + j;
     pa.part = part;
     pa.gram = gram;
-    pa.alpha_slot = alpha_slot;
+    pa.row_slot = row_slot;
     QDWHP_TRY(launch_panel(st, pa));
     const int64_t nc = n - j - jb;
     if (nc > 0) {

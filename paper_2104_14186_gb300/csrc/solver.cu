@@ -81,7 +81,9 @@ qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh) 
   return QDWHP_OK;
 }
 
-constexpr double kEps = 0x1.0p-52;
+// Stopping tolerance of the reduced-problem Jacobi when its vectors are used: the
+// normalised off-diagonal inner products (computed in double-double) down to ~2u.
+constexpr double kJacobiTight = 4.5e-16;
 
 struct Common {
   // small-problem and control buffers shared by both drivers
@@ -187,15 +189,19 @@ void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
 
 // Eigenvalues (Rayleigh quotients, into w.c.vals) and eigenvectors (S3) of the
 // symmetric ell x ell matrix in S1, whose spectrum lies above `lower`.
+// `values_only`: only the eigenvalues are used, and those are accurate to the square of
+// the Jacobi off-diagonal tolerance, so a loose tolerance (1e-9) is enough.
 qdwhp_status small_sym_eig(cudaStream_t st, int64_t ell, double lower, EigWs& w, int max_sweeps, HostScalars& hs,
-                           int* sweeps) {
+                           int* sweeps, bool values_only = false) {
   QDWHP_TRY(symmetrize_avg(st, ell, w.S1, ell));
   // G = M - lower I is positive semidefinite; its right singular vectors are M's eigenvectors.
   QDWHP_TRY(axpby(st, ell, ell, 1.0, w.S1, ell, 0.0, w.S2, ell, -lower));
   int conv = 0;
-  const double tol = kEps * std::sqrt((double)std::max<int64_t>(ell, 1));
+  const double tol = values_only ? 1e-9 : kJacobiTight;
   QDWHP_TRY(jacobi_onesided(st, ell, ell, w.S2, ell, w.S3, ell, max_sweeps, tol, w.c.jst, &hs.jst, sweeps, &conv));
   if (!conv) return QDWHP_ERR_NOT_CONVERGED;
+  // The accumulated rotations drift the column norms by O(rotations * u): rescale.
+  QDWHP_TRY(normalize_columns(st, ell, ell, w.S3, ell, nullptr));
   // Rayleigh quotients v_i^T M v_i
   QDWHP_TRY(gemm(st, false, false, ell, ell, ell, 1.0, w.S1, ell, w.S3, ell, 0.0, w.S2, ell));
   return column_dots(st, ell, ell, w.S3, ell, w.S2, ell, w.c.vals);
@@ -252,7 +258,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   QDWHP_TRY(gemm(st, false, false, n, b, n, eps_side, A, lda, Qb, n, 0.0, AQ, n));
   QDWHP_TRY(gemm(st, true, false, b, b, n, 1.0, Qb, n, AQ, n, 0.0, w.S1, b, FULL, 0.0, w.c.splitk, w.c.splitk_elems));
   int sweeps = 0;
-  QDWHP_TRY(small_sym_eig(st, b, lam_lo, w, o.jacobi_max_sweeps, hs, &sweeps));
+  QDWHP_TRY(small_sym_eig(st, b, lam_lo, w, o.jacobi_max_sweeps, hs, &sweeps, true));
   QDWHP_TRY(select_sort(st, b, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
   QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
@@ -400,7 +406,8 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   QDWHP_TRY(gemm(st, true, false, b, b, m, 1.0, w.C, m, w.C, m, 0.0, H, b, FULL, 0.0, w.c.splitk, w.c.splitk_elems));
   QDWHP_TRY(symmetrize_avg(st, b, H, b));
   int sweeps = 0, conv = 0;
-  const double tol_b = kEps * std::sqrt((double)b);
+  // values only: eigenvalue errors are of the order of the squared off-diagonal tolerance
+  const double tol_b = 1e-9;
   QDWHP_TRY(jacobi_onesided(st, b, b, H, b, w.Vj, b, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst, &sweeps, &conv));
   if (!conv) return QDWHP_ERR_NOT_CONVERGED;
   QDWHP_TRY(column_norms(st, b, b, H, b, w.c.vals));
@@ -459,9 +466,8 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
       QDWHP_TRY(gemm(st, false, false, m, ell, n, 1.0, A, lda, Q2, n, 0.0, w.C, m));
       QDWHP_TRY(geqrf(st, m, ell, w.C, m, w.q.qf, w.q.qr_scratch));
       QDWHP_TRY(copy_upper(st, ell, w.C, m, w.W, ell));
-      const double tol = kEps * std::sqrt((double)ell);
-      QDWHP_TRY(jacobi_onesided(st, ell, ell, w.W, ell, w.Vj, ell, o.jacobi_max_sweeps, tol, w.c.jst, &hs.jst, &sweeps,
-                                &conv));
+      QDWHP_TRY(jacobi_onesided(st, ell, ell, w.W, ell, w.Vj, ell, o.jacobi_max_sweeps, kJacobiTight, w.c.jst,
+                                &hs.jst, &sweeps, &conv));
       if (!conv) return QDWHP_ERR_NOT_CONVERGED;
       inf.jacobi_sweeps = sweeps;
       QDWHP_TRY(column_norms(st, ell, ell, w.W, ell, w.c.vals));
@@ -475,13 +481,17 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     s = std::max(0.5 * s, 1e-15);
   }
   if (count < k) return QDWHP_ERR_COUNT;
-  // Step 8: U1 = Q_C [W_sel Sigma_sel^{-1}; 0], V1 = Q2 Vj_sel.
+  // Step 8: U1 = Q_C [W_sel Sigma_sel^{-1}; 0] with the Jacobi-rotated columns of R (which
+  // stay orthogonal to high relative accuracy even for small sigma), V1 = Q2 V~1 with the
+  // selected rotation columns rescaled to unit norm (rotation rounding drifts their norms).
+  double* Vsel = w.X;               // ell x k
   QDWHP_TRY(gather_values(st, k, w.c.vals, w.c.order, sigma));
   QDWHP_TRY(gather_columns(st, ell, k, w.W, ell, w.c.order, w.c.vals, U, ldu));
   if (m > ell) QDWHP_TRY(set_matrix(st, m - ell, k, 0.0, 0.0, U + ell, ldu));
   QDWHP_TRY(ormqr_left(st, w.q.qf, U, k, ldu, w.q.qr_scratch));
-  QDWHP_TRY(gather_columns(st, ell, k, w.Vj, ell, w.c.order, nullptr, w.X, ell));
-  QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, w.X, ell, 0.0, V, ldv));
+  QDWHP_TRY(gather_columns(st, ell, k, w.Vj, ell, w.c.order, nullptr, Vsel, ell));
+  QDWHP_TRY(normalize_columns(st, ell, k, Vsel, ell, nullptr));
+  QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, Vsel, ell, 0.0, V, ldv));
   inf.ms_total = timer.stop();
   inf.retries = retries;
   inf.ell = ell;

@@ -128,3 +128,13 @@ def test_nonfinite_input_is_reported(Q):
     with pytest.raises(Q.QdwhpError) as e:
         Q.eig(dev(A), k=3)
     assert e.value.status == -5
+
+
+def test_svd_full_size_workload(Q):
+    """The benchmark workload at full size (4096 x 4096, sigma log-spaced 1..1e-12, top 5 %,
+    k = 205) in the launch configuration bench.py times, against the oracle and sigma*."""
+    q = I.svd_logspaced(4096, 4096, 2000, 0.05)
+    r = Q.svd(dev(q.A), k=q.k)
+    ref = O.qdwhp_svd(q.A, O.SvdOptions(k=q.k))
+    check_svd(q, r, ref)
+    assert r.info["it_chol"] == 3 and r.info["it_qr"] == 0
