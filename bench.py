@@ -330,6 +330,49 @@ def run_kernel_gemm(args):
                       "alg_bytes": 3 * n * n * 8}), flush=True)
 
 
+def run_eig_large(args):
+    """The n = 16384 EIG workload (clustered spectrum), 1 % or 20 % largest, timed per solve."""
+    import numpy as np
+    import torch
+
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import inputs as I
+    from paper_2104_14186_gb300 import qdwhp as Q
+
+    frac = args.fraction
+    A, lam, k = I.eig_clustered_device(16384, 3000, frac)
+    n = A.shape[0]
+    o = Q.default_opts()
+    ws = Q.workspace(Q.lib().qdwhp_eig_workspace_bytes(n, __import__("ctypes").byref(o)))
+    for _ in range(args.warmup):
+        r = Q.eig(A, k=k, ws=ws)
+    torch.cuda.synchronize()
+    ms = []
+    Q.profile_begin()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = Q.eig(A, k=k, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = Q.profile_end()
+    true = np.sort(lam)[::-1][:k]
+    err = float(np.max(np.abs(r.lam.cpu().numpy() - true)))
+    V = r.V
+    res = (torch.linalg.norm(A @ V - V * r.lam[None, :]) / torch.linalg.norm(A)).item()
+    ell = r.info["ell"]
+    fl = 3 * (n ** 3 + n ** 3 / 3 + 2 * n ** 3) + 4 / 3 * n ** 3 + 4 * n * n * ell + 2 * n * ell ** 2 + 9 * ell ** 3 \
+        + 2 * n * ell * k
+    t = statistics.median(ms) / 1e3
+    print(json.dumps({"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})", "ell": ell,
+                      "ms_median": 1e3 * t, "solves_per_s": 1 / t, "alg_tflops": fl / t / 1e12,
+                      "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9,
+                      "gemm_share": prof["gemm_ms"] / sum(ms), "lam_err": err, "resid": res,
+                      "jacobi_sweeps": r.info["jacobi_sweeps"]}), flush=True)
+
+
 def run_single(args):
     """One untimed solve of the workload: the command the ncu launch-list capture runs."""
     import numpy as np
@@ -358,7 +401,12 @@ def main():
     ap.add_argument("--kernel", choices=["gemm"], default=None,
                     help="time one building block in isolation instead of the full solve")
     ap.add_argument("--single", action="store_true", help="one untimed solve (for profiler launch lists)")
+    ap.add_argument("--eig16384", action="store_true", help="time the n = 16384 clustered EIG workload")
+    ap.add_argument("--fraction", type=float, default=0.01)
     args = ap.parse_args()
+    if args.eig16384:
+        run_eig_large(args)
+        return
     if args.single:
         run_single(args)
         return

@@ -112,3 +112,27 @@ def batch_sizes(count: int, seed: int, lo: int = 64, hi: int = 1024) -> np.ndarr
     """Sizes of the batched workload: `count` sizes drawn uniformly from [lo, hi]."""
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi + 1, size=count)
+
+
+def eig_clustered_device(n: int, seed: int, fraction: float, cluster_frac: float = 0.02, device="cuda"):
+    """The clustered EIG workload built on the GPU (for sizes where a host QR of an n x n
+    Gaussian matrix is too slow): same spectrum recipe as `eig_clustered`, with the
+    Gaussian matrix drawn by torch's CUDA generator (Philox) from `seed` and its
+    Householder QR done by torch.  Returns (A as a CUDA float64 tensor, lam as numpy, k)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    nc = int(round(cluster_frac * n))
+    lam = np.concatenate([rng.uniform(1.0 - 1e-6, 1.0 + 1e-6, nc), rng.uniform(-1.0, 0.9, n - nc)])
+    g = torch.Generator(device=device).manual_seed(seed)
+    G = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+    Q, R = torch.linalg.qr(G)
+    del G
+    d = torch.sign(torch.diagonal(R))
+    d[d == 0] = 1.0
+    Q = Q * d[None, :]
+    del R
+    lam_t = torch.from_numpy(lam).to(device)
+    A = (Q * lam_t[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    return A.contiguous(), lam, k_from_fraction(n, fraction)

@@ -1,0 +1,48 @@
+"""The n = 16384 EIG workload (2 % of the eigenvalues in 1 +- 1e-6, the rest uniform in
+[-1, 0.9]; 1 % and 20 % largest) at full size, in the launch configuration of the solver.
+The CPU oracle cannot run at this size, so the checks are the ones that hold at any
+size: the eigenvalues against the constructed spectrum, orthogonality and the residual
+(computed on the GPU in FP64)."""
+
+import numpy as np
+import pytest
+
+from paper_2104_14186_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def Q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp
+    return qdwhp
+
+
+@pytest.fixture(scope="module")
+def problem():
+    A, lam, _ = I.eig_clustered_device(16384, 3000, 0.01)
+    return A, lam
+
+
+@pytest.mark.parametrize("fraction", [0.01, 0.20])
+def test_eig_16384_clustered(Q, problem, fraction):
+    A, lam = problem
+    n = A.shape[0]
+    k = I.k_from_fraction(n, fraction)
+    r = Q.eig(A, k=k)
+    true = np.sort(lam)[::-1][:k]
+    got = r.lam.cpu().numpy()
+    assert got.shape == (k,)
+    assert np.max(np.abs(got - true)) <= 1e-12 * np.max(np.abs(lam))
+    V = r.V
+    orth = torch.linalg.norm(V.T @ V - torch.eye(k, dtype=torch.float64, device=V.device)).item()
+    res = (torch.linalg.norm(A @ V - V * r.lam[None, :]) / torch.linalg.norm(A)).item()
+    assert orth <= 5e-15 * n, orth
+    assert res <= 1e-13, res
+    assert r.info["ell"] >= k
