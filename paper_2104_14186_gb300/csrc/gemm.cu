@@ -15,6 +15,7 @@ namespace {
 
 constexpr int kBK = 16;
 constexpr int kChunk = 64;      // K slice summed separately before joining the accumulator
+constexpr int kGroupM = 16;     // tile rows per raster group
 constexpr int kThreads = 128;   // 2 x 2 warps
 
 __device__ __forceinline__ void dmma884(double (&c)[2], double a, double b) {
@@ -35,7 +36,18 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(int M, int N, int K, in
   __shared__ double As[kBK][BM + 8];
   __shared__ double Bs[kBK][BN + 8];
 
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // Grouped raster order over a 1-D grid: consecutive CTAs walk down kGroupM tile rows
+  // before moving one tile column right, so the CTAs resident at any time touch a
+  // narrow band of A and B that stays in L2 (row-major order re-streams all of A for
+  // every tile column once A exceeds L2).
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int pid = blockIdx.x;
+  const int group = pid / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int gsize = min(tiles_m - first_m, kGroupM);
+  const int tm = first_m + (pid % (kGroupM * tiles_n)) % gsize;
+  const int tn = (pid % (kGroupM * tiles_n)) / gsize;
+  const int m0 = tm * BM, n0 = tn * BN;
   if (uplo == LOWER && m0 + BM <= n0) return;   // tile strictly above the diagonal
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
@@ -214,7 +226,7 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   int kchunk = (K + split - 1) / split;
   kchunk = ((kchunk + kBK - 1) / kBK) * kBK;
   if (split > 1) split = (K + kchunk - 1) / kchunk;
-  dim3 grid(ceil_div(M, BM), ceil_div(N, BN), split);
+  dim3 grid(ceil_div(M, BM) * ceil_div(N, BN), 1, split);
   double* partial = split > 1 ? splitk_ws : nullptr;
   // algorithmic flops: 2 m n k, or n (n + 1) k for the lower triangle only
   const double flops = (uplo == LOWER) ? (double)N * (N + 1) * K : 2.0 * M * N * K;

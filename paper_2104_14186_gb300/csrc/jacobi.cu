@@ -3,7 +3,7 @@
 //
 // A sweep visits every column pair once in the round-robin ("circle method")
 // order: nc - 1 rounds of nc / 2 disjoint pairs (a dummy column pads odd nc).  The
-// pairs of a round are independent: a CTA takes a pair, forms ||g_p||^2, ||g_q||^2
+// pairs of a round are independent: a warp takes a pair, forms ||g_p||^2, ||g_q||^2
 // and g_p^T g_q, and applies the plane rotation that makes the two columns
 // orthogonal to G and to the accumulated Vj.  A whole sweep is one cooperative
 // launch with a grid barrier between rounds.
@@ -33,10 +33,15 @@ __device__ __forceinline__ void pair_of(int r, int h, int N, int& p, int& q) {
 }
 
 // Orthogonalise columns p and q of G (length mg) and rotate the same columns of Vj
-// (length nc).  `red`, `rot` and `flag` are shared scratch of the calling CTA; all
-// threads of the CTA call this together.
-__device__ void rotate_pair(int p, int q, int mg, int nc, double* G, int64_t ldg, double* Vj, int64_t ldv, double tol,
-                            JacobiState* jst, double (*red)[32], double* rot, int* flag) {
+// (length nc), by one warp: the lanes stride over the rows, the sums are combined with
+// shuffles, lane 0 forms the rotation and broadcasts it.  ||g_p||^2 and ||g_q||^2 are
+// summed plainly; g_p^T g_q, which decides convergence and goes to zero, is summed in
+// double-double (TwoProduct and TwoSum) once the sweep is near convergence (comp != 0),
+// so that it is accurate far below sqrt(mg) u and the stopping test can ask for
+// orthogonality at the level of u.
+__device__ void rotate_pair_warp(int p, int q, int mg, int nc, double* G, int64_t ldg, double* Vj, int64_t ldv,
+                                 double tol, int comp, JacobiState* jst) {
+  const int lane = threadIdx.x & 31;
   if (p > q) {
     const int t = p;
     p = q;
@@ -44,115 +49,108 @@ __device__ void rotate_pair(int p, int q, int mg, int nc, double* G, int64_t ldg
   }
   double* gp = G + (int64_t)p * ldg;
   double* gq = G + (int64_t)q * ldg;
-  // ||g_p||^2 and ||g_q||^2 plainly; g_p^T g_q, which decides convergence and goes to
-  // zero, in double-double (TwoProduct and TwoSum) so that it is accurate far below
-  // sqrt(mg) u and the stopping test can ask for orthogonality at the level of u.
   double a = 0.0, b = 0.0, c = 0.0, ce = 0.0;
-  for (int i = threadIdx.x; i < mg; i += blockDim.x) {
-    const double x = gp[i], y = gq[i];
-    a += x * x;
-    b += y * y;
-    const double pr = x * y;
-    const double pe = fma(x, y, -pr);
-    const double t = c + pr;
-    const double z = t - c;
-    ce += ((c - (t - z)) + (pr - z)) + pe;
-    c = t;
+  if (comp) {
+    for (int i = lane; i < mg; i += 32) {
+      const double x = gp[i], y = gq[i];
+      a = fma(x, x, a);
+      b = fma(y, y, b);
+      const double pr = x * y;
+      const double pe = fma(x, y, -pr);
+      const double t = c + pr;
+      const double z = t - c;
+      ce += ((c - (t - z)) + (pr - z)) + pe;
+      c = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double c2 = __shfl_xor_sync(0xffffffffu, c, o), e2 = __shfl_xor_sync(0xffffffffu, ce, o);
+      const double t = c + c2;
+      const double z = t - c;
+      ce += e2 + ((c - (t - z)) + (c2 - z));
+      c = t;
+    }
+    c += ce;
+  } else {
+    for (int i = lane; i < mg; i += 32) {
+      const double x = gp[i], y = gq[i];
+      a = fma(x, x, a);
+      b = fma(y, y, b);
+      c = fma(x, y, c);
+    }
+    c = warp_sum(c);
   }
   a = warp_sum(a);
   b = warp_sum(b);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double c2 = __shfl_xor_sync(0xffffffffu, c, o), e2 = __shfl_xor_sync(0xffffffffu, ce, o);
-    const double t = c + c2;
-    const double z = t - c;
-    ce += e2 + ((c - (t - z)) + (c2 - z));
-    c = t;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int do_rot = 0;
+  double cs = 1.0, sn = 0.0;
   if (lane == 0) {
-    red[0][wid] = a;
-    red[1][wid] = b;
-    red[2][wid] = c;
-    red[3][wid] = ce;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-    double sa = 0.0, sb = 0.0, sc = 0.0, se = 0.0;
-    for (int w = 0; w < nw; ++w) {
-      sa += red[0][w];
-      sb += red[1][w];
-      const double t = sc + red[2][w];
-      const double z = t - sc;
-      se += red[3][w] + ((sc - (t - z)) + (red[2][w] - z));
-      sc = t;
-    }
-    sc += se;
-    *flag = 1;   // skip
-    if (!isfinite(sa) || !isfinite(sb) || !isfinite(sc)) {
+    if (!isfinite(a) || !isfinite(b) || !isfinite(c)) {
       atomicExch(&jst->nonfinite, 1);
-    } else if (sa > 0.0 && sb > 0.0 && sc != 0.0) {
-      const double off = fabs(sc) / sqrt(sa * sb);
+    } else if (a > 0.0 && b > 0.0 && c != 0.0) {
+      const double off = fabs(c) / sqrt(a * b);
       atomicMax(&jst->max_off_bits, (unsigned long long)__double_as_longlong(off));
       if (off > tol) {
-        const double zeta = (sb - sa) / (2.0 * sc);
+        const double zeta = (b - a) / (2.0 * c);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t);
-        rot[0] = cs;
-        rot[1] = cs * t;
-        *flag = 0;
+        cs = 1.0 / sqrt(1.0 + t * t);
+        sn = cs * t;
+        do_rot = 1;
       }
     }
   }
-  __syncthreads();
-  if (*flag == 0) {
-    const double cs = rot[0], sn = rot[1];
-    for (int i = threadIdx.x; i < mg; i += blockDim.x) {
-      const double x = gp[i], y = gq[i];
-      gp[i] = cs * x - sn * y;
-      gq[i] = sn * x + cs * y;
-    }
-    double* vp = Vj + (int64_t)p * ldv;
-    double* vq = Vj + (int64_t)q * ldv;
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-      const double x = vp[i], y = vq[i];
-      vp[i] = cs * x - sn * y;
-      vq[i] = sn * x + cs * y;
-    }
+  do_rot = __shfl_sync(0xffffffffu, do_rot, 0);
+  if (!do_rot) return;
+  cs = __shfl_sync(0xffffffffu, cs, 0);
+  sn = __shfl_sync(0xffffffffu, sn, 0);
+  for (int i = lane; i < mg; i += 32) {
+    const double x = gp[i], y = gq[i];
+    gp[i] = cs * x - sn * y;
+    gq[i] = sn * x + cs * y;
   }
-  __syncthreads();
+  double* vp = Vj + (int64_t)p * ldv;
+  double* vq = Vj + (int64_t)q * ldv;
+  for (int i = lane; i < nc; i += 32) {
+    const double x = vp[i], y = vq[i];
+    vp[i] = cs * x - sn * y;
+    vq[i] = sn * x + cs * y;
+  }
 }
 
-// One full sweep (N - 1 rounds) in one cooperative launch: the CTAs share the pairs of
-// a round and meet at a grid barrier between rounds.
-__global__ void __launch_bounds__(256) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg, double* Vj,
-                                                           int64_t ldv, double tol, JacobiState* jst) {
+// One full sweep (N - 1 rounds) in one cooperative launch: every warp takes pairs of the
+// round, and the grid meets at a barrier between rounds.
+constexpr int kSweepThreads = 32;   // one warp per CTA: a round's pairs spread over all SMs
+__global__ void __launch_bounds__(kSweepThreads) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg,
+                                                                     double* Vj, int64_t ldv, double tol, int comp,
+                                                                     JacobiState* jst) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ double red[4][32];
-  __shared__ double rot[2];
-  __shared__ int flag;
+  const int wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nw = gridDim.x * wpb;
   for (int r = 0; r < N - 1; ++r) {
-    for (int h = blockIdx.x; h < N / 2; h += gridDim.x) {
+    for (int h = gw; h < N / 2; h += nw) {
       int p, q;
       pair_of(r, h, N, p, q);
-      if (p < nc && q < nc) rotate_pair(p, q, mg, nc, G, ldg, Vj, ldv, tol, jst, red, rot, &flag);
+      if (p < nc && q < nc) rotate_pair_warp(p, q, mg, nc, G, ldg, Vj, ldv, tol, comp, jst);
     }
     grid.sync();
   }
 }
 
+// CTAs for a sweep: enough warps for one pair each, capped at what is co-resident.
 int sweep_grid(int pairs) {
   static int max_blocks = 0;
   if (max_blocks == 0) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, 256, 0) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, kSweepThreads, 0) != cudaSuccess ||
+        per_sm < 1)
       per_sm = 1;
     int dev = 0, sms = kNumSMs;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    max_blocks = std::min(per_sm, 2) * sms;
+    max_blocks = std::min(per_sm, 8) * sms;
   }
-  return std::max(1, std::min(pairs, max_blocks));
+  const int want = (pairs + kSweepThreads / 32 - 1) / (kSweepThreads / 32);
+  return std::max(1, std::min(want, max_blocks));
 }
 
 __global__ void column_norms_kernel(int mg, const double* G, int64_t ldg, double* norms) {
@@ -234,8 +232,11 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     QDWHP_CUDA_TRY(cudaMemsetAsync(jst_dev, 0, sizeof(JacobiState), st));
     int mg_i = (int)mg, nc_i = (int)nc, N_i = N;
-    void* args[] = {&mg_i, &nc_i, &N_i, &G, &ldg, &Vj, &ldv, &tol, &jst_dev};
-    QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(256), args, 0, st));
+    // compensated inner products only when they matter: a tight target, near convergence
+    int comp = (tol < 1e-13 && prev < 1e-8) ? 1 : 0;
+    void* args[] = {&mg_i, &nc_i, &N_i, &G, &ldg, &Vj, &ldv, &tol, &comp, &jst_dev};
+    QDWHP_CUDA_TRY(
+        cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(kSweepThreads), args, 0, st));
     QDWHP_LAUNCH_CHECK();
     QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
     QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
