@@ -196,8 +196,9 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    sopts = {"precision": Q.MIXED if args.precision == "mixed" else Q.FP64, "refine_steps": args.refine}
     for _ in range(args.warmup):
-        r = Q.svd(A, k=k, ws=ws)
+        r = Q.svd(A, k=k, ws=ws, **sopts)
     torch.cuda.synchronize()
 
     # ---- timed region: inputs resident in HBM ----
@@ -212,7 +213,7 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        r = Q.svd(A, k=k, ws=ws)
+        r = Q.svd(A, k=k, ws=ws, **sopts)
         ev[i][1].record(stream)
         infos.append(r.info)
     torch.cuda.synchronize()
@@ -236,7 +237,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        rh = Q.svd(A_host, k=k, ws=ws, device=dev)
+        rh = Q.svd(A_host, k=k, ws=ws, device=dev, **sopts)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_total = sum(e2e_ms)
     if world > 1:
@@ -249,6 +250,14 @@ def run_ours(args):
 
     info = infos[-1]
     fl = svd_flops(M, N, info["ell"], k, info["it_qr"], info["it_chol"])
+    # accuracy of this result against sigma* and the residuals (FP64, outside the timed region)
+    sig_true = torch.from_numpy(p.sigma[:k]).to(dev)
+    nA = torch.linalg.norm(A)
+    acc = {"sigma_err": (torch.max(torch.abs(r.sigma - sig_true)) / sig_true[0]).item(),
+           "residV": (torch.linalg.norm(A @ r.V - r.U * r.sigma[None, :]) / nA).item(),
+           "residU": (torch.linalg.norm(A.T @ r.U - r.V * r.sigma[None, :]) / nA).item(),
+           "orthU": torch.linalg.norm(r.U.T @ r.U - torch.eye(k, dtype=torch.float64, device=dev)).item(),
+           "orthV": torch.linalg.norm(r.V.T @ r.V - torch.eye(k, dtype=torch.float64, device=dev)).item()}
     peaks = load_peaks()
     bf16 = peaks.get("bf16_tflops")
     peak = bf16 * NOMINAL_FP64_OVER_BF16 if bf16 else 1.9e3 * NOMINAL_FP64_OVER_BF16
@@ -256,7 +265,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(k),
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic", "config": dict(workload_config(k), precision=args.precision, refine_steps=args.refine),
+        "accuracy": acc,
         "tflops": fl / (total_ms / args.steps / 1e3) / 1e12,
         "tflops_frac_of_fp64_peak": fl / (total_ms / args.steps / 1e3) / 1e12 / peak,
         "solve": {"ell": info["ell"], "it_qr": info["it_qr"], "it_chol": info["it_chol"], "s": info["s"],
@@ -398,6 +409,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--refine", type=int, default=0, help="FP64 refinement steps on Q2 (SVD)")
     ap.add_argument("--kernel", choices=["gemm"], default=None,
                     help="time one building block in isolation instead of the full solve")
     ap.add_argument("--single", action="store_true", help="one untimed solve (for profiler launch lists)")

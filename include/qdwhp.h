@@ -59,7 +59,8 @@ typedef struct {
   int64_t count;          /* wanted count k; 0 = use `fraction` */
   double fraction;        /* k = ceil(fraction * n) (clamped to [1, n]) when count == 0 */
   int32_t side;           /* qdwhp_side (EIG only; SVD always returns the largest) */
-  int32_t precision;      /* qdwhp_precision (QDWHP_FP64; QDWHP_MIXED is rejected with ERR_ARG) */
+  int32_t precision;      /* qdwhp_precision: QDWHP_FP64, or QDWHP_MIXED (every Cholesky-based QDWH step
+                             but the last in FP32; all else FP64) */
   double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
   int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */
   int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
@@ -71,6 +72,8 @@ typedef struct {
   int32_t max_retries;    /* re-runs with a wider threshold if < k pairs are captured (2) */
   int32_t jacobi_max_sweeps; /* sweep limit of the reduced-problem Jacobi solver (30) */
   uint64_t seed;          /* seed of the SplitMix64 start vectors */
+  int32_t refine_steps;   /* SVD: FP64 subspace-iteration steps on Q2, Q2 <- orth(A^T A Q2), before the
+                             projection (default 0; for QDWHP_MIXED they restore FP64-level vectors) */
 } qdwhp_opts;
 
 /* Per-solve report (host struct, filled when the pointer is non-NULL). */
@@ -88,6 +91,7 @@ typedef struct {
   double ell_k[12];       /* ell_k after each QDWH step */
   double conv[12];        /* ||X_k - X_{k-1}||_F after each QDWH step */
   float ms_total;         /* device time of the solve (CUDA events) */
+  int32_t it_f32;         /* Cholesky-based steps run in FP32 (QDWHP_MIXED) */
 } qdwhp_info;
 
 QDWHP_API void qdwhp_default_opts(qdwhp_opts* opts);

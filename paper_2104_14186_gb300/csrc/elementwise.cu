@@ -11,42 +11,53 @@ inline int grid_for(size_t total) {
   return (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 8 * (size_t)kNumSMs));
 }
 
-__global__ void axpby_kernel(int M, int N, double alpha, const double* X, int64_t ldx, double beta, double* Y,
-                             int64_t ldy, double diag_add) {
+template <typename T>
+__global__ void axpby_kernel(int M, int N, T alpha, const T* X, int64_t ldx, T beta, T* Y, int64_t ldy, T diag_add) {
   const size_t total = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % M), j = (int)(e / M);
-    double v = alpha * X[i + (int64_t)j * ldx];
-    double* yp = Y + i + (int64_t)j * ldy;
-    if (beta != 0.0) v += beta * (*yp);
+    T v = alpha * X[i + (int64_t)j * ldx];
+    T* yp = Y + i + (int64_t)j * ldy;
+    if (beta != T(0)) v += beta * (*yp);
     if (i == j) v += diag_add;
     *yp = v;
   }
 }
 
-__global__ void axpby_diff_kernel(int M, int N, double a, double* Y, int64_t ldy, double b, const double* Z,
-                                  int64_t ldz, double* diff_part) {
+template <typename T>
+__global__ void axpby_diff_kernel(int M, int N, T a, T* Y, int64_t ldy, T b, const T* Z, int64_t ldz,
+                                  double* diff_part) {
   __shared__ double red[32];
   const size_t total = (size_t)M * N;
   double acc = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % M), j = (int)(e / M);
-    double* yp = Y + i + (int64_t)j * ldy;
-    const double old = *yp;
-    const double nw = a * old + b * Z[i + (int64_t)j * ldz];
+    T* yp = Y + i + (int64_t)j * ldy;
+    const T old = *yp;
+    const T nw = a * old + b * Z[i + (int64_t)j * ldz];
     *yp = nw;
-    const double d = nw - old;
+    const double d = (double)nw - (double)old;
     acc += d * d;
   }
   acc = block_sum(acc, red);
   if (diff_part != nullptr && threadIdx.x == 0) diff_part[blockIdx.x] = acc;
 }
 
-__global__ void set_kernel(int M, int N, double off, double diag, double* Y, int64_t ldy) {
+template <typename T>
+__global__ void set_kernel(int M, int N, T off, T diag, T* Y, int64_t ldy) {
   const size_t total = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % M), j = (int)(e / M);
     Y[i + (int64_t)j * ldy] = (i == j) ? diag : off;
+  }
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(int M, int N, const S* X, int64_t ldx, D* Y, int64_t ldy) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    Y[i + (int64_t)j * ldy] = (D)X[i + (int64_t)j * ldx];
   }
 }
 
@@ -87,38 +98,87 @@ __global__ void nonfinite_kernel(int M, int N, const double* X, int64_t ldx, uns
 
 }  // namespace
 
+template <typename T>
+qdwhp_status axpby_t(cudaStream_t st, int64_t m, int64_t n, T alpha, const T* X, int64_t ldx, T beta, T* Y,
+                     int64_t ldy, T diag_add) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  axpby_kernel<T><<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, alpha, X, ldx, beta, Y, ldy, diag_add);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
 qdwhp_status axpby(cudaStream_t st, int64_t m, int64_t n, double alpha, const double* X, int64_t ldx, double beta,
                    double* Y, int64_t ldy, double diag_add) {
+  return axpby_t<double>(st, m, n, alpha, X, ldx, beta, Y, ldy, diag_add);
+}
+qdwhp_status axpby(cudaStream_t st, int64_t m, int64_t n, float alpha, const float* X, int64_t ldx, float beta,
+                   float* Y, int64_t ldy, float diag_add) {
+  return axpby_t<float>(st, m, n, alpha, X, ldx, beta, Y, ldy, diag_add);
+}
+
+template <typename T>
+qdwhp_status axpby_diff_t(cudaStream_t st, int64_t m, int64_t n, T a, T* Y, int64_t ldy, T b, const T* Z,
+                          int64_t ldz, double* diff_part) {
   if (m <= 0 || n <= 0) return QDWHP_OK;
-  axpby_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, alpha, X, ldx, beta, Y, ldy, diag_add);
+  // Exactly kDiffParts blocks so that every partial slot is written.
+  axpby_diff_kernel<T><<<kDiffParts, 256, 0, st>>>((int)m, (int)n, a, Y, ldy, b, Z, ldz, diff_part);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }
 
 qdwhp_status axpby_diff(cudaStream_t st, int64_t m, int64_t n, double a, double* Y, int64_t ldy, double b,
                         const double* Z, int64_t ldz, double* diff_part) {
+  return axpby_diff_t<double>(st, m, n, a, Y, ldy, b, Z, ldz, diff_part);
+}
+qdwhp_status axpby_diff(cudaStream_t st, int64_t m, int64_t n, float a, float* Y, int64_t ldy, float b,
+                        const float* Z, int64_t ldz, double* diff_part) {
+  return axpby_diff_t<float>(st, m, n, a, Y, ldy, b, Z, ldz, diff_part);
+}
+
+template <typename T>
+qdwhp_status copy_matrix_t(cudaStream_t st, int64_t m, int64_t n, const T* X, int64_t ldx, T* Y, int64_t ldy) {
   if (m <= 0 || n <= 0) return QDWHP_OK;
-  // Exactly kDiffParts blocks so that every partial slot is written.
-  axpby_diff_kernel<<<kDiffParts, 256, 0, st>>>((int)m, (int)n, a, Y, ldy, b, Z, ldz, diff_part);
-  QDWHP_LAUNCH_CHECK();
+  if (ldx == m && ldy == m) {
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(Y, X, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, st));
+    return QDWHP_OK;
+  }
+  QDWHP_CUDA_TRY(cudaMemcpy2DAsync(Y, sizeof(T) * ldy, X, sizeof(T) * ldx, sizeof(T) * m, n,
+                                   cudaMemcpyDeviceToDevice, st));
   return QDWHP_OK;
 }
 
 qdwhp_status copy_matrix(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx, double* Y,
                          int64_t ldy) {
+  return copy_matrix_t<double>(st, m, n, X, ldx, Y, ldy);
+}
+qdwhp_status copy_matrix(cudaStream_t st, int64_t m, int64_t n, const float* X, int64_t ldx, float* Y, int64_t ldy) {
+  return copy_matrix_t<float>(st, m, n, X, ldx, Y, ldy);
+}
+
+template <typename T>
+qdwhp_status set_matrix_t(cudaStream_t st, int64_t m, int64_t n, T off, T diag, T* Y, int64_t ldy) {
   if (m <= 0 || n <= 0) return QDWHP_OK;
-  if (ldx == m && ldy == m) {
-    QDWHP_CUDA_TRY(cudaMemcpyAsync(Y, X, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, st));
-    return QDWHP_OK;
-  }
-  QDWHP_CUDA_TRY(cudaMemcpy2DAsync(Y, sizeof(double) * ldy, X, sizeof(double) * ldx, sizeof(double) * m, n,
-                                   cudaMemcpyDeviceToDevice, st));
+  set_kernel<T><<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, off, diag, Y, ldy);
+  QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }
 
 qdwhp_status set_matrix(cudaStream_t st, int64_t m, int64_t n, double off, double diag, double* Y, int64_t ldy) {
+  return set_matrix_t<double>(st, m, n, off, diag, Y, ldy);
+}
+qdwhp_status set_matrix(cudaStream_t st, int64_t m, int64_t n, float off, float diag, float* Y, int64_t ldy) {
+  return set_matrix_t<float>(st, m, n, off, diag, Y, ldy);
+}
+
+qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx, float* Y, int64_t ldy) {
   if (m <= 0 || n <= 0) return QDWHP_OK;
-  set_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, off, diag, Y, ldy);
+  convert_kernel<double, float><<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, X, ldx, Y, ldy);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const float* X, int64_t ldx, double* Y, int64_t ldy) {
+  if (m <= 0 || n <= 0) return QDWHP_OK;
+  convert_kernel<float, double><<<grid_for((size_t)m * n), 256, 0, st>>>((int)m, (int)n, X, ldx, Y, ldy);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

@@ -246,4 +246,112 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   return QDWHP_OK;
 }
 
+namespace {
+
+// FP32 GEMM on the CUDA cores (FFMA), for the reduced-precision QDWH steps.  64 x 64 CTA
+// tiles, 256 threads, 4 x 4 outputs per thread in a strided layout (rows ty + 16 i,
+// columns tx + 16 j) so that the shared-memory reads of a warp are broadcasts.
+constexpr int kSBK = 16;
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, float alpha, const float* A, int64_t lda,
+                                                    const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                                                    int uplo, float diag_add) {
+  constexpr int BM = 64, BN = 64;
+  __shared__ float As[kSBK][BM + 4];
+  __shared__ float Bs[kSBK][BN + 4];
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int pid = blockIdx.x;
+  const int group = pid / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int gsize = min(tiles_m - first_m, kGroupM);
+  const int tm = first_m + (pid % (kGroupM * tiles_n)) % gsize;
+  const int tn = (pid % (kGroupM * tiles_n)) / gsize;
+  const int m0 = tm * BM, n0 = tn * BN;
+  if (uplo == LOWER && m0 + BM <= n0) return;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  float ra[4], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + 256 * r;
+      const int i = TA ? e / kSBK : e % BM;
+      const int kk = TA ? e % kSBK : e / BM;
+      const int gi = m0 + i, gk = k0 + kk;
+      float v = 0.f;
+      if (gi < M && gk < K) v = TA ? A[gk + (int64_t)gi * lda] : A[gi + (int64_t)gk * lda];
+      ra[r] = v;
+      const int j = TB ? e % BN : e / kSBK;
+      const int kb = TB ? e / BN : e % kSBK;
+      const int gj = n0 + j, gkb = k0 + kb;
+      float w = 0.f;
+      if (gj < N && gkb < K) w = TB ? B[gj + (int64_t)gkb * ldb] : B[gkb + (int64_t)gj * ldb];
+      rb[r] = w;
+    }
+  };
+  if (K > 0) load(0);
+  for (int k0 = 0; k0 < K; k0 += kSBK) {
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + 256 * r;
+      As[TA ? e % kSBK : e / BM][TA ? e / kSBK : e % BM] = ra[r];
+      Bs[TB ? e / BN : e % kSBK][TB ? e % BN : e / kSBK] = rb[r];
+    }
+    __syncthreads();
+    if (k0 + kSBK < K) load(k0 + kSBK);
+#pragma unroll
+    for (int kk = 0; kk < kSBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = m0 + ty + 16 * i, col = n0 + tx + 16 * j;
+      if (row >= M || col >= N) continue;
+      if (uplo == LOWER && row < col) continue;
+      float v = alpha * acc[i][j];
+      float* cp = C + row + (int64_t)col * ldc;
+      if (beta != 0.f) v += beta * (*cp);
+      if (row == col) v += diag_add;
+      *cp = v;
+    }
+}
+
+}  // namespace
+
+qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                  int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, Uplo uplo,
+                  float diag_add) {
+  if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
+  if (m == 0 || n == 0) return QDWHP_OK;
+  if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return QDWHP_ERR_ARG;
+  const int M = (int)m, N = (int)n, K = (int)k;
+  dim3 grid(ceil_div(M, 64) * ceil_div(N, 64));
+  if (!ta && !tb)
+    sgemm_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add);
+  else if (!ta && tb)
+    sgemm_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add);
+  else if (ta && !tb)
+    sgemm_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add);
+  else
+    sgemm_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
 }  // namespace qdwhp

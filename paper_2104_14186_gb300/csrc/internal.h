@@ -17,6 +17,10 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
                   int64_t ldc, Uplo uplo = FULL, double diag_add = 0.0, double* splitk_ws = nullptr,
                   size_t splitk_ws_elems = 0);
 size_t gemm_splitk_ws_elems(int64_t m, int64_t n);
+// FP32 on the CUDA cores (reduced-precision QDWH steps).
+qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                  int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, Uplo uplo = FULL,
+                  float diag_add = 0.0f);
 
 // ---- elementwise.cu ----
 // Y = alpha X + beta Y (+ diag_add on the diagonal); beta == 0 never reads Y.
@@ -31,6 +35,15 @@ qdwhp_status copy_matrix(cudaStream_t st, int64_t m, int64_t n, const double* X,
                          int64_t ldy);
 qdwhp_status set_matrix(cudaStream_t st, int64_t m, int64_t n, double offdiag, double diag, double* Y,
                         int64_t ldy);
+// FP32 versions (reduced-precision QDWH steps) and precision conversion.
+qdwhp_status axpby(cudaStream_t st, int64_t m, int64_t n, float alpha, const float* X, int64_t ldx, float beta,
+                   float* Y, int64_t ldy, float diag_add = 0.0f);
+qdwhp_status axpby_diff(cudaStream_t st, int64_t m, int64_t n, float a, float* Y, int64_t ldy, float b,
+                        const float* Z, int64_t ldz, double* diff_part);
+qdwhp_status copy_matrix(cudaStream_t st, int64_t m, int64_t n, const float* X, int64_t ldx, float* Y, int64_t ldy);
+qdwhp_status set_matrix(cudaStream_t st, int64_t m, int64_t n, float offdiag, float diag, float* Y, int64_t ldy);
+qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const double* X, int64_t ldx, float* Y, int64_t ldy);
+qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const float* X, int64_t ldx, double* Y, int64_t ldy);
 // R (n x n) = upper triangle of A, zeros below.
 qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr);
 // Fills the lower triangle's mirror: Y(i, j) = Y(j, i) for i < j (n x n).
@@ -55,6 +68,10 @@ qdwhp_status potrf(cudaStream_t st, int64_t n, double* Z, int64_t ldz, double* L
 size_t trsm_scratch_elems(int64_t m, int64_t n);
 qdwhp_status trsm_right_lower(cudaStream_t st, bool trans, int64_t m, int64_t n, double* X, int64_t ldx,
                               const double* L, int64_t ldl, const double* Linv, double* scratch);
+// FP32 versions (reduced-precision QDWH steps).
+qdwhp_status potrf(cudaStream_t st, int64_t n, float* Z, int64_t ldz, float* Linv, float* scratch, int* fail_dev);
+qdwhp_status trsm_right_lower(cudaStream_t st, bool trans, int64_t m, int64_t n, float* X, int64_t ldx,
+                              const float* L, int64_t ldl, const float* Linv, float* scratch);
 
 // ---- qr.cu ----
 constexpr int kQRNB = 32;

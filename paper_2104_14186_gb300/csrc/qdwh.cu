@@ -65,7 +65,7 @@ qdwhp_status dwh_schedule(cudaStream_t st, const double* ell0_dev, double ell0_h
   return QDWHP_OK;
 }
 
-void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w) {
+void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w, bool need_f32) {
   w.m = m;
   w.n = n;
   w.Z = ar.take<double>((size_t)n * n);
@@ -84,6 +84,14 @@ void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w) {
     w.qf.tau = ar.take<double>(n);
     w.qf.diagR = ar.take<double>(n);
     w.qr_scratch = ar.take<double>(qr_scratch_elems(mm, n));
+  }
+  w.has_f32 = need_f32;
+  if (need_f32) {
+    w.X32 = ar.take<float>((size_t)m * n);
+    w.Z32 = ar.take<float>((size_t)n * n);
+    w.Linv32 = ar.take<float>(potrf_linv_elems(n));
+    w.Y32 = ar.take<float>((size_t)m * n);
+    w.scratch32 = ar.take<float>(std::max(potrf_scratch_elems(n), trsm_scratch_elems(m, n)));
   }
 }
 
@@ -114,6 +122,51 @@ qdwhp_status qr_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t l
   QDWHP_TRY(gemm(st, false, true, m, n, n, 1.0, w.S, mm, w.S + m, mm, 0.0, w.Y, m));
   QDWHP_TRY(axpby_diff(st, m, n, b / c, X, ldx, (a - b / c) / sc, w.Y, m, w.diff_parts));
   return reduce_parts(st, w.diff_parts, kDiffParts, w.diff + step);
+}
+
+qdwhp_status chol_step_f32(cudaStream_t st, int64_t m, int64_t n, double a, double b, double c, QdwhWs& w,
+                           int step) {
+  if (!w.has_f32) return QDWHP_ERR_ARG;
+  QDWHP_TRY(gemm(st, true, false, n, n, m, (float)c, w.X32, m, w.X32, m, 0.0f, w.Z32, n, LOWER, 1.0f));
+  QDWHP_TRY(potrf(st, n, w.Z32, n, w.Linv32, w.scratch32, w.fail));
+  QDWHP_TRY(copy_matrix(st, m, n, w.X32, m, w.Y32, m));
+  QDWHP_TRY(trsm_right_lower(st, true, m, n, w.Y32, m, w.Z32, n, w.Linv32, w.scratch32));
+  QDWHP_TRY(trsm_right_lower(st, false, m, n, w.Y32, m, w.Z32, n, w.Linv32, w.scratch32));
+  QDWHP_TRY(axpby_diff(st, m, n, (float)(b / c), w.X32, m, (float)(a - b / c), w.Y32, m, w.diff_parts));
+  return reduce_parts(st, w.diff_parts, kDiffParts, w.diff + step);
+}
+
+qdwhp_status run_schedule(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, const Schedule& sched,
+                          bool mixed, QdwhWs& w, int* n_qr, int* n_chol, int* n_f32) {
+  *n_qr = *n_chol = *n_f32 = 0;
+  int last_chol = -1;
+  for (int i = 0; i < sched.nsteps; ++i)
+    if (!sched.use_qr[i]) last_chol = i;
+  bool in_f32 = false;
+  for (int i = 0; i < sched.nsteps; ++i) {
+    const double a = sched.abc[3 * i], b = sched.abc[3 * i + 1], c = sched.abc[3 * i + 2];
+    const bool low = mixed && !sched.use_qr[i] && i != last_chol;
+    if (low && !in_f32) {
+      QDWHP_TRY(convert(st, m, n, X, ldx, w.X32, m));
+      in_f32 = true;
+    } else if (!low && in_f32) {
+      QDWHP_TRY(convert(st, m, n, w.X32, m, X, ldx));
+      in_f32 = false;
+    }
+    if (sched.use_qr[i]) {
+      QDWHP_TRY(qr_step(st, m, n, X, ldx, a, b, c, w, i));
+      ++*n_qr;
+    } else if (low) {
+      QDWHP_TRY(chol_step_f32(st, m, n, a, b, c, w, i));
+      ++*n_chol;
+      ++*n_f32;
+    } else {
+      QDWHP_TRY(chol_step(st, m, n, X, ldx, a, b, c, w, i));
+      ++*n_chol;
+    }
+  }
+  if (in_f32) QDWHP_TRY(convert(st, m, n, w.X32, m, X, ldx));
+  return QDWHP_OK;
 }
 
 }  // namespace qdwhp

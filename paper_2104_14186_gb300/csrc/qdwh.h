@@ -28,9 +28,16 @@ struct QdwhWs {
   double* S = nullptr;        // (m+n) x n stacked matrix, then its explicit Q
   QRFactors qf;
   double* qr_scratch = nullptr;
+  // FP32 buffers of the reduced-precision Cholesky steps (QDWHP_MIXED)
+  bool has_f32 = false;
+  float* X32 = nullptr;       // m x n
+  float* Z32 = nullptr;       // n x n
+  float* Linv32 = nullptr;
+  float* Y32 = nullptr;       // m x n
+  float* scratch32 = nullptr;
 };
 
-void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w);
+void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w, bool need_f32 = false);
 // Weights from ell_0 (device scalar if ell0_dev != null, else ell0_host); fixed_iters > 0
 // runs exactly that many steps, otherwise until |ell - 1| < 5 eps.
 qdwhp_status dwh_schedule(cudaStream_t st, const double* ell0_dev, double ell0_host, int fixed_iters, double c_qr,
@@ -39,5 +46,12 @@ qdwhp_status chol_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t
                        QdwhWs& w, int step);
 qdwhp_status qr_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, double a, double b, double c,
                      QdwhWs& w, int step);
+// Cholesky-based step in FP32 on w.X32 (m x n, ld m) with FP32 products, factorisation and solves.
+qdwhp_status chol_step_f32(cudaStream_t st, int64_t m, int64_t n, double a, double b, double c, QdwhWs& w, int step);
+// Runs the schedule's steps on X (FP64): QR-based steps in FP64; with `mixed`, every Cholesky-based
+// step but the last in FP32 (X converted down before and back up after), the last in FP64.
+// Returns the number of FP32 steps in *n_f32.
+qdwhp_status run_schedule(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, const Schedule& sched,
+                          bool mixed, QdwhWs& w, int* n_qr, int* n_chol, int* n_f32);
 
 }  // namespace qdwhp

@@ -175,7 +175,7 @@ struct EigWs {
 
 void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   carve_common(ar, n, n, o.lanczos_steps, w.c);
-  carve_qdwh(ar, n, n, false, w.q);
+  carve_qdwh(ar, n, n, false, w.q, o.precision == QDWHP_MIXED);
   w.X = ar.take<double>((size_t)n * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
@@ -279,9 +279,9 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     // Steps 1-2: X0 = (1-s) B / |mu| - s I with B = eps A - t I.
     QDWHP_TRY(axpby(st, n, n, (1.0 - s) * eps_side / absmu, A, lda, 0.0, w.X, n, -((1.0 - s) * t / absmu + s)));
     QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
-    for (int i = 0; i < hs.sched.nsteps; ++i)
-      QDWHP_TRY(chol_step(st, n, n, w.X, n, hs.sched.abc[3 * i], hs.sched.abc[3 * i + 1], hs.sched.abc[3 * i + 2],
-                          w.q, i));
+    int n_qr = 0, n_chol = 0, n_f32 = 0;
+    QDWHP_TRY(run_schedule(st, n, n, w.X, n, hs.sched, o.precision == QDWHP_MIXED, w.q, &n_qr, &n_chol, &n_f32));
+    inf.it_f32 = n_f32;
     // Step 3: QR of (r(A~) + I) / 2.
     QDWHP_TRY(axpby(st, n, n, 0.5, w.X, n, 0.0, w.X, n, 0.5));
     QDWHP_TRY(geqrf(st, n, n, w.X, n, w.f, w.qr_scratch));
@@ -354,7 +354,7 @@ struct SvdWs {
 
 void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
   carve_common(ar, m, n, o.lanczos_steps, w.c);
-  carve_qdwh(ar, m, n, true, w.q);
+  carve_qdwh(ar, m, n, true, w.q, o.precision == QDWHP_MIXED);
   w.X = ar.take<double>((size_t)m * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
@@ -427,17 +427,10 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     // Step 2: QDWH on A / alpha from ell_0 = s.
     QDWHP_TRY(axpby(st, m, n, 1.0 / alpha, A, lda, 0.0, w.X, m));
     QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
-    inf.it_qr = inf.it_chol = 0;
-    for (int i = 0; i < hs.sched.nsteps; ++i) {
-      const double a = hs.sched.abc[3 * i], bb = hs.sched.abc[3 * i + 1], c = hs.sched.abc[3 * i + 2];
-      if (hs.sched.use_qr[i]) {
-        QDWHP_TRY(qr_step(st, m, n, w.X, m, a, bb, c, w.q, i));
-        ++inf.it_qr;
-      } else {
-        QDWHP_TRY(chol_step(st, m, n, w.X, m, a, bb, c, w.q, i));
-        ++inf.it_chol;
-      }
-    }
+    int n_f32 = 0;
+    QDWHP_TRY(run_schedule(st, m, n, w.X, m, hs.sched, o.precision == QDWHP_MIXED, w.q, &inf.it_qr, &inf.it_chol,
+                           &n_f32));
+    inf.it_f32 = n_f32;
     // Step 3: QR of I - X^T X.
     double* B = w.q.Z;
     QDWHP_TRY(gemm(st, true, false, n, n, m, -1.0, w.X, m, w.X, m, 0.0, B, n, LOWER, 1.0));
@@ -463,6 +456,13 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
       // on R: R Vj = W, sigma_i = ||w_i||, so A Q2 = (Q_C W Sigma^{-1}) Sigma Vj^T.
       double* Q2 = w.q.Y;
       QDWHP_TRY(orgqr_columns(st, w.f, ind, ell, Q2, n, w.qr_scratch));
+      // Optional FP64 subspace iteration on Q2 (not in the paper): the components of the wanted
+      // right singular vectors outside span(Q2) shrink by (sigma_out / sigma_k)^2 per step.
+      for (int r = 0; r < o.refine_steps; ++r) {
+        QDWHP_TRY(gemm(st, false, false, m, ell, n, 1.0, A, lda, Q2, n, 0.0, w.C, m));
+        QDWHP_TRY(gemm(st, true, false, n, ell, m, 1.0, A, lda, w.C, m, 0.0, w.X, n));
+        QDWHP_TRY(orth(st, n, ell, w.X, Q2, w.f, w.qr_scratch));
+      }
       QDWHP_TRY(gemm(st, false, false, m, ell, n, 1.0, A, lda, Q2, n, 0.0, w.C, m));
       QDWHP_TRY(geqrf(st, m, ell, w.C, m, w.q.qf, w.q.qr_scratch));
       QDWHP_TRY(copy_upper(st, ell, w.C, m, w.W, ell));
@@ -506,8 +506,9 @@ bool opts_valid(const qdwhp_opts& o) {
   return o.s_eig > 0.0 && o.s_eig < 1.0 && o.iters_eig >= 1 && o.iters_eig <= kMaxSteps && o.tol > 0.0 &&
          o.c_qr > 0.0 && o.block_extra >= 0 && o.power_steps >= 0 && o.power_steps <= 16 && o.lanczos_steps >= 1 &&
          o.guard >= 0.0 && o.guard < 1.0 && o.max_retries >= 0 && o.jacobi_max_sweeps >= 1 &&
+         o.refine_steps >= 0 && o.refine_steps <= 64 &&
          (o.side == QDWHP_LARGEST || o.side == QDWHP_SMALLEST) &&
-         o.precision == QDWHP_FP64;
+         (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED);
 }
 
 }  // namespace
@@ -535,6 +536,7 @@ QDWHP_API void qdwhp_default_opts(qdwhp_opts* o) {
   o->max_retries = 2;
   o->jacobi_max_sweeps = 30;
   o->seed = 1234;
+  o->refine_steps = 0;
 }
 
 QDWHP_API const char* qdwhp_status_string(qdwhp_status s) {
