@@ -384,6 +384,100 @@ def run_eig_large(args):
                       "jacobi_sweeps": r.info["jacobi_sweeps"]}), flush=True)
 
 
+def run_batched(args):
+    """512 independent EIG problems (n uniform in [64, 1024], lambda ~ U[-1, 1], top 10 % each)
+    through qdwhp_eig_batched; FP64 or mixed."""
+    import torch
+
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import inputs as I
+    from paper_2104_14186_gb300 import qdwhp as Q
+
+    sizes = I.batch_sizes(args.count, 4000)
+    As = [I.eig_uniform_device(int(n), 4000 + i, 0.10)[0] for i, n in enumerate(sizes)]
+    prec = Q.MIXED if args.precision == "mixed" else Q.FP64
+    Q.eig_batched(As[:8], 0.10, concurrency=args.concurrency, precision=prec)    # warm-up
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res, sts = Q.eig_batched(As, 0.10, concurrency=args.concurrency, precision=prec)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        assert all(s == 0 for s in sts), sts
+    fl = sum(3 * (n ** 3 + n ** 3 / 3 + 2 * n ** 3) + 4 / 3 * n ** 3 for n in sizes)
+    t = statistics.median(times)
+    # accuracy of every result against the constructed spectra (outside the timed region)
+    import numpy as np
+    worst_lam, worst_res = 0.0, 0.0
+    for i, (A, r) in enumerate(zip(As, res)):
+        lam_i = np.random.default_rng(4000 + i).uniform(-1.0, 1.0, int(sizes[i]))   # the generator's spectrum
+        true = torch.from_numpy(np.sort(lam_i)[::-1][: r.lam.shape[0]].copy()).to(A.device)
+        worst_lam = max(worst_lam, torch.max(torch.abs(r.lam - true)).item())
+        worst_res = max(worst_res, (torch.linalg.norm(A @ r.V - r.V * r.lam[None, :]) / torch.linalg.norm(A)).item())
+    print(json.dumps({"workload": f"batched QDWHpartial-EIG: {args.count} matrices, n in [64, 1024], top 10 %",
+                      "precision": args.precision, "concurrency": args.concurrency,
+                      "solves_per_s": args.count / t, "ms_per_batch": 1e3 * t, "alg_tflops_lower_bound": fl / t / 1e12,
+                      "max_lam_err": worst_lam, "max_resid": worst_res}), flush=True)
+
+
+def run_serve(args):
+    """Poisson-arrival stream of mixed EIG / SVD requests through the qdwhp queue (continuous
+    batching, HBM-budget admission); p50 / p99 latency and solves/s."""
+    import numpy as np
+    import torch
+
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import inputs as I
+    from paper_2104_14186_gb300 import qdwhp as Q
+
+    reqs, gaps = I.serving_stream(args.count, 5000)
+    prep = []
+    for r in reqs:
+        if r["kind"] == "eig":
+            A, _, k = I.eig_uniform_device(r["n"], r["seed"], r["fraction"])
+        else:
+            A, _, k = I.svd_logspaced_device(r["m"], r["n"], r["seed"], r["fraction"])
+        prep.append((r["kind"], A, k))
+    prec = Q.MIXED if args.precision == "mixed" else Q.FP64
+    extra = {"precision": prec}
+    svd_extra = dict(extra, refine_steps=args.refine)
+    # service-time calibration: a few requests one at a time
+    q = Q.Queue(args.budget_gb << 30, max_slots=args.concurrency)
+    t0 = time.perf_counter()
+    for kind, A, k in prep[:8]:
+        rid = q.submit_eig(A, k, **extra) if kind == "eig" else q.submit_svd(A, k, **svd_extra)
+        q.wait(rid)
+        q.release(rid)
+    mean_service = (time.perf_counter() - t0) / 8
+    rate = 0.8 * args.concurrency / mean_service if args.rate <= 0 else args.rate
+    arrivals = np.cumsum(gaps / rate)
+    torch.cuda.synchronize()
+    start = time.perf_counter()
+    ids = []
+    for (kind, A, k), ta in zip(prep, arrivals):
+        delay = start + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        rid = q.submit_eig(A, k, **extra) if kind == "eig" else q.submit_svd(A, k, **svd_extra)
+        ids.append((rid, start + ta))
+    for rid, _ in ids:
+        q.wait(rid, 3600000)
+    end = max(q.times(rid)[2] for rid, _ in ids)
+    t_first = min(q.times(rid)[0] for rid, _ in ids)
+    lat = [q.times(rid)[2] - q.times(rid)[0] for rid, _ in ids]   # completion - submission (= arrival)
+    q.close()
+    print(json.dumps({"workload": f"serving: {args.count} Poisson-arrival requests, EIG n in [128, 2048], "
+                                  f"SVD n in [128, 1024] m in [n, 2n], fractions 1-20 %",
+                      "precision": args.precision, "refine_steps": args.refine, "concurrency": args.concurrency,
+                      "arrival_rate_per_s": rate, "mean_service_s": mean_service,
+                      "solves_per_s": len(ids) / (end - t_first),
+                      "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}),
+          flush=True)
+
+
 def run_single(args):
     """One untimed solve of the workload: the command the ncu launch-list capture runs."""
     import numpy as np
@@ -415,10 +509,22 @@ def main():
                     help="time one building block in isolation instead of the full solve")
     ap.add_argument("--single", action="store_true", help="one untimed solve (for profiler launch lists)")
     ap.add_argument("--eig16384", action="store_true", help="time the n = 16384 clustered EIG workload")
+    ap.add_argument("--batched", action="store_true", help="time the batched EIG workload")
+    ap.add_argument("--serve", action="store_true", help="run the serving stream")
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--concurrency", type=int, default=8)
+    ap.add_argument("--budget-gb", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=0.0)
     ap.add_argument("--fraction", type=float, default=0.01)
     args = ap.parse_args()
     if args.eig16384:
         run_eig_large(args)
+        return
+    if args.batched:
+        run_batched(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     if args.single:
         run_single(args)

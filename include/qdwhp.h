@@ -129,6 +129,54 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
                                  double* V, int64_t ldv, void* workspace, size_t ws_bytes,
                                  qdwhp_info* info, void* stream);
 
+/* ---- Request queue (serving) and batched solves; not part of the paper's method ---- */
+
+/*
+ * A queue runs submitted solves on `max_slots` worker threads, each with its own CUDA
+ * stream, inside one device allocation of `hbm_budget_bytes` (the only allocation the
+ * library makes; freed by qdwhp_queue_destroy).  A request is admitted when a worker is
+ * free and its workspace (qdwhp_eig/svd_workspace_bytes) fits in the unused part of the
+ * budget; pending requests are taken oldest first, skipping those that do not fit yet.
+ * Requests that arrive while others run start as soon as a slot and memory free up, and
+ * their kernels overlap on the device.
+ *   `stream` (create): unused, reserved.  `stream` (submit): the caller's stream on which
+ *   the input is produced; the solve starts after the work enqueued on it so far.
+ *   Inputs and outputs are the caller's device buffers and must stay valid until the
+ *   request completes; outputs are complete when qdwhp_poll / qdwhp_wait return OK.
+ *   Submit returns QDWHP_ERR_QUEUE_FULL if the request can never fit the budget.
+ */
+typedef struct qdwhp_queue qdwhp_queue;
+QDWHP_API qdwhp_status qdwhp_queue_create(size_t hbm_budget_bytes, int32_t max_slots, void* stream,
+                                          qdwhp_queue** q);
+QDWHP_API qdwhp_status qdwhp_submit_eig(qdwhp_queue* q, const double* A, int64_t n, int64_t lda,
+                                        const qdwhp_opts* opts, double* lambda, double* V, int64_t ldv,
+                                        void* stream, uint64_t* req_id);
+QDWHP_API qdwhp_status qdwhp_submit_svd(qdwhp_queue* q, const double* A, int64_t m, int64_t n, int64_t lda,
+                                        int64_t k, const qdwhp_opts* opts, double* sigma, double* U, int64_t ldu,
+                                        double* V, int64_t ldv, void* stream, uint64_t* req_id);
+/* QDWHP_PENDING while running; then the request's own status (info filled on completion). */
+QDWHP_API qdwhp_status qdwhp_poll(qdwhp_queue* q, uint64_t req_id, qdwhp_info* info);
+/* Waits at most timeout_ms (host wait); QDWHP_ERR_TIMEOUT if still running. */
+QDWHP_API qdwhp_status qdwhp_wait(qdwhp_queue* q, uint64_t req_id, int32_t timeout_ms, qdwhp_info* info);
+/* Host steady-clock seconds of submission, start and completion (QDWHP_PENDING until done). */
+QDWHP_API qdwhp_status qdwhp_request_times(qdwhp_queue* q, uint64_t req_id, double* t_submit, double* t_start,
+                                           double* t_done);
+/* Forgets a completed request (its id becomes invalid). */
+QDWHP_API qdwhp_status qdwhp_release(qdwhp_queue* q, uint64_t req_id);
+/* Finishes every pending request, joins the workers and frees the budget allocation. */
+QDWHP_API qdwhp_status qdwhp_queue_destroy(qdwhp_queue* q);
+
+/*
+ * `count` independent QDWHpartial-EIG solves (host arrays of device pointers and sizes;
+ * one `opts` for all) run `concurrency` at a time through a queue sized for the largest
+ * workspaces, largest problems first.  statuses[i] (and infos[i], if non-NULL) per
+ * problem; returns the first error, if any.  Allocates (and frees) the queue's budget.
+ */
+QDWHP_API qdwhp_status qdwhp_eig_batched(int64_t count, const double* const* A, const int64_t* n,
+                                         const int64_t* lda, const qdwhp_opts* opts, double* const* lambda,
+                                         double* const* V, const int64_t* ldv, int32_t concurrency,
+                                         qdwhp_status* statuses, qdwhp_info* infos, void* stream);
+
 /* ---- Building blocks (the dense kernels the solvers are made of) ---- */
 
 /*

@@ -13,6 +13,8 @@
 //     eigenvalues are then taken as Rayleigh quotients v_i^T M v_i.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "internal.h"
 #include "krylov.h"
 
@@ -139,8 +141,9 @@ __global__ void __launch_bounds__(kSweepThreads) jacobi_sweep_kernel(int mg, int
 
 // CTAs for a sweep: enough warps for one pair each, capped at what is co-resident.
 int sweep_grid(int pairs) {
+  static std::once_flag once;
   static int max_blocks = 0;
-  if (max_blocks == 0) {
+  std::call_once(once, [] {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, kSweepThreads, 0) != cudaSuccess ||
         per_sm < 1)
@@ -148,7 +151,7 @@ int sweep_grid(int pairs) {
     int dev = 0, sms = kNumSMs;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     max_blocks = std::min(per_sm, 8) * sms;
-  }
+  });
   const int want = (pairs + kSweepThreads / 32 - 1) / (kSweepThreads / 32);
   return std::max(1, std::min(want, max_blocks));
 }
@@ -235,9 +238,7 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     // compensated inner products only when they matter: a tight target, near convergence
     int comp = (tol < 1e-13 && prev < 1e-8) ? 1 : 0;
     void* args[] = {&mg_i, &nc_i, &N_i, &G, &ldg, &Vj, &ldv, &tol, &comp, &jst_dev};
-    QDWHP_CUDA_TRY(
-        cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(grid), dim3(kSweepThreads), args, 0, st));
-    QDWHP_LAUNCH_CHECK();
+    QDWHP_TRY(launch_cooperative((const void*)jacobi_sweep_kernel, dim3(grid), dim3(kSweepThreads), args, 0, st));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
     QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
     *sweeps_out = sweep + 1;

@@ -28,6 +28,23 @@ size_t g_used = 0;
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_last = nullptr;
+}  // namespace
+
+qdwhp_status launch_cooperative(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
+  // Cooperative kernels run one at a time on the GPU: each waits (on its own stream) for the
+  // previous one, so two grids never hold parts of the GPU while waiting at their barriers.
+  std::lock_guard<std::mutex> lk(g_coop_mu);
+  if (g_coop_last == nullptr) QDWHP_CUDA_TRY(cudaEventCreateWithFlags(&g_coop_last, cudaEventDisableTiming));
+  else QDWHP_CUDA_TRY(cudaStreamWaitEvent(st, g_coop_last, 0));
+  QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, st));
+  QDWHP_LAUNCH_CHECK();
+  QDWHP_CUDA_TRY(cudaEventRecord(g_coop_last, st));
+  return QDWHP_OK;
+}
+
 bool gemm_prof_enabled() { return g_on; }
 
 int gemm_prof_start(cudaStream_t st, double flops, const double* shape) {

@@ -16,6 +16,8 @@
 // reproducible run to run.  The trailing update and the formation of Q are GEMMs.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -236,16 +238,15 @@ size_t panel_smem_bytes(int R, int G) {
 qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
   const int G = panel_ctas(pa.R);
   const size_t smem = panel_smem_bytes(pa.R, G);
-  static bool attr_set = false;
-  if (!attr_set) {
-    QDWHP_CUDA_TRY(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-    attr_set = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  });
+  QDWHP_CUDA_TRY(attr_err);
   if (smem > 160 * 1024) return QDWHP_ERR_ARG;
   void* args[] = {&pa};
-  QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, st));
-  QDWHP_LAUNCH_CHECK();
-  return QDWHP_OK;
+  return launch_cooperative((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, st);
 }
 
 }  // namespace

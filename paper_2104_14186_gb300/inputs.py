@@ -136,3 +136,57 @@ def eig_clustered_device(n: int, seed: int, fraction: float, cluster_frac: float
     A = (Q * lam_t[None, :]) @ Q.T
     A = 0.5 * (A + A.T)
     return A.contiguous(), lam, k_from_fraction(n, fraction)
+
+
+def _haar_device(n: int, g, device, m: int | None = None):
+    import torch
+    m = n if m is None else m
+    G = torch.randn(m, n, dtype=torch.float64, device=device, generator=g)
+    Q, R = torch.linalg.qr(G)
+    d = torch.sign(torch.diagonal(R))
+    d[d == 0] = 1.0
+    return Q * d[None, :]
+
+
+def eig_uniform_device(n: int, seed: int, fraction: float = 0.10, device="cuda"):
+    """`eig_uniform`'s spectrum (lambda ~ U[-1, 1] from numpy PCG64) with the Haar factor
+    drawn and orthogonalised on the GPU (torch Philox generator + Householder QR).
+    Returns (A as a CUDA float64 tensor, lam, k)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(-1.0, 1.0, n)
+    g = torch.Generator(device=device).manual_seed(seed)
+    Q = _haar_device(n, g, device)
+    A = (Q * torch.from_numpy(lam).to(device)[None, :]) @ Q.T
+    return (0.5 * (A + A.T)).contiguous(), lam, k_from_fraction(n, fraction)
+
+
+def svd_logspaced_device(m: int, n: int, seed: int, fraction: float, decades: float = 10.0, device="cuda"):
+    """`svd_logspaced`'s spectrum with Haar factors drawn on the GPU; returns (A, sigma, k)."""
+    import torch
+    i = np.arange(n, dtype=np.float64)
+    sigma = 10.0 ** (-decades * i / max(n - 1, 1))
+    g = torch.Generator(device=device).manual_seed(seed)
+    U = _haar_device(n, g, device, m)
+    V = _haar_device(n, g, device)
+    A = (U * torch.from_numpy(sigma).to(device)[None, :]) @ V.T
+    return A.contiguous(), sigma, k_from_fraction(n, fraction)
+
+
+def serving_stream(count: int, seed: int, eig_n=(128, 2048), svd_n=(128, 1024), frac=(0.01, 0.20)):
+    """Seeded request stream: half EIG (n uniform in eig_n, largest side), half SVD (n uniform in
+    svd_n, m uniform in [n, 2n]); wanted fraction uniform in frac; unit-rate exponential
+    inter-arrival gaps (scaled by the caller to the target rate)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        f = float(rng.uniform(*frac))
+        if rng.uniform() < 0.5:
+            n = int(rng.integers(eig_n[0], eig_n[1] + 1))
+            reqs.append({"kind": "eig", "m": n, "n": n, "fraction": f, "seed": seed * 100003 + i})
+        else:
+            n = int(rng.integers(svd_n[0], svd_n[1] + 1))
+            m = int(rng.integers(n, 2 * n + 1))
+            reqs.append({"kind": "svd", "m": m, "n": n, "fraction": f, "seed": seed * 100003 + i})
+    gaps = rng.exponential(1.0, count)
+    return reqs, gaps

@@ -91,6 +91,18 @@ SIGNATURES = {
     "qdwhp_qdwh_steps_f64": (C.c_int, [I64, I64, P, I64, C.c_int32, C.POINTER(D), C.POINTER(C.c_int32),
                                        C.POINTER(D), P, C.c_size_t, P]),
     "qdwhp_potrf_f64_noalloc": (C.c_int, [I64, P, I64, C.POINTER(C.c_int), P]),
+    "qdwhp_queue_create": (C.c_int, [C.c_size_t, C.c_int32, P, C.POINTER(P)]),
+    "qdwhp_submit_eig": (C.c_int, [P, P, I64, I64, C.POINTER(Opts), P, P, I64, P, C.POINTER(C.c_uint64)]),
+    "qdwhp_submit_svd": (C.c_int, [P, P, I64, I64, I64, I64, C.POINTER(Opts), P, P, I64, P, I64, P,
+                                   C.POINTER(C.c_uint64)]),
+    "qdwhp_poll": (C.c_int, [P, C.c_uint64, C.POINTER(Info)]),
+    "qdwhp_wait": (C.c_int, [P, C.c_uint64, C.c_int32, C.POINTER(Info)]),
+    "qdwhp_request_times": (C.c_int, [P, C.c_uint64, C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
+    "qdwhp_release": (C.c_int, [P, C.c_uint64]),
+    "qdwhp_queue_destroy": (C.c_int, [P]),
+    "qdwhp_eig_batched": (C.c_int, [I64, C.POINTER(P), C.POINTER(I64), C.POINTER(I64), C.POINTER(Opts),
+                                    C.POINTER(P), C.POINTER(P), C.POINTER(I64), C.c_int32, C.POINTER(C.c_int),
+                                    C.POINTER(Info), P]),
     "qdwhp_launch_count": (C.c_ulonglong, []),
     "qdwhp_profile_begin": (C.c_int, []),
     "qdwhp_profile_end": (C.c_int, [C.POINTER(D), C.POINTER(D), C.POINTER(I64)]),
@@ -246,6 +258,93 @@ class _nullctx:
 
     def __exit__(self, *a):
         return False
+
+
+class Queue:
+    """qdwhp_queue: serving queue with HBM-budget admission (argument marshalling only).
+
+    Keeps the tensors of every request alive until it is released."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4):
+        self.h = P()
+        _check(lib().qdwhp_queue_create(int(hbm_budget_bytes), int(max_slots), None, C.byref(self.h)),
+               "qdwhp_queue_create")
+        self.keep = {}
+
+    def submit_eig(self, A: torch.Tensor, k: int, side: str = "largest", stream=None, **opts) -> int:
+        n = A.shape[0]
+        o = default_opts(side=side, **opts)
+        o.count = int(k)
+        Ac = _colmajor(A)
+        lam = torch.empty(k, dtype=torch.float64, device=A.device)
+        Vt = torch.empty(k, n, dtype=torch.float64, device=A.device)
+        rid = C.c_uint64(0)
+        _check(lib().qdwhp_submit_eig(self.h, _ptr(Ac), n, n, C.byref(o), _ptr(lam), _ptr(Vt), n, _stream(stream),
+                                      C.byref(rid)), "qdwhp_submit_eig")
+        self.keep[rid.value] = ("eig", Ac, lam, Vt, o)
+        return rid.value
+
+    def submit_svd(self, A: torch.Tensor, k: int, stream=None, **opts) -> int:
+        m, n = A.shape
+        o = default_opts(**opts)
+        Ac = _colmajor(A)
+        sig = torch.empty(k, dtype=torch.float64, device=A.device)
+        Ut = torch.empty(k, m, dtype=torch.float64, device=A.device)
+        Vt = torch.empty(k, n, dtype=torch.float64, device=A.device)
+        rid = C.c_uint64(0)
+        _check(lib().qdwhp_submit_svd(self.h, _ptr(Ac), m, n, m, int(k), C.byref(o), _ptr(sig), _ptr(Ut), m, _ptr(Vt),
+                                      n, _stream(stream), C.byref(rid)), "qdwhp_submit_svd")
+        self.keep[rid.value] = ("svd", Ac, sig, Ut, Vt, o)
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        return int(lib().qdwhp_poll(self.h, rid, None))
+
+    def wait(self, rid: int, timeout_ms: int = 600000):
+        info = Info()
+        st = lib().qdwhp_wait(self.h, rid, int(timeout_ms), C.byref(info))
+        _check(st, "qdwhp_wait")
+        kept = self.keep[rid]
+        if kept[0] == "eig":
+            return EigResult(kept[2], kept[3].t(), info.as_dict())
+        return SvdResult(kept[2], kept[3].t(), kept[4].t(), info.as_dict())
+
+    def times(self, rid: int):
+        a, b, c = D(0), D(0), D(0)
+        lib().qdwhp_request_times(self.h, rid, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    def release(self, rid: int):
+        lib().qdwhp_release(self.h, rid)
+        self.keep.pop(rid, None)
+
+    def close(self):
+        if self.h:
+            _check(lib().qdwhp_queue_destroy(self.h), "qdwhp_queue_destroy")
+            self.h = P()
+            self.keep.clear()
+
+
+def eig_batched(As, ks_fraction: float = 0.1, concurrency: int = 8, side: str = "largest", **opts):
+    """qdwhp_eig_batched over a list of symmetric CUDA float64 matrices; returns (results, statuses)."""
+    cnt = len(As)
+    o = default_opts(side=side, **opts)
+    o.count = 0
+    o.fraction = float(ks_fraction)
+    cols = [_colmajor(A) for A in As]
+    ns = [A.shape[0] for A in As]
+    kk = [k_from_fraction(n, ks_fraction) for n in ns]
+    lams = [torch.empty(k, dtype=torch.float64, device=A.device) for k, A in zip(kk, As)]
+    Vts = [torch.empty(k, n, dtype=torch.float64, device=A.device) for k, n, A in zip(kk, ns, As)]
+    Pa = (P * cnt)(*[_ptr(c) for c in cols])
+    Pl = (P * cnt)(*[_ptr(x) for x in lams])
+    Pv = (P * cnt)(*[_ptr(x) for x in Vts])
+    Na = (I64 * cnt)(*ns)
+    sts = (C.c_int * cnt)()
+    infos = (Info * cnt)()
+    lib().qdwhp_eig_batched(cnt, Pa, Na, Na, C.byref(o), Pl, Pv, Na, int(concurrency), sts, infos, _stream(None))
+    res = [EigResult(lams[i], Vts[i].t(), infos[i].as_dict()) for i in range(cnt)]
+    return res, [int(sts[i]) for i in range(cnt)]
 
 
 def launch_count() -> int:

@@ -94,3 +94,12 @@ def test_argument_errors_return_before_any_launch(lib):
 def test_status_strings(lib):
     for s in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9, 1):
         assert lib.qdwhp_status_string(s)
+
+
+def test_queue_argument_errors(lib):
+    from paper_2104_14186_gb300 import qdwhp as Q
+    h = Q.P()
+    assert lib.qdwhp_queue_create(1 << 30, 0, None, C.byref(h)) == -1       # no slots
+    assert lib.qdwhp_queue_create(100, 2, None, C.byref(h)) == -1           # budget too small
+    assert lib.qdwhp_poll(None, 1, None) == -1
+    assert lib.qdwhp_queue_destroy(None) == -1
