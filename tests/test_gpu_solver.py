@@ -16,6 +16,11 @@ torch = pytest.importorskip("torch")
 LAM_TOL = 1e-12
 ORTH_TOL = 5e-15
 RES_TOL = 1e-13
+# SVD: ||A V - U S||_F / ||A||_F, the direct analogue of the EIG residual, is held to RES_TOL;
+# the transposed residual ||A^T U - V S||_F / ||A||_F measures how well span(Q2) contains the
+# right singular vectors, which Theorem 1 bounds only through tol = 0.01 (the FP64 oracle
+# itself reaches 1.2e-13 on a 700 x 350 log-spaced problem), so it is held to 1e-12.
+RES_TOL_T = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -89,9 +94,11 @@ def check_svd(q, r, ref=None):
     assert sig.shape == (q.k,) and U.shape == (m_, q.k) and V.shape == (n_, q.k)
     assert mt["sigma_err"] <= LAM_TOL, mt
     assert mt["orthU"] <= ORTH_TOL * max(m_, n_) and mt["orthV"] <= ORTH_TOL * max(m_, n_), mt
-    assert mt["residV"] <= RES_TOL and mt["residU"] <= RES_TOL, mt
+    assert mt["residV"] <= RES_TOL and mt["residU"] <= RES_TOL_T, mt
     if ref is not None:
         assert np.max(np.abs(sig - ref.sigma)) <= LAM_TOL * q.sigma[0]
+        mo = O.svd_metrics(q.A, ref.sigma, ref.U, ref.V)
+        assert mt["residU"] <= 10 * mo["residU"] + 1e-14, (mt, mo)   # no worse than the oracle's
     return mt
 
 
@@ -110,7 +117,7 @@ def test_svd_wide(Q):
     sig, U, V = r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy()
     assert U.shape == (240, q.k) and V.shape == (300, q.k)
     mt = O.svd_metrics(At, sig, U, V, q.sigma[: q.k])
-    assert mt["sigma_err"] <= LAM_TOL and mt["residV"] <= RES_TOL and mt["residU"] <= RES_TOL
+    assert mt["sigma_err"] <= LAM_TOL and mt["residV"] <= RES_TOL and mt["residU"] <= RES_TOL_T
 
 
 def test_svd_small_threshold_takes_qr_step(Q):
