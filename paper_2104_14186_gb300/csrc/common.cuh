@@ -41,8 +41,9 @@ void set_last_error(cudaError_t e, const char* what, const char* file, int line)
 // Sets the text returned by qdwhp_last_error_message() for a non-CUDA error.
 void set_error_message(const char* msg);
 void note_launch();
-// Launches a cooperative kernel behind the process-wide gate that serialises cooperative
-// kernels on the GPU (streams of concurrent solves may otherwise overlap two of them).
+// Launches a cooperative kernel behind the process-wide gate that keeps the CTAs of all
+// cooperative kernels that can be in flight together at most the SM count (streams of
+// concurrent solves may otherwise oversubscribe the GPU with grids waiting at barriers).
 qdwhp_status launch_cooperative(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st);
 
 // Opt-in timing of the DMMA GEMM launches (CUDA events around each launch on its stream).

@@ -121,7 +121,7 @@ __device__ void rotate_pair_warp(int p, int q, int mg, int nc, double* G, int64_
 
 // One full sweep (N - 1 rounds) in one cooperative launch: every warp takes pairs of the
 // round, and the grid meets at a barrier between rounds.
-constexpr int kSweepThreads = 32;   // one warp per CTA: a round's pairs spread over all SMs
+constexpr int kSweepThreads = 64;   // two warps (pairs) per CTA, at most one CTA per SM
 __global__ void __launch_bounds__(kSweepThreads) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg,
                                                                      double* Vj, int64_t ldv, double tol, int comp,
                                                                      JacobiState* jst) {
@@ -139,18 +139,15 @@ __global__ void __launch_bounds__(kSweepThreads) jacobi_sweep_kernel(int mg, int
   }
 }
 
-// CTAs for a sweep: enough warps for one pair each, capped at what is co-resident.
+// CTAs for a sweep: enough warps for one pair each, at most one CTA per SM (the budget of
+// the cooperative-launch gate, which spreads the pairs over all SMs).
 int sweep_grid(int pairs) {
   static std::once_flag once;
   static int max_blocks = 0;
   std::call_once(once, [] {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, kSweepThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
     int dev = 0, sms = kNumSMs;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    max_blocks = std::min(per_sm, 8) * sms;
+    max_blocks = sms;
   });
   const int want = (pairs + kSweepThreads / 32 - 1) / (kSweepThreads / 32);
   return std::max(1, std::min(want, max_blocks));

@@ -5,6 +5,7 @@
 // ends, so callers can report the achieved FP64 rate of the dominant kernel from
 // inside a real solve.  Profiling is process-wide and meant for one host thread.
 #include <atomic>
+#include <deque>
 #include <mutex>
 #include <vector>
 
@@ -29,19 +30,57 @@ size_t g_used = 0;
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
+// In-flight cooperative kernels: their completion events and CTA counts, oldest first.
+struct CoopEntry {
+  cudaEvent_t done;
+  int ctas;
+};
 std::mutex g_coop_mu;
-cudaEvent_t g_coop_last = nullptr;
+std::deque<CoopEntry> g_coop_inflight;
+std::vector<cudaEvent_t> g_coop_free_events;
+int g_coop_total = 0;
+int g_coop_capacity = 0;
 }  // namespace
 
 qdwhp_status launch_cooperative(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
-  // Cooperative kernels run one at a time on the GPU: each waits (on its own stream) for the
-  // previous one, so two grids never hold parts of the GPU while waiting at their barriers.
+  // Cooperative kernels may run concurrently (streams of concurrent solves) as long as the CTAs
+  // of all cooperative grids that can be in flight together number at most the SM count: each
+  // CTA fits on an empty SM and ordinary kernels always drain, so every such grid eventually
+  // becomes fully resident and its grid barriers complete.  Before a launch that would exceed
+  // the budget, the stream waits (on the GPU) for the oldest in-flight cooperative kernels.
   std::lock_guard<std::mutex> lk(g_coop_mu);
-  if (g_coop_last == nullptr) QDWHP_CUDA_TRY(cudaEventCreateWithFlags(&g_coop_last, cudaEventDisableTiming));
-  else QDWHP_CUDA_TRY(cudaStreamWaitEvent(st, g_coop_last, 0));
+  if (g_coop_capacity == 0) {
+    int dev = 0, sms = kNumSMs;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_coop_capacity = sms;
+  }
+  const int ctas = (int)(grid.x * grid.y * grid.z);
+  if (ctas > g_coop_capacity) return QDWHP_ERR_ARG;
+  // forget kernels that have finished
+  while (!g_coop_inflight.empty() && cudaEventQuery(g_coop_inflight.front().done) == cudaSuccess) {
+    g_coop_total -= g_coop_inflight.front().ctas;
+    g_coop_free_events.push_back(g_coop_inflight.front().done);
+    g_coop_inflight.pop_front();
+  }
+  cudaGetLastError();   // cudaEventQuery reports cudaErrorNotReady for running kernels
+  while (g_coop_total + ctas > g_coop_capacity && !g_coop_inflight.empty()) {
+    QDWHP_CUDA_TRY(cudaStreamWaitEvent(st, g_coop_inflight.front().done, 0));
+    g_coop_total -= g_coop_inflight.front().ctas;
+    g_coop_free_events.push_back(g_coop_inflight.front().done);
+    g_coop_inflight.pop_front();
+  }
   QDWHP_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, st));
   QDWHP_LAUNCH_CHECK();
-  QDWHP_CUDA_TRY(cudaEventRecord(g_coop_last, st));
+  cudaEvent_t ev = nullptr;
+  if (!g_coop_free_events.empty()) {
+    ev = g_coop_free_events.back();
+    g_coop_free_events.pop_back();
+  } else {
+    QDWHP_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  QDWHP_CUDA_TRY(cudaEventRecord(ev, st));
+  g_coop_inflight.push_back({ev, ctas});
+  g_coop_total += ctas;
   return QDWHP_OK;
 }
 
