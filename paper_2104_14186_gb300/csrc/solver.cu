@@ -13,7 +13,7 @@
 //     1 % of the spread outwards); Algorithm 1 step 1 scales by |mu|;
 //   * a requested count k becomes a threshold through the k-th Ritz value of a
 //     (k+p)-dimensional subspace (Cauchy interlacing guarantees >= k pairs beyond it);
-//   * the wanted width is kept >= guard * spread (default 5 %);
+//   * the wanted width is kept >= guard * spread (default 10 %, unwanted side scaled by <= ~9);
 //   * QR-based QDWH steps while c_k > c_qr (default 100), Section 4.2.
 #include <cstdio>
 
@@ -81,6 +81,8 @@ qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh) 
   return QDWHP_OK;
 }
 
+// Block Krylov bases of the count-to-threshold step wider than this keep only the last block.
+constexpr int64_t kKrylovMaxCols = 2048;
 // Stopping tolerance of the reduced-problem Jacobi when its vectors are used: the
 // normalised off-diagonal inner products (computed in double-double) down to ~2u.
 constexpr double kJacobiTight = 4.5e-16;
@@ -240,26 +242,38 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   const double spread = std::max(hi_raw - lo_raw, 1e-300);
   const double lam_lo = lo_raw - 0.01 * spread, lam_hi = hi_raw + 0.01 * spread;
 
-  // Threshold for the requested count: q power steps on lam_hi I - A', Rayleigh-Ritz of A'.
+  // Threshold for the requested count: block Krylov space of P = lam_hi I - A' from k + p
+  // SplitMix64 vectors (each block orthonormalised before the next product), Rayleigh-Ritz of A'
+  // on it; when (q+1) b > 2048 columns only the last block, P^(q+1) Om, is kept.
   const int64_t b = std::min<int64_t>(n, k + o.block_extra);
-  double* Om = w.X;          // n x b
-  double* Yb = w.q.Y;        // n x b
-  double* Qb = w.q.Z;        // n x b
-  double* AQ = w.S2;         // n x b
-  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Om, n));
-  QDWHP_TRY(axpby(st, n, b, lam_hi, Om, n, 0.0, Yb, n));
-  QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Om, n, 1.0, Yb, n));
-  for (int it = 0; it < o.power_steps; ++it) {
-    QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
-    QDWHP_TRY(axpby(st, n, b, lam_hi, Qb, n, 0.0, Yb, n));
-    QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Qb, n, 1.0, Yb, n));
+  const int q = o.power_steps > 0 ? o.power_steps : 6;
+  const bool krylov = (int64_t)(q + 1) * b <= std::min<int64_t>(n, kKrylovMaxCols);
+  const int64_t width = krylov ? (q + 1) * b : b;
+  double* Y = w.X;           // n x b
+  double* Kb = w.S3;         // n x width
+  double* Qj = w.q.Z;        // n x b
+  double* AK = w.q.Y;        // n x width
+  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Y, n));
+  for (int j = 0; j <= q; ++j) {
+    double* Qdst = krylov ? Kb + (int64_t)j * b * n : Qj;
+    QDWHP_TRY(orth(st, n, b, Y, Qdst, w.f, w.qr_scratch));
+    if (j < q || !krylov) {
+      QDWHP_TRY(axpby(st, n, b, lam_hi, Qdst, n, 0.0, Y, n));
+      QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Qdst, n, 1.0, Y, n));
+    }
   }
-  QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
-  QDWHP_TRY(gemm(st, false, false, n, b, n, eps_side, A, lda, Qb, n, 0.0, AQ, n));
-  QDWHP_TRY(gemm(st, true, false, b, b, n, 1.0, Qb, n, AQ, n, 0.0, w.S1, b, FULL, 0.0, w.c.splitk, w.c.splitk_elems));
+  if (krylov) {
+    QDWHP_TRY(copy_matrix(st, n, width, Kb, n, AK, n));
+    QDWHP_TRY(orth(st, n, width, AK, Kb, w.f, w.qr_scratch));
+  } else {
+    QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
+  }
+  QDWHP_TRY(gemm(st, false, false, n, width, n, eps_side, A, lda, Kb, n, 0.0, AK, n));
+  QDWHP_TRY(gemm(st, true, false, width, width, n, 1.0, Kb, n, AK, n, 0.0, w.S1, width, FULL, 0.0, w.c.splitk,
+                 w.c.splitk_elems));
   int sweeps = 0;
-  QDWHP_TRY(small_sym_eig(st, b, lam_lo, w, o.jacobi_max_sweeps, hs, &sweeps, true));
-  QDWHP_TRY(select_sort(st, b, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
+  QDWHP_TRY(small_sym_eig(st, width, lam_lo, w, o.jacobi_max_sweeps, hs, &sweeps, true));
+  QDWHP_TRY(select_sort(st, width, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
   QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
   double theta_k = 0.0;
@@ -384,34 +398,46 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   const double alpha = std::sqrt(std::max(hs.lst.out[2] + hs.lst.out[3], 0.0));
   if (!(alpha > 0.0)) return QDWHP_ERR_ARG;
 
-  // Relative threshold s from the k-th Ritz value of A^T A on a (k+p)-dim subspace.
+  // Relative threshold s from the k-th Ritz value of A^T A on the block Krylov space of k + p
+  // SplitMix64 vectors (only the last block when (q+1) b > 2048 columns).
   const int64_t b = std::min<int64_t>(n, k + o.block_extra);
-  double* Om = w.q.Z;    // n x b
+  const int q = o.power_steps > 0 ? o.power_steps : 2;
+  const bool krylov = (int64_t)(q + 1) * b <= std::min<int64_t>(n, kKrylovMaxCols);
+  const int64_t width = krylov ? (q + 1) * b : b;
+  double* Y = w.q.Y;     // n x b
+  double* Kb = w.Vj;     // n x width
+  double* Qj = w.q.Z;    // n x b
   double* T1 = w.X;      // m x b
-  double* Yb = w.q.Y;    // n x b
-  double* Qb = w.Vj;     // n x b
-  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Om, n));
-  QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Om, n, 0.0, T1, m));
-  QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Yb, n));
-  for (int it = 0; it < o.power_steps; ++it) {
-    QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
-    QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qb, n, 0.0, T1, m));
-    QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Yb, n));
+  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Y, n));
+  for (int j = 0; j <= q; ++j) {
+    double* Qdst = krylov ? Kb + (int64_t)j * b * n : Qj;
+    QDWHP_TRY(orth(st, n, b, Y, Qdst, w.f, w.qr_scratch));
+    if (j < q || !krylov) {
+      QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qdst, n, 0.0, T1, m));
+      QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Y, n));
+    }
   }
-  QDWHP_TRY(orth(st, n, b, Yb, Qb, w.f, w.qr_scratch));
-  QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qb, n, 0.0, w.C, m));
-  // Ritz values of A^T A on span(Qb): eigenvalues of H = C^T C (b x b, positive semidefinite,
-  // so they are its singular values: column norms after one-sided Jacobi).
+  if (krylov) {
+    QDWHP_TRY(copy_matrix(st, n, width, Kb, n, w.C, n));
+    QDWHP_TRY(orth(st, n, width, w.C, Kb, w.f, w.qr_scratch));
+  } else {
+    QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
+  }
+  QDWHP_TRY(gemm(st, false, false, m, width, n, 1.0, A, lda, Kb, n, 0.0, w.C, m));
+  // Ritz values of A^T A on span(K): eigenvalues of H = C^T C (positive semidefinite, so they
+  // are its singular values: column norms after one-sided Jacobi).
   double* H = w.W;
-  QDWHP_TRY(gemm(st, true, false, b, b, m, 1.0, w.C, m, w.C, m, 0.0, H, b, FULL, 0.0, w.c.splitk, w.c.splitk_elems));
-  QDWHP_TRY(symmetrize_avg(st, b, H, b));
+  QDWHP_TRY(gemm(st, true, false, width, width, m, 1.0, w.C, m, w.C, m, 0.0, H, width, FULL, 0.0, w.c.splitk,
+                 w.c.splitk_elems));
+  QDWHP_TRY(symmetrize_avg(st, width, H, width));
   int sweeps = 0, conv = 0;
   // values only: eigenvalue errors are of the order of the squared off-diagonal tolerance
   const double tol_b = 1e-9;
-  QDWHP_TRY(jacobi_onesided(st, b, b, H, b, w.Vj, b, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst, &sweeps, &conv));
+  QDWHP_TRY(jacobi_onesided(st, width, width, H, width, w.Vj, width, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst,
+                            &sweeps, &conv));
   if (!conv) return QDWHP_ERR_NOT_CONVERGED;
-  QDWHP_TRY(column_norms(st, b, b, H, b, w.c.vals));
-  QDWHP_TRY(select_sort(st, b, w.c.vals, -1.0, INFINITY, w.c.order, w.c.ints + 1));
+  QDWHP_TRY(column_norms(st, width, width, H, width, w.c.vals));
+  QDWHP_TRY(select_sort(st, width, w.c.vals, -1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.q.Z));
   double theta_k = 0.0;
   QDWHP_TRY(sync_read(st, &theta_k, w.q.Z, sizeof(double)));
@@ -531,8 +557,8 @@ QDWHP_API void qdwhp_default_opts(qdwhp_opts* o) {
   o->tol = 0.01;
   o->c_qr = 100.0;
   o->block_extra = 16;
-  o->power_steps = 2;
-  o->guard = 0.05;
+  o->power_steps = 0;   // automatic: 6 for EIG, 2 for SVD
+  o->guard = 0.10;
   o->max_retries = 2;
   o->jacobi_max_sweeps = 30;
   o->seed = 1234;
