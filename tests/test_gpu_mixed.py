@@ -1,8 +1,9 @@
 """The mixed-precision path (QDWHP_MIXED): every Cholesky-based QDWH step but the last in
 FP32, everything else in FP64.  Its accuracy is stated per result:
-  * without refinement, eigen/singular values are accurate to ~1e-8 (EIG) / ~1e-12 (SVD)
-    relative to ||A||_2 but vectors only to ~1e-5 / ~1e-6 (the FP32 rounding rotates the
-    captured subspace by ~u_32 / gap);
+  * without refinement, eigen/singular values are accurate to ~1e-6 (EIG) / ~1e-12 (SVD)
+    relative to ||A||_2 but vectors only to ~1e-4 / ~1e-6: the FP32 rounding (u_32 = 6e-8)
+    of the iterates, amplified by the condition of Z = I + c X^T X (up to ~1.5e3 when the
+    unwanted side is scaled by the guard's limit of ~9), rotates the captured subspace;
   * with FP64 subspace-iteration steps on Q2 (refine_steps) the SVD reaches the FP64
     tolerances again."""
 
@@ -36,8 +37,8 @@ def test_mixed_eig_stated_accuracy(Q):
     r = Q.eig(dev(p.A), k=p.k, precision=Q.MIXED)
     assert r.info["it_f32"] == 2
     m = O.eig_metrics(p.A, r.lam.cpu().numpy(), r.V.cpu().numpy(), np.sort(p.lam)[::-1][: p.k])
-    assert m["lam_err"] <= 1e-7, m
-    assert m["resid"] <= 1e-4, m
+    assert m["lam_err"] <= 1e-6, m
+    assert m["resid"] <= 1e-3, m
     assert m["orth"] <= 5e-15 * 512, m
 
 
