@@ -69,6 +69,15 @@ __global__ void copy_upper_kernel(int N, const double* A, int64_t lda, double* R
   }
 }
 
+// G = R^T for the upper triangle R of A (the strictly lower part of G is R's upper part).
+__global__ void copy_upper_t_kernel(int N, const double* A, int64_t lda, double* G, int64_t ldg) {
+  const size_t total = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    G[i + (int64_t)j * ldg] = (j <= i) ? A[j + (int64_t)i * lda] : 0.0;
+  }
+}
+
 __global__ void symmetrize_kernel(int N, double* Y, int64_t ldy) {
   const size_t total = (size_t)N * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -186,6 +195,13 @@ qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const float* X, int6
 qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr) {
   if (n <= 0) return QDWHP_OK;
   copy_upper_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>((int)n, A, lda, R, ldr);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status copy_upper_t(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* G, int64_t ldg) {
+  if (n <= 0) return QDWHP_OK;
+  copy_upper_t_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>((int)n, A, lda, G, ldg);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

@@ -410,7 +410,9 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   double* T1 = w.X;      // m x b
   QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Y, n));
   for (int j = 0; j <= q; ++j) {
-    double* Qdst = krylov ? Kb + (int64_t)j * b * n : Qj;
+    // blocks stored dominant first (P^q Om leads): the R factor below is then graded with
+    // decreasing diagonal, the ordering under which Jacobi on R^T converges fastest
+    double* Qdst = krylov ? Kb + (int64_t)(q - j) * b * n : Qj;
     QDWHP_TRY(orth(st, n, b, Y, Qdst, w.f, w.qr_scratch));
     if (j < q || !krylov) {
       QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qdst, n, 0.0, T1, m));
@@ -424,24 +426,23 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
   }
   QDWHP_TRY(gemm(st, false, false, m, width, n, 1.0, A, lda, Kb, n, 0.0, w.C, m));
-  // Ritz values of A^T A on span(K): eigenvalues of H = C^T C (positive semidefinite, so they
-  // are its singular values: column norms after one-sided Jacobi).
-  double* H = w.W;
-  QDWHP_TRY(gemm(st, true, false, width, width, m, 1.0, w.C, m, w.C, m, 0.0, H, width, FULL, 0.0, w.c.splitk,
-                 w.c.splitk_elems));
-  QDWHP_TRY(symmetrize_avg(st, width, H, width));
+  // Ritz values of A^T A on span(K) are the squared singular values of C = A K = Q_C R, i.e. of
+  // R^T.  Forming C^T C instead would square the grading of K (its blocks span decades of
+  // sigma^2), and one-sided Jacobi on it then needs tens of sweeps; on R^T it needs about ten.
+  QDWHP_TRY(geqrf(st, m, width, w.C, m, w.q.qf, w.q.qr_scratch));
+  double* G = w.W;
+  QDWHP_TRY(copy_upper_t(st, width, w.C, m, G, width));
   int sweeps = 0, conv = 0;
-  // values only: eigenvalue errors are of the order of the squared off-diagonal tolerance
+  // values only: singular value errors are of the order of the squared off-diagonal tolerance
   const double tol_b = 1e-9;
-  QDWHP_TRY(jacobi_onesided(st, width, width, H, width, w.Vj, width, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst,
+  QDWHP_TRY(jacobi_onesided(st, width, width, G, width, w.Vj, width, o.jacobi_max_sweeps, tol_b, w.c.jst, &hs.jst,
                             &sweeps, &conv));
   if (!conv) return QDWHP_ERR_NOT_CONVERGED;
-  QDWHP_TRY(column_norms(st, width, width, H, width, w.c.vals));
+  QDWHP_TRY(column_norms(st, width, width, G, width, w.c.vals));
   QDWHP_TRY(select_sort(st, width, w.c.vals, -1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.q.Z));
-  double theta_k = 0.0;
-  QDWHP_TRY(sync_read(st, &theta_k, w.q.Z, sizeof(double)));
-  const double sig_hat = std::sqrt(std::max(theta_k, 0.0));
+  double sig_hat = 0.0;
+  QDWHP_TRY(sync_read(st, &sig_hat, w.q.Z, sizeof(double)));
   double s = std::max(sig_hat / alpha * (1.0 - 1e-10), 1e-15);
 
   int retries = 0;
