@@ -66,8 +66,9 @@ typedef struct {
   int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
   double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.01) */
   double c_qr;            /* SVD: QR-based step while c_k > c_qr (default 100) */
-  int32_t block_extra;    /* p: the count-to-threshold block Krylov space starts from k + p vectors (16) */
-  int32_t power_steps;    /* q: its depth (products with the operator); 0 = automatic (EIG 6, SVD 2) */
+  int32_t block_extra;    /* p: the count-to-threshold subspace starts from k + p vectors (16) */
+  int32_t power_steps;    /* q: products with the operator; 0 = automatic.  EIG: block Krylov space of
+                             depth q (6); SVD: subspace iteration with q + 1 products of A^T A (2) */
   double guard;           /* EIG: minimum wanted width / spectral spread (default 0.10) */
   int32_t max_retries;    /* re-runs with a wider threshold if < k pairs are captured (2) */
   int32_t jacobi_max_sweeps; /* sweep limit of the reduced-problem Jacobi solver (30) */

@@ -10,9 +10,10 @@ stated at the step and listed in the design notes:
     pushed 1 % outwards (Algorithm 1 step 1 asks for "a few steps").
   * Count -> threshold: the k-th Ritz value of any subspace is a one-sided bound
     on the k-th eigenvalue (Cauchy interlacing), so a threshold there captures at
-    least k wanted eigenpairs.  The subspace is the block Krylov space of k+p
-    starting vectors and q products with a positive semidefinite shift of the
-    operator (only the last block when that basis would exceed 2048 columns).
+    least k wanted eigenpairs.  EIG: the block Krylov space of k+p starting vectors
+    and q products with a positive semidefinite shift of the operator (only the
+    last block when that basis would exceed 2048 columns).  SVD: subspace
+    iteration, q+1 products of A^T A with k+p vectors.
   * Threshold placement guard: the wanted interval is kept at least 10 % of the
     spectral spread wide, so that the unwanted side is never scaled by more
     than about 9 (a threshold inside a tight cluster, or just below the largest
@@ -168,19 +169,16 @@ def threshold_from_count_eig(A: np.ndarray, eps_side: float, k: int, lam_hi: flo
 
 
 def threshold_from_count_svd(A: np.ndarray, k: int, p: int, q: int, seed: int) -> float:
-    """sigma_hat_k <= sigma_k: square root of the k-th largest Ritz value of A^T A on the block
-    Krylov space span[Om, (A^T A) Om, ..., (A^T A)^q Om] (or on the last block when
-    (q+1)(k+p) exceeds KRYLOV_MAX_COLS); Cauchy interlacing."""
+    """sigma_hat_k <= sigma_k: square root of the k-th largest Ritz value of A^T A on
+    span((A^T A)^(q+1) Om) (subspace iteration, each block orthonormalised before the next
+    product); Cauchy interlacing.  The powers of A^T A separate the spectrum fast enough that
+    a Krylov basis would not shrink ell measurably, at (q+1) times the Rayleigh-Ritz width."""
     n = A.shape[1]
     b = min(n, k + p)
     Y = _block_start(n, b, seed)
-    krylov = (q + 1) * b <= min(n, KRYLOV_MAX_COLS)
-    blocks = [_orth(Y)] if krylov else []
-    for _ in range(q):
+    for _ in range(q + 1):
         Y = A.T @ (A @ _orth(Y))
-        if krylov:
-            blocks.append(_orth(Y))
-    K = _orth(np.hstack(blocks)) if krylov else _orth(A.T @ (A @ _orth(Y)))
+    K = _orth(Y)
     C = A @ K
     H = C.T @ C
     H = 0.5 * (H + H.T)

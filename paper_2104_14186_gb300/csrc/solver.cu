@@ -398,37 +398,26 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   const double alpha = std::sqrt(std::max(hs.lst.out[2] + hs.lst.out[3], 0.0));
   if (!(alpha > 0.0)) return QDWHP_ERR_ARG;
 
-  // Relative threshold s from the k-th Ritz value of A^T A on the block Krylov space of k + p
-  // SplitMix64 vectors (only the last block when (q+1) b > 2048 columns).
+  // Relative threshold s from the k-th Ritz value of A^T A on span((A^T A)^(q+1) Om), Om of
+  // k + p SplitMix64 columns (subspace iteration, each block orthonormalised before the next
+  // product).
   const int64_t b = std::min<int64_t>(n, k + o.block_extra);
   const int q = o.power_steps > 0 ? o.power_steps : 2;
-  const bool krylov = (int64_t)(q + 1) * b <= std::min<int64_t>(n, kKrylovMaxCols);
-  const int64_t width = krylov ? (q + 1) * b : b;
+  const int64_t width = b;
   double* Y = w.q.Y;     // n x b
-  double* Kb = w.Vj;     // n x width
-  double* Qj = w.q.Z;    // n x b
+  double* Kb = w.Vj;     // n x b
   double* T1 = w.X;      // m x b
   QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Y, n));
   for (int j = 0; j <= q; ++j) {
-    // blocks stored dominant first (P^q Om leads): the R factor below is then graded with
-    // decreasing diagonal, the ordering under which Jacobi on R^T converges fastest
-    double* Qdst = krylov ? Kb + (int64_t)(q - j) * b * n : Qj;
-    QDWHP_TRY(orth(st, n, b, Y, Qdst, w.f, w.qr_scratch));
-    if (j < q || !krylov) {
-      QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Qdst, n, 0.0, T1, m));
-      QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Y, n));
-    }
-  }
-  if (krylov) {
-    QDWHP_TRY(copy_matrix(st, n, width, Kb, n, w.C, n));
-    QDWHP_TRY(orth(st, n, width, w.C, Kb, w.f, w.qr_scratch));
-  } else {
     QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
+    QDWHP_TRY(gemm(st, false, false, m, b, n, 1.0, A, lda, Kb, n, 0.0, T1, m));
+    QDWHP_TRY(gemm(st, true, false, n, b, m, 1.0, A, lda, T1, m, 0.0, Y, n));
   }
+  QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
   QDWHP_TRY(gemm(st, false, false, m, width, n, 1.0, A, lda, Kb, n, 0.0, w.C, m));
   // Ritz values of A^T A on span(K) are the squared singular values of C = A K = Q_C R, i.e. of
-  // R^T.  Forming C^T C instead would square the grading of K (its blocks span decades of
-  // sigma^2), and one-sided Jacobi on it then needs tens of sweeps; on R^T it needs about ten.
+  // R^T.  Forming C^T C instead would square the grading of the columns (they span decades of
+  // sigma^2), which slows one-sided Jacobi; on R^T it needs about ten sweeps.
   QDWHP_TRY(geqrf(st, m, width, w.C, m, w.q.qf, w.q.qr_scratch));
   double* G = w.W;
   QDWHP_TRY(copy_upper_t(st, width, w.C, m, G, width));
