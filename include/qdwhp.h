@@ -93,6 +93,7 @@ typedef struct {
   double conv[12];        /* ||X_k - X_{k-1}||_F after each QDWH step */
   float ms_total;         /* device time of the solve (CUDA events) */
   int32_t it_f32;         /* Cholesky-based steps run in FP32 (QDWHP_MIXED) */
+  int32_t dc_nodes;       /* EIG: spectral splits of the Rayleigh-Ritz problem (0 = Jacobi alone) */
 } qdwhp_info;
 
 QDWHP_API void qdwhp_default_opts(qdwhp_opts* opts);
@@ -129,6 +130,37 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
                                  const qdwhp_opts* opts, double* sigma, double* U, int64_t ldu,
                                  double* V, int64_t ldv, void* workspace, size_t ws_bytes,
                                  qdwhp_info* info, void* stream);
+
+/*
+ * Full symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG,
+ * Section 2.2, eq. pdeig): A - sigma I = U_p H, the projector (I + U_p) / 2 splits the
+ * spectrum at sigma (the mean eigenvalue), and the two Rayleigh-Ritz blocks are split
+ * again until they are small enough for one-sided Jacobi.  The same solver handles the
+ * Rayleigh-Ritz problems of qdwhp_eig when they are large.
+ *   A: n x n symmetric (both triangles stored; the average of A and A^T is used), lda >= n,
+ *      never modified.
+ *   lambda: n doubles, ascending.  V: n x n (ldv >= n), orthonormal eigenvectors in the
+ *      same order (signs unspecified).
+ *   workspace/ws_bytes: at least qdwhp_syev_workspace_bytes(n).
+ *   Errors: QDWHP_ERR_ARG (bad sizes or pointers, nothing launched), QDWHP_ERR_NOMEM
+ *   (workspace too small), QDWHP_ERR_NONFINITE (A holds NaN/Inf), QDWHP_ERR_NOT_CONVERGED
+ *   (a Jacobi leaf hit its sweep limit), QDWHP_ERR_BREAKDOWN (a Cholesky-based polar step
+ *   failed).  Synchronises `stream` at every split (it reads the split point and rank).
+ */
+typedef struct {
+  int32_t nodes;          /* spectral splits */
+  int32_t leaves;         /* Jacobi subproblems */
+  int32_t depth;          /* deepest split level */
+  int32_t qdwh_steps;     /* polar (QDWH) steps over all splits */
+  int32_t refinements;    /* extra subspace-iteration passes beyond the first */
+  int32_t jacobi_sweeps;  /* largest sweep count of a leaf */
+  double max_offblock;    /* largest ||Q2^T M Q1||_F / ||M - sigma I||_2 of a split */
+  float ms_total;         /* device time (CUDA events) */
+} qdwhp_syev_info;
+QDWHP_API size_t qdwhp_syev_workspace_bytes(int64_t n);
+QDWHP_API qdwhp_status qdwhp_syev_f64(const double* A, int64_t n, int64_t lda, double* lambda, double* V,
+                                      int64_t ldv, void* workspace, size_t ws_bytes, qdwhp_syev_info* info,
+                                      void* stream);
 
 /* ---- Request queue (serving) and batched solves; not part of the paper's method ---- */
 

@@ -24,6 +24,10 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                          LAPACK eigh/svd, Theorem 1 containment bound
   subspace size ell      parity unpinned (several ell are correct; only final
                          outputs are compared)
+  syev                   the definition (all eigenpairs); pinned: constructed
+                         spectra, brute-force Jacobi
+  full.split / qdwh_eig  pinned: rank(C) = #eigenvalues above sigma, C = V+ V+^T
+                         on known spectra; all eigenpairs against constructed spectra
 """
 
 from .rng import splitmix64, uniform_pm1  # noqa: F401
@@ -34,4 +38,6 @@ from .partial import (  # noqa: F401
     qdwhp_eig, qdwhp_svd, qdwhp_eig_negative, qdwhp_svd_threshold, index_from_diag,
 )
 from .jacobi import jacobi_eig  # noqa: F401
+from .full import syev  # noqa: F401
+from . import full  # noqa: F401
 from .metrics import eig_metrics, svd_metrics  # noqa: F401

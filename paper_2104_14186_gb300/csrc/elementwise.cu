@@ -78,6 +78,18 @@ __global__ void copy_upper_t_kernel(int N, const double* A, int64_t lda, double*
   }
 }
 
+__global__ void symmetrize_avg_kernel(int n, double* H, int64_t ldh) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) {
+      const double v = 0.5 * (H[i + (int64_t)j * ldh] + H[j + (int64_t)i * ldh]);
+      H[i + (int64_t)j * ldh] = v;
+      H[j + (int64_t)i * ldh] = v;
+    }
+  }
+}
+
 __global__ void symmetrize_kernel(int N, double* Y, int64_t ldy) {
   const size_t total = (size_t)N * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -195,6 +207,14 @@ qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const float* X, int6
 qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr) {
   if (n <= 0) return QDWHP_OK;
   copy_upper_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>((int)n, A, lda, R, ldr);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh) {
+  if (n <= 1) return QDWHP_OK;
+  const size_t total = (size_t)n * n;
+  symmetrize_avg_kernel<<<(int)std::min<size_t>((total + 255) / 256, 8 * kNumSMs), 256, 0, st>>>((int)n, H, ldh);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

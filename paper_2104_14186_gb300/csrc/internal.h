@@ -48,6 +48,8 @@ qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const float* X, int6
 qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr);
 // G (n x n) = R^T, R the upper triangle of the leading n x n block of A.
 qdwhp_status copy_upper_t(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* G, int64_t ldg);
+// H := (H + H^T) / 2 (n x n).
+qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh);
 // Fills the lower triangle's mirror: Y(i, j) = Y(j, i) for i < j (n x n).
 qdwhp_status symmetrize_from_lower(cudaStream_t st, int64_t n, double* Y, int64_t ldy);
 // Sum of kDiffParts partials -> out (device scalar); also checks finiteness of the sum.

@@ -121,10 +121,10 @@ __device__ void rotate_pair_warp(int p, int q, int mg, int nc, double* G, int64_
 
 // One full sweep (N - 1 rounds) in one cooperative launch: every warp takes pairs of the
 // round, and the grid meets at a barrier between rounds.
-constexpr int kSweepThreads = 64;   // two warps (pairs) per CTA, at most one CTA per SM
-__global__ void __launch_bounds__(kSweepThreads) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg,
-                                                                     double* Vj, int64_t ldv, double tol, int comp,
-                                                                     JacobiState* jst) {
+constexpr int kSweepMaxThreads = 512;   // up to 16 warps (pairs) per CTA, at most one CTA per SM
+__global__ void __launch_bounds__(kSweepMaxThreads) jacobi_sweep_kernel(int mg, int nc, int N, double* G, int64_t ldg,
+                                                                        double* Vj, int64_t ldv, double tol, int comp,
+                                                                        JacobiState* jst) {
   cg::grid_group grid = cg::this_grid();
   const int wpb = blockDim.x >> 5;
   const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
@@ -139,9 +139,16 @@ __global__ void __launch_bounds__(kSweepThreads) jacobi_sweep_kernel(int mg, int
   }
 }
 
-// CTAs for a sweep: enough warps for one pair each, at most one CTA per SM (the budget of
-// the cooperative-launch gate, which spreads the pairs over all SMs).
-int sweep_grid(int pairs) {
+// Launch shape of a sweep: at most one CTA per SM (the budget of the cooperative-launch gate).
+// A pair is one warp's work, and an SM's FP64 pipe is the bottleneck once it holds a few
+// warps, so the pairs are first spread over the SMs at two warps each; only when there are
+// more pairs than that (long rounds) does a CTA take more warps, up to 16, to hide the
+// latency of the column loads.
+struct SweepShape {
+  int grid;
+  int threads;
+};
+SweepShape sweep_shape(int pairs) {
   static std::once_flag once;
   static int max_blocks = 0;
   std::call_once(once, [] {
@@ -149,8 +156,10 @@ int sweep_grid(int pairs) {
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     max_blocks = sms;
   });
-  const int want = (pairs + kSweepThreads / 32 - 1) / (kSweepThreads / 32);
-  return std::max(1, std::min(want, max_blocks));
+  const int max_warps = kSweepMaxThreads / 32;
+  const int warps = std::max(2, std::min(max_warps, (pairs + max_blocks - 1) / max_blocks));
+  const int grid = std::max(1, std::min(max_blocks, (pairs + warps - 1) / warps));
+  return {grid, warps * 32};
 }
 
 __global__ void column_norms_kernel(int mg, const double* G, int64_t ldg, double* norms) {
@@ -223,7 +232,7 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     return QDWHP_OK;
   }
   const int N = (int)(nc + (nc & 1));
-  const int grid = sweep_grid(N / 2);
+  const SweepShape shape = sweep_shape(N / 2);
   // Converged when the largest normalised inner product of a sweep is <= tol, or, once it
   // is below sqrt(mg) u (the level of a plain dot product's rounding), when a sweep no
   // longer reduces it by 4x: rotations of that size only stir rounding noise.
@@ -235,7 +244,8 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     // compensated inner products only when they matter: a tight target, near convergence
     int comp = (tol < 1e-13 && prev < 1e-8) ? 1 : 0;
     void* args[] = {&mg_i, &nc_i, &N_i, &G, &ldg, &Vj, &ldv, &tol, &comp, &jst_dev};
-    QDWHP_TRY(launch_cooperative((const void*)jacobi_sweep_kernel, dim3(grid), dim3(kSweepThreads), args, 0, st));
+    QDWHP_TRY(launch_cooperative((const void*)jacobi_sweep_kernel, dim3(shape.grid), dim3(shape.threads), args, 0,
+                                 st));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
     QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
     *sweeps_out = sweep + 1;

@@ -17,6 +17,7 @@
 //   * QR-based QDWH steps while c_k > c_qr (default 100), Section 4.2.
 #include <cstdio>
 
+#include "dc.h"
 #include "internal.h"
 #include "krylov.h"
 #include "qdwh.h"
@@ -46,18 +47,6 @@ __global__ void index_scan_kernel(int n, const double* diagR, double tol, int* i
   if (threadIdx.x == 0) *ind = best;
 }
 
-__global__ void symmetrize_avg_kernel(int n, double* H, int64_t ldh) {
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    if (i < j) {
-      const double v = 0.5 * (H[i + (int64_t)j * ldh] + H[j + (int64_t)i * ldh]);
-      H[i + (int64_t)j * ldh] = v;
-      H[j + (int64_t)i * ldh] = v;
-    }
-  }
-}
-
 __global__ void transpose_kernel(int rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb) {
   // B (cols x rows) = A^T
   __shared__ double tile[32][33];
@@ -71,14 +60,6 @@ __global__ void transpose_kernel(int rows, int cols, const double* A, int64_t ld
     const int i = by + threadIdx.x, j = bx + k;   // B(i, j) = A(j, i)
     if (i < cols && j < rows) B[i + (int64_t)j * ldb] = tile[threadIdx.x][k];
   }
-}
-
-qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh) {
-  if (n <= 1) return QDWHP_OK;
-  const size_t total = (size_t)n * n;
-  symmetrize_avg_kernel<<<(int)std::min<size_t>((total + 255) / 256, 8 * kNumSMs), 256, 0, st>>>((int)n, H, ldh);
-  QDWHP_LAUNCH_CHECK();
-  return QDWHP_OK;
 }
 
 // Block Krylov bases of the count-to-threshold step wider than this keep only the last block.
@@ -173,6 +154,9 @@ struct EigWs {
   double* S1 = nullptr;  // n x n capacity: M (Rayleigh-Ritz matrix) / H
   double* S2 = nullptr;  // n x n capacity: G, then M V, then gathered W
   double* S3 = nullptr;  // n x n capacity: Vj
+  bool has_dc = false;   // n > kDcMin: Rayleigh-Ritz problems may need divide and conquer
+  DcWs dc;               // its own buffers; the large ones are lent from the above at run time
+  int dc_nodes = 0;      // splits of the last divide-and-conquer solve
 };
 
 void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
@@ -187,15 +171,34 @@ void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   w.S1 = ar.take<double>((size_t)n * n);
   w.S2 = ar.take<double>((size_t)n * n);
   w.S3 = ar.take<double>((size_t)n * n);
+  w.has_dc = n > kDcMin;
+  if (w.has_dc) carve_dc_own(ar, n, w.dc);
 }
 
-// Eigenvalues (Rayleigh quotients, into w.c.vals) and eigenvectors (S3) of the
-// symmetric ell x ell matrix in S1, whose spectrum lies above `lower`.
+// Eigenvalues (into w.c.vals) and eigenvectors (S3, ld ell) of the symmetric ell x ell
+// matrix in S1, whose spectrum lies in [lower, upper].  Up to kDcMin: one-sided Jacobi with
+// Rayleigh quotients; larger: QDWH spectral divide and conquer (S1 is then destroyed), run in
+// the buffers that are dead at this point (X, S2, the extraction QR, q.Z).
 // `values_only`: only the eigenvalues are used, and those are accurate to the square of
 // the Jacobi off-diagonal tolerance, so a loose tolerance (1e-9) is enough.
-qdwhp_status small_sym_eig(cudaStream_t st, int64_t ell, double lower, EigWs& w, int max_sweeps, HostScalars& hs,
-                           int* sweeps, bool values_only = false) {
+qdwhp_status small_sym_eig(cudaStream_t st, int64_t ell, double lower, double upper, uint64_t seed, EigWs& w,
+                           int max_sweeps, HostScalars& hs, int* sweeps, bool values_only = false) {
+  w.dc_nodes = 0;
   QDWHP_TRY(symmetrize_avg(st, ell, w.S1, ell));
+  if (ell > kDcMin && w.has_dc) {
+    DcWs dv = w.dc;
+    dv.M = w.S1;
+    dv.X = w.X;
+    dv.Q = w.S2;
+    dv.W = w.q.Z;
+    dv.f = w.f;
+    dv.qr_scratch = w.qr_scratch;
+    DcStats stats;
+    QDWHP_TRY(sym_eig_dc(st, ell, lower, upper, seed, !values_only, max_sweeps, w.c.vals, w.S3, ell, dv, &stats));
+    *sweeps = stats.jacobi_sweeps;
+    w.dc_nodes = stats.nodes;
+    return QDWHP_OK;
+  }
   // G = M - lower I is positive semidefinite; its right singular vectors are M's eigenvectors.
   QDWHP_TRY(axpby(st, ell, ell, 1.0, w.S1, ell, 0.0, w.S2, ell, -lower));
   int conv = 0;
@@ -272,7 +275,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   QDWHP_TRY(gemm(st, true, false, width, width, n, 1.0, Kb, n, AK, n, 0.0, w.S1, width, FULL, 0.0, w.c.splitk,
                  w.c.splitk_elems));
   int sweeps = 0;
-  QDWHP_TRY(small_sym_eig(st, width, lam_lo, w, o.jacobi_max_sweeps, hs, &sweeps, true));
+  QDWHP_TRY(small_sym_eig(st, width, lam_lo, lam_hi, o.seed, w, o.jacobi_max_sweeps, hs, &sweeps, true));
   QDWHP_TRY(select_sort(st, width, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
   QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
@@ -324,8 +327,9 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
       QDWHP_TRY(gemm(st, false, false, n, ell, n, 1.0, A, lda, Q2, n, 0.0, AQ2, n));
       QDWHP_TRY(gemm(st, true, false, ell, ell, n, 1.0, Q2, n, AQ2, n, 0.0, w.S1, ell, FULL, 0.0, w.c.splitk,
                      w.c.splitk_elems));
-      const double a_lo = th_min - r_min - 0.01 * spread;   // lower bound of A's spectrum
-      QDWHP_TRY(small_sym_eig(st, ell, a_lo, w, o.jacobi_max_sweeps, hs, &sweeps));
+      const double a_lo = th_min - r_min - 0.01 * spread;   // bounds of A's spectrum
+      const double a_hi = th_max + r_max + 0.01 * spread;
+      QDWHP_TRY(small_sym_eig(st, ell, a_lo, a_hi, o.seed, w, o.jacobi_max_sweeps, hs, &sweeps));
       inf.jacobi_sweeps = sweeps;
       // wanted: eps * theta <= t, ordered ascending in eps * theta
       QDWHP_TRY(select_sort(st, ell, w.c.vals, eps_side, t, w.c.order, w.c.ints + 1));
@@ -349,6 +353,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   inf.k = k;
   inf.t = eps_side * t;
   inf.mu = eps_side * mu;
+  inf.dc_nodes = w.dc_nodes;
   if (info) *info = inf;
   return QDWHP_OK;
 }

@@ -47,7 +47,7 @@ class Info(C.Structure):
         ("it_qr", C.c_int32), ("it_chol", C.c_int32), ("retries", C.c_int32), ("jacobi_sweeps", C.c_int32),
         ("ell", C.c_int64), ("k", C.c_int64), ("t", C.c_double), ("mu", C.c_double), ("s", C.c_double),
         ("alpha", C.c_double), ("ell_k", C.c_double * 12), ("conv", C.c_double * 12), ("ms_total", C.c_float),
-        ("it_f32", C.c_int32),
+        ("it_f32", C.c_int32), ("dc_nodes", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -56,6 +56,17 @@ class Info(C.Structure):
         d["ell_k"] = list(self.ell_k)[:n]
         d["conv"] = list(self.conv)[:n]
         return d
+
+
+class SyevInfo(C.Structure):
+    _fields_ = [
+        ("nodes", C.c_int32), ("leaves", C.c_int32), ("depth", C.c_int32), ("qdwh_steps", C.c_int32),
+        ("refinements", C.c_int32), ("jacobi_sweeps", C.c_int32), ("max_offblock", C.c_double),
+        ("ms_total", C.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class QdwhpError(RuntimeError):
@@ -82,6 +93,8 @@ SIGNATURES = {
     "qdwhp_svd_workspace_bytes": (C.c_size_t, [I64, I64, C.POINTER(Opts)]),
     "qdwhp_svd": (C.c_int, [P, I64, I64, I64, I64, C.POINTER(Opts), P, P, I64, P, I64, P, C.c_size_t,
                             C.POINTER(Info), P]),
+    "qdwhp_syev_workspace_bytes": (C.c_size_t, [I64]),
+    "qdwhp_syev_f64": (C.c_int, [P, I64, I64, P, P, I64, P, C.c_size_t, C.POINTER(SyevInfo), P]),
     "qdwhp_gemm_f64": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P]),
     "qdwhp_potrf_workspace_bytes": (C.c_size_t, [I64]),
     "qdwhp_potrf_f64": (C.c_int, [I64, P, I64, P, C.c_size_t, C.POINTER(C.c_int), P]),
@@ -207,6 +220,25 @@ def eig(A: torch.Tensor, k: int | None = None, fraction: float | None = None, si
                          _stream(stream))
     _check(st, "qdwhp_eig")
     return EigResult(lam[:kk], Vt[:kk].t(), info.as_dict())
+
+
+def syev(A: torch.Tensor, ws: torch.Tensor | None = None, stream=None):
+    """qdwhp_syev_f64: all eigenpairs of the symmetric CUDA float64 matrix A (ascending).
+    Returns (lam, V, info dict)."""
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("A must be square")
+    Ac = _colmajor(A)
+    lam = torch.empty(n, dtype=torch.float64, device=A.device)
+    Vt = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    need = lib().qdwhp_syev_workspace_bytes(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    info = SyevInfo()
+    st = lib().qdwhp_syev_f64(_ptr(Ac), n, n, _ptr(lam), _ptr(Vt), n, _ptr(ws), ws.numel(), C.byref(info),
+                              _stream(stream))
+    _check(st, "qdwhp_syev_f64")
+    return lam, Vt.t(), info.as_dict()
 
 
 def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws: torch.Tensor | None = None,
