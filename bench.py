@@ -381,7 +381,7 @@ def run_eig_large(args):
                       "ms_median": 1e3 * t, "solves_per_s": 1 / t, "alg_tflops": fl / t / 1e12,
                       "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9,
                       "gemm_share": prof["gemm_ms"] / sum(ms), "lam_err": err, "resid": res,
-                      "jacobi_sweeps": r.info["jacobi_sweeps"]}), flush=True)
+                      "jacobi_sweeps": r.info["jacobi_sweeps"], "dc_nodes": r.info["dc_nodes"]}), flush=True)
 
 
 def run_batched(args):
@@ -444,15 +444,19 @@ def run_serve(args):
     prec = Q.MIXED if args.precision == "mixed" else Q.FP64
     extra = {"precision": prec}
     svd_extra = dict(extra, refine_steps=args.refine)
-    # service-time calibration: a few requests one at a time
+    # capacity calibration: the first 64 requests submitted at once (the queue runs them
+    # concurrently); the arrival rate is 80 % of that throughput
     q = Q.Queue(args.budget_gb << 30, max_slots=args.concurrency)
+    ncal = min(64, len(prep))
     t0 = time.perf_counter()
-    for kind, A, k in prep[:8]:
-        rid = q.submit_eig(A, k, **extra) if kind == "eig" else q.submit_svd(A, k, **svd_extra)
-        q.wait(rid)
+    cal = [q.submit_eig(A, k, **extra) if kind == "eig" else q.submit_svd(A, k, **svd_extra)
+           for kind, A, k in prep[:ncal]]
+    for rid in cal:
+        q.wait(rid, 3600000)
         q.release(rid)
-    mean_service = (time.perf_counter() - t0) / 8
-    rate = 0.8 * args.concurrency / mean_service if args.rate <= 0 else args.rate
+    capacity = ncal / (time.perf_counter() - t0)
+    mean_service = 1.0 / capacity
+    rate = 0.8 * capacity if args.rate <= 0 else args.rate
     arrivals = np.cumsum(gaps / rate)
     torch.cuda.synchronize()
     start = time.perf_counter()
@@ -472,7 +476,7 @@ def run_serve(args):
     print(json.dumps({"workload": f"serving: {args.count} Poisson-arrival requests, EIG n in [128, 2048], "
                                   f"SVD n in [128, 1024] m in [n, 2n], fractions 1-20 %",
                       "precision": args.precision, "refine_steps": args.refine, "concurrency": args.concurrency,
-                      "arrival_rate_per_s": rate, "mean_service_s": mean_service,
+                      "arrival_rate_per_s": rate, "calibrated_capacity_per_s": capacity,
                       "solves_per_s": len(ids) / (end - t_first),
                       "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}),
           flush=True)

@@ -12,7 +12,7 @@ stated at the step and listed in the design notes:
     on the k-th eigenvalue (Cauchy interlacing), so a threshold there captures at
     least k wanted eigenpairs.  EIG: the block Krylov space of k+p starting vectors
     and q products with a positive semidefinite shift of the operator (only the
-    last block when that basis would exceed 2048 columns).  SVD: subspace
+    last block when that basis would exceed min(n/8, 2048) columns).  SVD: subspace
     iteration, q+1 products of A^T A with k+p vectors.
   * Threshold placement guard: the wanted interval is kept at least 10 % of the
     spectral spread wide, so that the unwanted side is never scaled by more
@@ -138,7 +138,10 @@ def _orth(Y: np.ndarray) -> np.ndarray:
     return np.linalg.qr(Y, mode="reduced")[0]
 
 
-KRYLOV_MAX_COLS = 2048   # block Krylov basis width limit; wider uses the last power block only
+# A block Krylov basis is used only while it has at most min(n / 8, 2048) columns; a wider
+# one would cost a Rayleigh-Ritz problem comparable to the solve itself, and the last
+# power block alone is kept instead.
+KRYLOV_MAX_COLS = 2048
 
 
 def threshold_from_count_eig(A: np.ndarray, eps_side: float, k: int, lam_hi: float,
@@ -149,12 +152,13 @@ def threshold_from_count_eig(A: np.ndarray, eps_side: float, k: int, lam_hi: flo
     semidefinite, dominant part = the wanted small end of A'), each block orthonormalised
     before the next product; Rayleigh-Ritz of A' on K.  By Cauchy interlacing the k-th
     smallest Ritz value is >= the k-th smallest eigenvalue, so it is a valid threshold.
-    When (q+1)(k+p) exceeds KRYLOV_MAX_COLS only the last block is kept (subspace iteration).
+    When (q+1)(k+p) exceeds min(n/8, KRYLOV_MAX_COLS) only the last block is kept (subspace
+    iteration).
     """
     n = A.shape[0]
     b = min(n, k + p)
     Y = _block_start(n, b, seed)
-    krylov = (q + 1) * b <= min(n, KRYLOV_MAX_COLS)
+    krylov = (q + 1) * b <= min(n // 8, KRYLOV_MAX_COLS)
     blocks = [_orth(Y)] if krylov else []
     for _ in range(q):
         Qy = _orth(Y)

@@ -62,7 +62,8 @@ __global__ void transpose_kernel(int rows, int cols, const double* A, int64_t ld
   }
 }
 
-// Block Krylov bases of the count-to-threshold step wider than this keep only the last block.
+// Block Krylov bases of the count-to-threshold step wider than min(n / 8, this) keep only the
+// last block: a wider basis would make its Rayleigh-Ritz problem cost as much as the solve.
 constexpr int64_t kKrylovMaxCols = 2048;
 // Stopping tolerance of the reduced-problem Jacobi when its vectors are used: the
 // normalised off-diagonal inner products (computed in double-double) down to ~2u.
@@ -247,10 +248,10 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
 
   // Threshold for the requested count: block Krylov space of P = lam_hi I - A' from k + p
   // SplitMix64 vectors (each block orthonormalised before the next product), Rayleigh-Ritz of A'
-  // on it; when (q+1) b > 2048 columns only the last block, P^(q+1) Om, is kept.
+  // on it; when (q+1) b > min(n/8, 2048) columns only the last block, P^(q+1) Om, is kept.
   const int64_t b = std::min<int64_t>(n, k + o.block_extra);
   const int q = o.power_steps > 0 ? o.power_steps : 6;
-  const bool krylov = (int64_t)(q + 1) * b <= std::min<int64_t>(n, kKrylovMaxCols);
+  const bool krylov = (int64_t)(q + 1) * b <= std::min<int64_t>(n / 8, kKrylovMaxCols);
   const int64_t width = krylov ? (q + 1) * b : b;
   double* Y = w.X;           // n x b
   double* Kb = w.S3;         // n x width
