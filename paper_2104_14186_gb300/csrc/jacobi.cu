@@ -34,6 +34,61 @@ __device__ __forceinline__ void pair_of(int r, int h, int N, int& p, int& q) {
   }
 }
 
+// Per-lane sums of one row: ||g_p||^2, ||g_q||^2 plainly, g_p^T g_q in double-double
+// (TwoProduct, then TwoSum into (c, ce)).
+__device__ __forceinline__ void accumulate_comp(double x, double y, double& a, double& b, double& c, double& ce) {
+  a = fma(x, x, a);
+  b = fma(y, y, b);
+  const double pr = x * y;
+  const double pe = fma(x, y, -pr);
+  const double t = c + pr;
+  const double z = t - c;
+  ce += ((c - (t - z)) + (pr - z)) + pe;
+  c = t;
+}
+
+// Warp sum of the double-double (c, ce) with TwoSum at every level; returns c + ce.
+__device__ __forceinline__ double warp_sum_comp(double c, double ce) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double c2 = __shfl_xor_sync(0xffffffffu, c, o), e2 = __shfl_xor_sync(0xffffffffu, ce, o);
+    const double t = c + c2;
+    const double z = t - c;
+    ce += e2 + ((c - (t - z)) + (c2 - z));
+    c = t;
+  }
+  return c + ce;
+}
+
+// Lane 0 records the normalised inner product and, when it exceeds tol, forms the rotation
+// that orthogonalises the pair; the decision and (cs, sn) are broadcast to the warp.
+__device__ __forceinline__ int rotation_from_sums(double a, double b, double c, double tol, JacobiState* jst,
+                                                  double& cs, double& sn) {
+  const int lane = threadIdx.x & 31;
+  int do_rot = 0;
+  cs = 1.0;
+  sn = 0.0;
+  if (lane == 0) {
+    if (!isfinite(a) || !isfinite(b) || !isfinite(c)) {
+      atomicExch(&jst->nonfinite, 1);
+    } else if (a > 0.0 && b > 0.0 && c != 0.0) {
+      const double off = fabs(c) / sqrt(a * b);
+      atomicMax(&jst->max_off_bits, (unsigned long long)__double_as_longlong(off));
+      if (off > tol) {
+        const double zeta = (b - a) / (2.0 * c);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        cs = 1.0 / sqrt(1.0 + t * t);
+        sn = cs * t;
+        do_rot = 1;
+      }
+    }
+  }
+  do_rot = __shfl_sync(0xffffffffu, do_rot, 0);
+  cs = __shfl_sync(0xffffffffu, cs, 0);
+  sn = __shfl_sync(0xffffffffu, sn, 0);
+  return do_rot;
+}
+
 // Orthogonalise columns p and q of G (length mg) and rotate the same columns of Vj
 // (length nc), by one warp: the lanes stride over the rows, the sums are combined with
 // shuffles, lane 0 forms the rotation and broadcasts it.  ||g_p||^2 and ||g_q||^2 are
@@ -53,26 +108,8 @@ __device__ void rotate_pair_warp(int p, int q, int mg, int nc, double* G, int64_
   double* gq = G + (int64_t)q * ldg;
   double a = 0.0, b = 0.0, c = 0.0, ce = 0.0;
   if (comp) {
-    for (int i = lane; i < mg; i += 32) {
-      const double x = gp[i], y = gq[i];
-      a = fma(x, x, a);
-      b = fma(y, y, b);
-      const double pr = x * y;
-      const double pe = fma(x, y, -pr);
-      const double t = c + pr;
-      const double z = t - c;
-      ce += ((c - (t - z)) + (pr - z)) + pe;
-      c = t;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double c2 = __shfl_xor_sync(0xffffffffu, c, o), e2 = __shfl_xor_sync(0xffffffffu, ce, o);
-      const double t = c + c2;
-      const double z = t - c;
-      ce += e2 + ((c - (t - z)) + (c2 - z));
-      c = t;
-    }
-    c += ce;
+    for (int i = lane; i < mg; i += 32) accumulate_comp(gp[i], gq[i], a, b, c, ce);
+    c = warp_sum_comp(c, ce);
   } else {
     for (int i = lane; i < mg; i += 32) {
       const double x = gp[i], y = gq[i];
@@ -84,27 +121,8 @@ __device__ void rotate_pair_warp(int p, int q, int mg, int nc, double* G, int64_
   }
   a = warp_sum(a);
   b = warp_sum(b);
-  int do_rot = 0;
-  double cs = 1.0, sn = 0.0;
-  if (lane == 0) {
-    if (!isfinite(a) || !isfinite(b) || !isfinite(c)) {
-      atomicExch(&jst->nonfinite, 1);
-    } else if (a > 0.0 && b > 0.0 && c != 0.0) {
-      const double off = fabs(c) / sqrt(a * b);
-      atomicMax(&jst->max_off_bits, (unsigned long long)__double_as_longlong(off));
-      if (off > tol) {
-        const double zeta = (b - a) / (2.0 * c);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        cs = 1.0 / sqrt(1.0 + t * t);
-        sn = cs * t;
-        do_rot = 1;
-      }
-    }
-  }
-  do_rot = __shfl_sync(0xffffffffu, do_rot, 0);
-  if (!do_rot) return;
-  cs = __shfl_sync(0xffffffffu, cs, 0);
-  sn = __shfl_sync(0xffffffffu, sn, 0);
+  double cs, sn;
+  if (!rotation_from_sums(a, b, c, tol, jst, cs, sn)) return;
   for (int i = lane; i < mg; i += 32) {
     const double x = gp[i], y = gq[i];
     gp[i] = cs * x - sn * y;
@@ -116,6 +134,74 @@ __device__ void rotate_pair_warp(int p, int q, int mg, int nc, double* G, int64_
     const double x = vp[i], y = vq[i];
     vp[i] = cs * x - sn * y;
     vq[i] = sn * x + cs * y;
+  }
+}
+
+// The same pair update for columns of at most 32 R rows (mg, nc <= 32 R): the four columns
+// are loaded into registers once, up front, so a pair costs one round trip to L2 instead of
+// one per 32 rows; the arithmetic and its order are those of rotate_pair_warp.
+template <int R>
+__device__ void rotate_pair_warp_reg(int p, int q, int mg, int nc, double* G, int64_t ldg, double* Vj, int64_t ldv,
+                                     double tol, int comp, JacobiState* jst) {
+  const int lane = threadIdx.x & 31;
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+  double* gp = G + (int64_t)p * ldg;
+  double* gq = G + (int64_t)q * ldg;
+  double* vp = Vj + (int64_t)p * ldv;
+  double* vq = Vj + (int64_t)q * ldv;
+  double x[R], y[R], u[R], v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    x[r] = i < mg ? gp[i] : 0.0;
+    y[r] = i < mg ? gq[i] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    u[r] = i < nc ? vp[i] : 0.0;
+    v[r] = i < nc ? vq[i] : 0.0;
+  }
+  double a = 0.0, b = 0.0, c = 0.0, ce = 0.0;
+  if (comp) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (lane + 32 * r < mg) accumulate_comp(x[r], y[r], a, b, c, ce);
+    c = warp_sum_comp(c, ce);
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (lane + 32 * r < mg) {
+        a = fma(x[r], x[r], a);
+        b = fma(y[r], y[r], b);
+        c = fma(x[r], y[r], c);
+      }
+    }
+    c = warp_sum(c);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  double cs, sn;
+  if (!rotation_from_sums(a, b, c, tol, jst, cs, sn)) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < mg) {
+      gp[i] = cs * x[r] - sn * y[r];
+      gq[i] = sn * x[r] + cs * y[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < nc) {
+      vp[i] = cs * u[r] - sn * v[r];
+      vq[i] = sn * u[r] + cs * v[r];
+    }
   }
 }
 
@@ -139,6 +225,27 @@ __global__ void __launch_bounds__(kSweepMaxThreads) jacobi_sweep_kernel(int mg, 
   }
 }
 
+// Sweep kernel of the register-resident pair update (columns of at most 32 R rows).
+constexpr int kSweepRegMaxThreads = 256;
+template <int R>
+__global__ void __launch_bounds__(kSweepRegMaxThreads) jacobi_sweep_reg_kernel(int mg, int nc, int N, double* G,
+                                                                               int64_t ldg, double* Vj, int64_t ldv,
+                                                                               double tol, int comp,
+                                                                               JacobiState* jst) {
+  cg::grid_group grid = cg::this_grid();
+  const int wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nw = gridDim.x * wpb;
+  for (int r = 0; r < N - 1; ++r) {
+    for (int h = gw; h < N / 2; h += nw) {
+      int p, q;
+      pair_of(r, h, N, p, q);
+      if (p < nc && q < nc) rotate_pair_warp_reg<R>(p, q, mg, nc, G, ldg, Vj, ldv, tol, comp, jst);
+    }
+    grid.sync();
+  }
+}
+
 // Launch shape of a sweep: at most one CTA per SM (the budget of the cooperative-launch gate).
 // A pair is one warp's work, and an SM's FP64 pipe is the bottleneck once it holds a few
 // warps, so the pairs are first spread over the SMs at two warps each; only when there are
@@ -148,7 +255,7 @@ struct SweepShape {
   int grid;
   int threads;
 };
-SweepShape sweep_shape(int pairs) {
+SweepShape sweep_shape(int pairs, int max_threads) {
   static std::once_flag once;
   static int max_blocks = 0;
   std::call_once(once, [] {
@@ -156,7 +263,7 @@ SweepShape sweep_shape(int pairs) {
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     max_blocks = sms;
   });
-  const int max_warps = kSweepMaxThreads / 32;
+  const int max_warps = max_threads / 32;
   const int warps = std::max(2, std::min(max_warps, (pairs + max_blocks - 1) / max_blocks));
   const int grid = std::max(1, std::min(max_blocks, (pairs + warps - 1) / warps));
   return {grid, warps * 32};
@@ -232,7 +339,19 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     return QDWHP_OK;
   }
   const int N = (int)(nc + (nc & 1));
-  const SweepShape shape = sweep_shape(N / 2);
+  // columns of at most 512 rows stay in registers during a pair update
+  const int64_t len = std::max(mg, nc);
+  const void* fn = (const void*)jacobi_sweep_kernel;
+  int max_threads = kSweepMaxThreads;
+  if (len <= 128) {
+    fn = (const void*)jacobi_sweep_reg_kernel<4>;
+  } else if (len <= 256) {
+    fn = (const void*)jacobi_sweep_reg_kernel<8>;
+  } else if (len <= 512) {
+    fn = (const void*)jacobi_sweep_reg_kernel<16>;
+  }
+  if (len <= 512) max_threads = kSweepRegMaxThreads;
+  const SweepShape shape = sweep_shape(N / 2, max_threads);
   // Converged when the largest normalised inner product of a sweep is <= tol, or, once it
   // is below sqrt(mg) u (the level of a plain dot product's rounding), when a sweep no
   // longer reduces it by 4x: rotations of that size only stir rounding noise.
@@ -244,8 +363,7 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     // compensated inner products only when they matter: a tight target, near convergence
     int comp = (tol < 1e-13 && prev < 1e-8) ? 1 : 0;
     void* args[] = {&mg_i, &nc_i, &N_i, &G, &ldg, &Vj, &ldv, &tol, &comp, &jst_dev};
-    QDWHP_TRY(launch_cooperative((const void*)jacobi_sweep_kernel, dim3(shape.grid), dim3(shape.threads), args, 0,
-                                 st));
+    QDWHP_TRY(launch_cooperative(fn, dim3(shape.grid), dim3(shape.threads), args, 0, st));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(jst_host, jst_dev, sizeof(JacobiState), cudaMemcpyDeviceToHost, st));
     QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
     *sweeps_out = sweep + 1;
