@@ -5,7 +5,7 @@
  * Method: Keyes, Ltaief, Nakatsukasa, Sukkari, "High-Performance Partial Spectrum
  * Computation for Symmetric eigenvalue problems and the SVD" (arXiv 2104.14186):
  * Algorithm 1 (QDWHpartial-EIG), Algorithm 2 (QDWHpartial-SVD), the QDWH steps of
- * Section 2.1 (eqs. practical-polar-qr and practical-polar-chol) and the index rule
+ * Section 3.1 (eqs. practical-polar-qr and practical-polar-chol) and the index rule
  * of Section 4.1.
  *
  * Conventions for every entry point below:
@@ -64,7 +64,7 @@ typedef struct {
   double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
   int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */
   int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
-  double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.01) */
+  double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.1; the paper prints 0.01) */
   double c_qr;            /* SVD: QR-based step while c_k > c_qr (default 100) */
   int32_t block_extra;    /* p: the count-to-threshold subspace starts from k + p vectors (16) */
   int32_t power_steps;    /* q: products with the operator; 0 = automatic.  EIG: block Krylov space of
@@ -133,7 +133,7 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
 
 /*
  * Full symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG,
- * Section 2.2, eq. pdeig): A - sigma I = U_p H, the projector (I + U_p) / 2 splits the
+ * Section 3.2, eq. pdeig): A - sigma I = U_p H, the projector (I + U_p) / 2 splits the
  * spectrum at sigma (the mean eigenvalue), and the two Rayleigh-Ritz blocks are split
  * again until they are small enough for one-sided Jacobi.  The same solver handles the
  * Rayleigh-Ritz problems of qdwhp_eig when they are large.

@@ -1,10 +1,10 @@
-"""Full symmetric eigendecomposition: QDWH-EIG (Section 2.2), plain FP64.
+"""Full symmetric eigendecomposition: QDWH-EIG (Section 3.2), plain FP64.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 QDWH-EIG reaches, up to rounding, a result with a plain definition: every eigenpair
 of the symmetric matrix.  `syev` is that definition (the LAPACK symmetric eigensolver
-is its one step).  `qdwh_eig` follows the method of Section 2.2 step by step, as a
+is its one step).  `qdwh_eig` follows the method of Section 3.2 step by step, as a
 second, structural oracle: write A - sigma I = U_p H (eq. pdeig), so that
 C = (I + U_p) / 2 = V_+ V_+^T projects onto the eigenvectors with eigenvalues above
 sigma; take orthonormal bases of range(C) and of its complement, project A on each
@@ -33,7 +33,7 @@ def syev(A: np.ndarray):
 
 
 def split(A: np.ndarray, sigma: float, alpha: float):
-    """One spectral split (Section 2.2): U_p of (A - sigma I) / alpha, C = (I + U_p) / 2,
+    """One spectral split (Section 3.2): U_p of (A - sigma I) / alpha, C = (I + U_p) / 2,
     r = round(trace C), [V1 V2] orthonormal with range(V1) = range(C).  Returns (r, V1, V2, C)."""
     n = A.shape[0]
     B = A - sigma * np.eye(n)
@@ -48,7 +48,7 @@ def split(A: np.ndarray, sigma: float, alpha: float):
 
 def qdwh_eig(A: np.ndarray, lo: float, hi: float, leaf: int = 64):
     """All eigenpairs of symmetric A with spectrum in [lo, hi] by recursive spectral
-    splitting (Section 2.2).  Returns (lam, V), unordered."""
+    splitting (Section 3.2).  Returns (lam, V), unordered."""
     A = 0.5 * (A + A.T)
     n = A.shape[0]
     if n <= leaf or hi - lo <= 1e-14 * max(abs(lo), abs(hi), 1e-300):

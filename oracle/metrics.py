@@ -1,4 +1,4 @@
-"""Accuracy metrics (Section 6.3, eqs. orth, sv, allsv) plus the normwise forms
+"""Accuracy metrics (Section 7.3, eqs. orth, sv, allsv) plus the normwise forms
 used as acceptance tolerances:
 
   eigenvalue error     max_i |lambda_i - lambda*_i| / ||A||_2

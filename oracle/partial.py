@@ -21,6 +21,13 @@ stated at the step and listed in the design notes:
     at a 5 % guard the residual reached 4e-13 on a uniform spectrum).
   * QR step while c_k > 100, Cholesky step otherwise (Section 4.2 asks for a
     QR-based first step when s is small).
+  * Index rule tolerance 0.1 for the solvers (the printed algorithms use 0.01).
+    Section 4.1 bounds the containment of the wanted subspace by u / sigma_min(R11)
+    and asks for sigma_min(R11) >= tol = Omega(1), reading sigma_min(R11) off diag(R)
+    on the grounds that the QR is rank revealing; without pivoting or a random
+    Omega it is not quite, and at tol = 0.01 the residuals reached 2.1e-13 (EIG, n =
+    512) and 1.2e-13 (SVD transposed residual), against 2.3e-14 and 1.4e-14 at 0.1,
+    for about 5 % (EIG) and 10-20 % (SVD) more captured columns.
 """
 
 from __future__ import annotations
@@ -45,7 +52,7 @@ class EigOptions:
     side: str = "largest"       # "largest" or "smallest"
     s: float = 0.2              # shift and ell_0 (Algorithm 1 step 2)
     iters: int = 3              # QDWH iterations (three for s = 0.2, two for s = 0.875)
-    tol: float = 0.01           # index rule tolerance (Algorithm 1 step 4)
+    tol: float = 0.1            # index rule tolerance (Algorithm 1 step 4; see the module notes)
     lanczos_steps: int = 30
     block_extra: int = 16       # p in the (k+p)-dimensional threshold subspace
     power_steps: int = 6        # q (block Krylov depth)
@@ -57,7 +64,7 @@ class EigOptions:
 @dataclass
 class SvdOptions:
     k: int
-    tol: float = 0.01
+    tol: float = 0.1
     c_qr: float = 100.0         # QR-based step while c_k > c_qr
     lanczos_steps: int = 30
     block_extra: int = 16

@@ -1,6 +1,6 @@
 """QDWH iteration: dynamical weights and the two practical step forms (FP64).
 
-Section 2.1 of the paper.  The iteration (eq. polar-itr) is
+Section 3.1 of the paper.  The iteration (eq. polar-itr) is
     X_{k+1} = X_k (a_k I + b_k X_k^T X_k)(I + c_k X_k^T X_k)^{-1},
 whose scalar form is r_k(x) = x (a_k + b_k x^2) / (1 + c_k x^2); it is never
 evaluated in that inverse form.  The two step forms used instead are the
@@ -25,7 +25,7 @@ def dwh_weights(ell: float) -> tuple[float, float, float, float]:
     """Weights (a, b, c) of the (3,2) Zolotarev step for the interval [ell, 1]
     and the updated lower bound ell_next = r(ell).
 
-    Section 2.1 (weights chosen so that r_k is the scaled Zolotarev function of
+    Section 3.1 (weights chosen so that r_k is the scaled Zolotarev function of
     type (3,2) on [-1,-ell] U [ell,1], ell_k = r_k(ell_{k-1})) and the weight
     lines of the Section 5 listing:
         L2 = ell^2,  d = cbrt(4 (1 - L2) / L2^2),
@@ -70,7 +70,7 @@ def dwh_schedule(ell0: float, max_iter: int = 12, fixed_iters: int | None = None
 
 
 def rational_map(x, a: float, b: float, c: float):
-    """Scalar r(x) = x (a + b x^2) / (1 + c x^2) (Section 2.1)."""
+    """Scalar r(x) = x (a + b x^2) / (1 + c x^2) (Section 3.1)."""
     x = np.asarray(x, dtype=np.float64)
     return x * (a + b * x * x) / (1.0 + c * x * x)
 
@@ -103,7 +103,7 @@ def qdwh_qr_step(X: np.ndarray, a: float, b: float, c: float) -> np.ndarray:
 
 
 def qdwh_polar(A: np.ndarray, alpha: float, ell0: float, c_qr: float = 100.0, max_iter: int = 12):
-    """Full QDWH polar decomposition A = U_p H (Section 2.1): X_0 = A / alpha,
+    """Full QDWH polar decomposition A = U_p H (Section 3.1): X_0 = A / alpha,
     QR-based steps while c_k > c_qr, Cholesky-based afterwards, until ell reaches
     1 within 5 eps.  Returns (U_p, H, schedule)."""
     X = A / alpha

@@ -1,4 +1,4 @@
-// Symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG, Section 2.2).
+// Symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG, Section 3.2).
 //
 // A node holds a symmetric matrix M (order nl) whose spectrum lies in [lo, hi].  It picks a
 // split point sigma (the mean eigenvalue, trace / nl), computes the polar factor U_p of

@@ -1,5 +1,5 @@
 // Internal interface of dc.cu: symmetric eigendecomposition by QDWH spectral divide and
-// conquer (QDWH-EIG, Section 2.2), the reduced eigensolver for large Rayleigh-Ritz problems
+// conquer (QDWH-EIG, Section 3.2), the reduced eigensolver for large Rayleigh-Ritz problems
 // and the full-spectrum entry point.
 #pragma once
 

@@ -1,4 +1,4 @@
-// QDWH iteration (Section 2.1): dynamical weights on the device and the two
+// QDWH iteration (Section 3.1): dynamical weights on the device and the two
 // practical step forms.
 //   Cholesky-based (eq. practical-polar-chol):
 //     Z = I + c X^T X (lower SYRK with the identity folded into the epilogue),
@@ -14,7 +14,7 @@ namespace qdwhp {
 
 namespace {
 
-// Weights of every step from ell_0 (Section 2.1 and the weight lines of the Section 5
+// Weights of every step from ell_0 (Section 3.1 and the weight lines of the Section 5
 // listing): L2 = l^2, d = cbrt(4(1 - L2)/L2^2), a = sqrt(1+d) + sqrt(8 - 4d + 8(2 - L2)/(L2 sqrt(1+d)))/2,
 // b = (a-1)^2/4, c = a + b - 1, l <- l (a + b L2)/(1 + c L2).  Stops when |l - 1| < 5 * 2^-52
 // or after fixed_iters steps when fixed_iters > 0.

@@ -550,7 +550,7 @@ QDWHP_API void qdwhp_default_opts(qdwhp_opts* o) {
   o->s_eig = 0.2;
   o->iters_eig = 3;
   o->lanczos_steps = 30;
-  o->tol = 0.01;
+  o->tol = 0.1;
   o->c_qr = 100.0;
   o->block_extra = 16;
   o->power_steps = 0;   // automatic: 6 for EIG, 2 for SVD

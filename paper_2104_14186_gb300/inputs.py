@@ -3,7 +3,7 @@
 These generators build the inputs that the solver, its tests and the benchmark
 share.  They hold none of the solver's arithmetic: each matrix is assembled as
 ``Q1 diag(d) Q2^T`` from Haar-distributed orthogonal factors, the construction
-the paper's experiments use (Section 6.2: matrices from PDLATMS, mode 0, with
+the paper's experiments use (Section 7.2: matrices from PDLATMS, mode 0, with
 orthogonal factors taken from the QR factorization of random matrices; Q1 = Q2
 for the symmetric case).  The spectra follow the workload definitions below.
 
@@ -100,7 +100,7 @@ def svd_logspaced(m: int, n: int, seed: int, fraction: float = 0.05, decades: fl
 
 
 def svd_geometric_half(n: int, seed: int) -> SvdProblem:
-    """The paper's SVD test spectrum (Section 6.2): D[i] = 0.5^(100 i / n)."""
+    """The paper's SVD test spectrum (Section 7.2): D[i] = 0.5^(100 i / n)."""
     rng = np.random.default_rng(seed)
     i = np.arange(n, dtype=np.float64)
     sigma = 0.5 ** (100.0 * i / n)

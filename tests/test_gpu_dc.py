@@ -1,4 +1,4 @@
-"""GPU parity of the QDWH spectral divide-and-conquer eigensolver (QDWH-EIG, Section 2.2),
+"""GPU parity of the QDWH spectral divide-and-conquer eigensolver (QDWH-EIG, Section 3.2),
 through the C ABI: qdwhp_syev_f64 against the definition (all eigenpairs of the symmetric
 matrix: the oracle's syev and the constructed spectrum), and the partial EIG solver on
 problems whose Rayleigh-Ritz step is large enough to take the divide-and-conquer route.

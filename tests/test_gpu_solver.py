@@ -16,11 +16,10 @@ torch = pytest.importorskip("torch")
 LAM_TOL = 1e-12
 ORTH_TOL = 5e-15
 RES_TOL = 1e-13
-# SVD: ||A V - U S||_F / ||A||_F, the direct analogue of the EIG residual, is held to RES_TOL;
-# the transposed residual ||A^T U - V S||_F / ||A||_F measures how well span(Q2) contains the
-# right singular vectors, which Theorem 1 bounds only through tol = 0.01 (the FP64 oracle
-# itself reaches 1.2e-13 on a 700 x 350 log-spaced problem), so it is held to 1e-12.
-RES_TOL_T = 1e-12
+# SVD: ||A V - U S||_F / ||A||_F, the direct analogue of the EIG residual, and the transposed
+# residual ||A^T U - V S||_F / ||A||_F, which measures how well span(Q2) contains the right
+# singular vectors (Theorem 1: O(u / sigma_min(R11)), kept small by the index tolerance 0.1).
+RES_TOL_T = 1e-13
 
 
 @pytest.fixture(scope="module")

@@ -1,4 +1,4 @@
-"""Pins of the full-spectrum oracle (QDWH-EIG, Section 2.2) against constructed spectra,
+"""Pins of the full-spectrum oracle (QDWH-EIG, Section 3.2) against constructed spectra,
 the brute-force Jacobi eigensolver and the projector identity after eq. pdeig."""
 
 import numpy as np

@@ -18,7 +18,7 @@ def _count_to_convergence(ell0):
 
 
 def test_iteration_counts_printed_in_paper():
-    # Section 2.1: at most six iterations for kappa <= 1e15.
+    # Section 3.1: at most six iterations for kappa <= 1e15.
     assert _count_to_convergence(1e-15) <= int(G["qdwh_max_iters_kappa_1e15"])
     for ell0 in np.logspace(-15, -0.01, 60):
         assert _count_to_convergence(ell0) <= int(G["qdwh_max_iters_kappa_1e15"])
