@@ -204,12 +204,27 @@ size_t gemm_splitk_ws_elems(int64_t m, int64_t n) {
   return mn * kMaxSplit;
 }
 
+thread_local void* t_emu_ws = nullptr;
+thread_local size_t t_emu_bytes = 0;
+
+EmulationScope::EmulationScope(void* ws, size_t bytes) : prev_ws(t_emu_ws), prev_bytes(t_emu_bytes) {
+  t_emu_ws = ws;
+  t_emu_bytes = bytes;
+}
+EmulationScope::~EmulationScope() {
+  t_emu_ws = prev_ws;
+  t_emu_bytes = prev_bytes;
+}
+
 qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                   int64_t ldc, Uplo uplo, double diag_add, double* splitk_ws, size_t splitk_ws_elems) {
   if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
   if (m == 0 || n == 0) return QDWHP_OK;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return QDWHP_ERR_ARG;
+  if (t_emu_ws != nullptr && m >= 128 && n >= 128 && k >= 256 && gemm_ozaki_ws_bytes(m, n, k) <= t_emu_bytes)
+    return gemm_ozaki(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, t_emu_ws,
+                      t_emu_bytes);
   const int M = (int)m, N = (int)n, K = (int)k;
   // 32 x 32 tiles throughout: the DMMA pipe is slow enough that a small tile (96 registers,
   // many resident CTAs per SM) beats larger tiles (1.07 vs 1.00-1.02 TFLOP/s at 4096^3).

@@ -190,6 +190,25 @@ QDWHP_API qdwhp_status qdwhp_gemm_f64(int transa, int transb, int64_t m, int64_t
   return gemm((cudaStream_t)stream, transa != 0, transb != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+QDWHP_API size_t qdwhp_gemm_f64_emulated_workspace_bytes(int64_t m, int64_t n, int64_t k) {
+  return gemm_ozaki_ws_bytes(m, n, k);
+}
+
+QDWHP_API qdwhp_status qdwhp_gemm_f64_emulated(int transa, int transb, int64_t m, int64_t n, int64_t k,
+                                               double alpha, const double* A, int64_t lda, const double* B,
+                                               int64_t ldb, double beta, double* C, int64_t ldc, void* workspace,
+                                               size_t ws_bytes, void* stream) {
+  if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
+  if (m == 0 || n == 0) return QDWHP_OK;
+  const int64_t rowsA = transa ? k : m, rowsB = transb ? n : k;
+  if (C == nullptr || ldc < m || lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB))
+    return QDWHP_ERR_ARG;
+  if (k > 0 && (A == nullptr || B == nullptr)) return QDWHP_ERR_ARG;
+  if (k > 0 && (workspace == nullptr || ((uintptr_t)workspace & 15) != 0)) return QDWHP_ERR_ARG;
+  return gemm_ozaki((cudaStream_t)stream, transa != 0, transb != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                    FULL, 0.0, workspace, ws_bytes);
+}
+
 QDWHP_API size_t qdwhp_potrf_workspace_bytes(int64_t n) {
   Arena ar;
   ar.dry = true;

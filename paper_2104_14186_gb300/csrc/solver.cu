@@ -158,6 +158,8 @@ struct EigWs {
   bool has_dc = false;   // n > kDcMin: Rayleigh-Ritz problems may need divide and conquer
   DcWs dc;               // its own buffers; the large ones are lent from the above at run time
   int dc_nodes = 0;      // splits of the last divide-and-conquer solve
+  char* emu = nullptr;   // QDWHP_FP64_EMULATED: scratch of the emulated products
+  size_t emu_bytes = 0;
 };
 
 void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
@@ -174,6 +176,10 @@ void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   w.S3 = ar.take<double>((size_t)n * n);
   w.has_dc = n > kDcMin;
   if (w.has_dc) carve_dc_own(ar, n, w.dc);
+  if (o.precision == QDWHP_FP64_EMULATED) {
+    w.emu_bytes = gemm_ozaki_ws_bytes(n, n, n);
+    w.emu = ar.take<char>(w.emu_bytes);
+  }
 }
 
 // Eigenvalues (into w.c.vals) and eigenvectors (S3, ld ell) of the symmetric ell x ell
@@ -221,6 +227,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   EigWs w;
   carve_eig(ar, n, o, w);
   if (!ar.ok()) return QDWHP_ERR_NOMEM;
+  EmulationScope emu_scope(w.emu, w.emu_bytes);
   Timer timer(st);
   HostScalars hs;
   qdwhp_info inf;
@@ -370,6 +377,8 @@ struct SvdWs {
   double* Vj = nullptr;   // n x n capacity
   double* W = nullptr;    // n x n capacity: gathered V~
   double* At = nullptr;   // transposed input when m < n
+  char* emu = nullptr;    // QDWHP_FP64_EMULATED: scratch of the emulated products
+  size_t emu_bytes = 0;
 };
 
 void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
@@ -385,6 +394,11 @@ void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, b
   w.Vj = ar.take<double>((size_t)n * n);
   w.W = ar.take<double>((size_t)n * n);
   if (need_transpose) w.At = ar.take<double>((size_t)m * n);
+  if (o.precision == QDWHP_FP64_EMULATED) {
+    const int64_t d = std::max(m, n);
+    w.emu_bytes = gemm_ozaki_ws_bytes(d, d, d);
+    w.emu = ar.take<char>(w.emu_bytes);
+  }
 }
 
 qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_t k, const qdwhp_opts& o,
@@ -530,7 +544,7 @@ bool opts_valid(const qdwhp_opts& o) {
          o.guard >= 0.0 && o.guard < 1.0 && o.max_retries >= 0 && o.jacobi_max_sweeps >= 1 &&
          o.refine_steps >= 0 && o.refine_steps <= 64 &&
          (o.side == QDWHP_LARGEST || o.side == QDWHP_SMALLEST) &&
-         (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED);
+         (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED || o.precision == QDWHP_FP64_EMULATED);
 }
 
 }  // namespace
@@ -634,6 +648,7 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
   SvdWs w;
   carve_svd(ar, mm, nn, *opts, w, m < n);
   if (!ar.ok()) return QDWHP_ERR_NOMEM;
+  EmulationScope emu_scope(w.emu, w.emu_bytes);
   if (m >= n) return svd_impl(A, m, n, lda, kk, *opts, sigma, U, ldu, V, ldv, w, info, st);
   // m < n: solve on A^T (n x m) and swap the roles of U and V (Section 4.2).
   dim3 grid(ceil_div(m, 32), ceil_div(n, 32));

@@ -29,7 +29,7 @@ STATUS_NAMES = {
     -5: "ERR_NONFINITE", -6: "ERR_TIMEOUT", -7: "ERR_CUDA", -8: "ERR_QUEUE_FULL", -9: "ERR_COUNT", 1: "PENDING",
 }
 LARGEST, SMALLEST = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, FP64_EMULATED = 0, 1, 2
 
 
 class Opts(C.Structure):
@@ -95,6 +95,9 @@ SIGNATURES = {
                             C.POINTER(Info), P]),
     "qdwhp_syev_workspace_bytes": (C.c_size_t, [I64]),
     "qdwhp_syev_f64": (C.c_int, [P, I64, I64, P, P, I64, P, C.c_size_t, C.POINTER(SyevInfo), P]),
+    "qdwhp_gemm_f64_emulated_workspace_bytes": (C.c_size_t, [I64, I64, I64]),
+    "qdwhp_gemm_f64_emulated": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P,
+                                          C.c_size_t, P]),
     "qdwhp_gemm_f64": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P]),
     "qdwhp_potrf_workspace_bytes": (C.c_size_t, [I64]),
     "qdwhp_potrf_f64": (C.c_int, [I64, P, I64, P, C.c_size_t, C.POINTER(C.c_int), P]),
@@ -413,6 +416,22 @@ def gemm_f64(A: torch.Tensor, B: torch.Tensor, transa=False, transb=False, alpha
     st = lib().qdwhp_gemm_f64(int(transa), int(transb), m, n, k, alpha, _ptr(Ac), A.shape[0], _ptr(Bc), B.shape[0],
                               beta, _ptr(Ct), m, _stream(stream))
     _check(st, "qdwhp_gemm_f64")
+    return Ct.t()
+
+
+def gemm_f64_emulated(A: torch.Tensor, B: torch.Tensor, transa=False, transb=False, alpha=1.0, beta=0.0,
+                      Cmat: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The same product through qdwhp_gemm_f64_emulated (Ozaki split on the BF16 tensor cores)."""
+    Ac, Bc = _colmajor(A), _colmajor(B)
+    m = A.shape[1] if transa else A.shape[0]
+    k = A.shape[0] if transa else A.shape[1]
+    n = B.shape[0] if transb else B.shape[1]
+    Ct = (torch.zeros(n, m, dtype=torch.float64, device=A.device) if Cmat is None else _colmajor(Cmat))
+    need = lib().qdwhp_gemm_f64_emulated_workspace_bytes(m, n, k)
+    ws = workspace(max(need, 1), A.device)
+    st = lib().qdwhp_gemm_f64_emulated(int(transa), int(transb), m, n, k, alpha, _ptr(Ac), A.shape[0], _ptr(Bc),
+                                       B.shape[0], beta, _ptr(Ct), m, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "qdwhp_gemm_f64_emulated")
     return Ct.t()
 
 

@@ -1,0 +1,107 @@
+"""FP64 products emulated on the BF16 tensor cores (Ozaki splitting), through the C ABI.
+
+The emulated GEMM is checked against its definition (the numpy FP64 product) with the
+scheme's error bound: the inputs are rounded to 54 bits relative to the largest entry of
+each row of op(A) and column of op(B), digit pairs below 2^-66 of those are dropped, and the
+53 exact partial products are summed in FP64.  The solvers in QDWHP_FP64_EMULATED mode must
+meet the plain-FP64 tolerances: |lambda - lambda*| <= 1e-12 ||A||_2,
+||V^T V - I||_F <= 5e-15 n, residuals <= 1e-13."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2104_14186_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def Q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_14186_gb300 import build
+    build.build()
+    from paper_2104_14186_gb300 import qdwhp
+    return qdwhp
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def emulation_bound(opA, opB, alpha, beta, C0):
+    k = opA.shape[1]
+    absA, absB = np.abs(opA), np.abs(opB)
+    scale = abs(alpha) * (absA @ absB) + abs(beta) * np.abs(C0)
+    rowmax = absA.max(axis=1, initial=0.0)[:, None]
+    colmax = absB.max(axis=0, initial=0.0)[None, :]
+    trunc = abs(alpha) * 2.0 ** -52 * (rowmax * absB.sum(axis=0)[None, :] + colmax * absA.sum(axis=1)[:, None])
+    dropped = abs(alpha) * 1e-16 * k * rowmax * colmax
+    # (4 k + 64) u |A||B|: the FP64 reference's own rounding plus the 53-term FP64 sum
+    return (4 * k + 64) * U64 * scale + trunc + dropped + 1e-300
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 128, 256), (300, 257, 1000), (37, 530, 300), (130, 200, 9000),
+                                   (512, 512, 512)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
+def test_emulated_gemm_within_bound(Q, m, n, k, ta, tb):
+    rng = np.random.default_rng(m * 11 + n * 5 + k + 2 * ta + tb)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    A[3] *= 1e-8            # rows and columns of very different magnitude
+    B[:, 5] *= 1e6
+    C0 = rng.standard_normal((m, n))
+    opA, opB = (A.T if ta else A), (B.T if tb else B)
+    ref = 1.5 * opA @ opB - 0.5 * C0
+    got = Q.gemm_f64_emulated(dev(A), dev(B), ta, tb, alpha=1.5, beta=-0.5, Cmat=dev(C0)).cpu().numpy()
+    err = np.abs(got - ref)
+    bound = emulation_bound(opA, opB, 1.5, -0.5, C0)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    # and it agrees with the native FP64 product to FP64 accuracy, normwise
+    nat = Q.gemm_f64(dev(A), dev(B), ta, tb, alpha=1.5, beta=-0.5, Cmat=dev(C0)).cpu().numpy()
+    assert np.linalg.norm(got - nat) <= 1e-14 * np.linalg.norm(np.abs(opA) @ np.abs(opB))
+
+
+def test_emulated_gemm_zero_and_nonfinite_rows(Q):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((200, 300))
+    B = rng.standard_normal((300, 150))
+    A[7] = 0.0
+    A[9, 4] = np.nan
+    got = Q.gemm_f64_emulated(dev(A), dev(B)).cpu().numpy()
+    assert np.all(got[7] == 0.0)
+    assert np.all(np.isnan(got[9]))
+    ok = np.ones(200, bool)
+    ok[[7, 9]] = False
+    assert np.all(np.isfinite(got[ok]))
+    ref = A[ok] @ B
+    assert np.all(np.abs(got[ok] - ref) <= emulation_bound(A[ok], B, 1.0, 0.0, np.zeros_like(ref)))
+
+
+def test_emulated_gemm_beta_zero_ignores_nan_in_c(Q):
+    A = np.eye(256)
+    C0 = np.full((256, 256), np.nan)
+    got = Q.gemm_f64_emulated(dev(A), dev(A), beta=0.0, Cmat=dev(C0)).cpu().numpy()
+    assert np.array_equal(got, np.eye(256))
+
+
+def test_emulated_eig_workload_n512(Q):
+    p = I.eig_uniform(512, 1000, 0.10)
+    r = Q.eig(dev(p.A), k=p.k, precision=Q.FP64_EMULATED)
+    m = O.eig_metrics(p.A, r.lam.cpu().numpy(), r.V.cpu().numpy(), np.sort(p.lam)[::-1][: p.k])
+    assert m["lam_err"] <= 1e-12 and m["orth"] <= 5e-15 * 512 and m["resid"] <= 1e-13, m
+
+
+@pytest.mark.parametrize("m,n,frac,seed", [(700, 500, 0.05, 2000), (4096, 4096, 0.05, 2000)])
+def test_emulated_svd(Q, m, n, frac, seed):
+    q = I.svd_logspaced(m, n, seed, frac)
+    r = Q.svd(dev(q.A), k=q.k, precision=Q.FP64_EMULATED)
+    mt = O.svd_metrics(q.A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), q.sigma[: q.k])
+    assert mt["sigma_err"] <= 1e-12, mt
+    assert mt["orthU"] <= 5e-15 * n and mt["orthV"] <= 5e-15 * n, mt
+    assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-13, mt
