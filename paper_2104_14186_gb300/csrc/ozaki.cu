@@ -36,7 +36,7 @@ constexpr int kOzS = 9;          // digits per entry
 constexpr int kOzBeta = 6;       // bits per digit
 constexpr int kOzT = 11;         // keep digit pairs with s + t <= kOzT (1-based)
 constexpr int kOzKc = 4096;      // FP32-exact chunk: kOzKc * 63^2 < 2^24
-constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 32;
+constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 32;
 constexpr int kOzLd = kOzBK + 8; // smem row stride (bf16): 80 bytes, conflict-free ldmatrix
 constexpr int kOzStages = 3;
 constexpr int kOzThreads = 256;
@@ -165,75 +165,83 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One CTA: a kOzBM x kOzBN tile of C.  8 warps as 4 (rows) x 2 (columns), warp tile 32 x 32 =
-// 2 x 4 mma tiles of 16 x 8.
-__global__ void __launch_bounds__(kOzThreads) oz_gemm_kernel(int M, int N, int k_pad, int rows_a_pad, int rows_b_pad,
-                                                             const unsigned short* __restrict__ Asl,
-                                                             const unsigned short* __restrict__ Bsl,
-                                                             const int* __restrict__ ea, const int* __restrict__ eb,
-                                                             double alpha, double beta, double* C, int64_t ldc,
-                                                             int uplo, double diag_add) {
-  __shared__ __align__(128) unsigned short sA[kOzStages][kOzBM * kOzLd];
-  __shared__ __align__(128) unsigned short sB[kOzStages][kOzBN * kOzLd];
+// One CTA: a kOzBM x kOzBN tile of C.  8 warps as 2 (rows) x 4 (columns), warp tile 64 x 32 =
+// 4 x 4 mma tiles of 16 x 8 (16 mma per 6 ldmatrix.x4 per 16-deep step).  The exact FP32
+// digit products live in registers; their FP64 sums live in shared memory, one column of 64
+// doubles per thread (index f * 256 + thread), read and written only by that thread.
+constexpr size_t kOzSmemStages = (size_t)kOzStages * (kOzBM + kOzBN) * kOzLd * sizeof(unsigned short);
+constexpr size_t kOzSmemBytes = kOzSmemStages + (size_t)64 * kOzThreads * sizeof(double);
+
+__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, int k_pad, int rows_a_pad,
+                                                                int rows_b_pad, const unsigned short* __restrict__ Asl,
+                                                                const unsigned short* __restrict__ Bsl,
+                                                                const int* __restrict__ ea,
+                                                                const int* __restrict__ eb, double alpha, double beta,
+                                                                double* C, int64_t ldc, int uplo, double diag_add) {
+  extern __shared__ __align__(128) unsigned char oz_smem[];
+  unsigned short* sA = reinterpret_cast<unsigned short*>(oz_smem);
+  unsigned short* sB = sA + (size_t)kOzStages * kOzBM * kOzLd;
+  double* acc64 = reinterpret_cast<double*>(oz_smem + kOzSmemStages);
   const int bm = blockIdx.y, bn = blockIdx.x;
   const int m0 = bm * kOzBM, n0 = bn * kOzBN;
   if (uplo == LOWER && m0 + kOzBM <= n0) return;   // tile strictly above the diagonal
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;
+  const int wm = warp & 1, wn = warp >> 1;
   const int nkb = k_pad / kOzBK;
   const int npairs = c_pairs.npairs;
   const int total = npairs * nkb;
   const size_t slice_a = (size_t)rows_a_pad * k_pad, slice_b = (size_t)rows_b_pad * k_pad;
 
-  auto load_stage = [&](int step, int buf) {
-    const int p = step / nkb, kb = step - p * nkb;
-    const unsigned short* As = Asl + (size_t)c_pairs.s[p] * slice_a + (size_t)m0 * k_pad + kb * kOzBK;
-    const unsigned short* Bs = Bsl + (size_t)c_pairs.t[p] * slice_b + (size_t)n0 * k_pad + kb * kOzBK;
-    // A: 128 rows x 4 chunks of 16 bytes; B: 64 rows x 4 chunks
+  // the (pair, K block) of the next stage to load, advanced incrementally
+  int lp = 0, lkb = 0;
+  auto load_next = [&](int buf) {
+    const unsigned short* As = Asl + (size_t)c_pairs.s[lp] * slice_a + (size_t)m0 * k_pad + lkb * kOzBK;
+    const unsigned short* Bs = Bsl + (size_t)c_pairs.t[lp] * slice_b + (size_t)n0 * k_pad + lkb * kOzBK;
+    unsigned short* da = sA + (size_t)buf * kOzBM * kOzLd;
+    unsigned short* db = sB + (size_t)buf * kOzBN * kOzLd;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int c = tid + kOzThreads * q;
       const int row = c >> 2, ch = c & 3;
-      cp_async16(&sA[buf][row * kOzLd + ch * 8], As + (size_t)row * k_pad + ch * 8);
+      cp_async16(da + row * kOzLd + ch * 8, As + (size_t)row * k_pad + ch * 8);
+      cp_async16(db + row * kOzLd + ch * 8, Bs + (size_t)row * k_pad + ch * 8);
     }
-    {
-      const int row = tid >> 2, ch = tid & 3;
-      cp_async16(&sB[buf][row * kOzLd + ch * 8], Bs + (size_t)row * k_pad + ch * 8);
+    if (++lkb == nkb) {
+      lkb = 0;
+      ++lp;
     }
   };
 
-  float acc[2][4][4];
-  double acc64[2][4][4];
+  float acc[4][4][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[i][j][q] = 0.f;
-        acc64[i][j][q] = 0.0;
-      }
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll 8
+  for (int f = 0; f < 64; ++f) acc64[f * kOzThreads + tid] = 0.0;
 
 #pragma unroll
   for (int st = 0; st < kOzStages - 1; ++st) {
-    if (st < total) load_stage(st, st);
+    if (st < total) load_next(st);
     cp_async_commit();
   }
+  int cp = 0, ckb = 0;   // (pair, K block) being computed
   for (int step = 0; step < total; ++step) {
     cp_async_wait<kOzStages - 2>();
     __syncthreads();
-    const int nxt = step + kOzStages - 1;
-    if (nxt < total) load_stage(nxt, nxt % kOzStages);
+    if (step + kOzStages - 1 < total) load_next((step + kOzStages - 1) % kOzStages);
     cp_async_commit();
     const int buf = step % kOzStages;
-    const unsigned short* a_s = sA[buf];
-    const unsigned short* b_s = sB[buf];
+    const unsigned short* a_s = sA + (size_t)buf * kOzBM * kOzLd;
+    const unsigned short* b_s = sB + (size_t)buf * kOzBN * kOzLd;
 #pragma unroll
     for (int kk = 0; kk < kOzBK; kk += 16) {
-      unsigned af[2][4];
+      unsigned af[4][4];
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int row = wm * 32 + mt * 16 + (lane & 15);
+      for (int mt = 0; mt < 4; ++mt) {
+        const int row = wm * 64 + mt * 16 + (lane & 15);
         const int col = kk + ((lane >> 4) << 3);
         ldmatrix_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], a_s + row * kOzLd + col);
       }
@@ -250,23 +258,27 @@ __global__ void __launch_bounds__(kOzThreads) oz_gemm_kernel(int M, int N, int k
         bfr[2 * np + 1][1] = r3;
       }
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
+      for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
     }
     // flush the exact FP32 digit product into FP64 at the end of a pair's K range or chunk
-    const int p = step / nkb, kb = step - p * nkb;
-    if (kb == nkb - 1 || ((kb + 1) % (kOzKc / kOzBK)) == 0) {
-      const double sc = c_pairs.scale[p];
+    if (ckb == nkb - 1 || ((ckb + 1) % (kOzKc / kOzBK)) == 0) {
+      const double sc = c_pairs.scale[cp];
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            acc64[i][j][q] = fma((double)acc[i][j][q], sc, acc64[i][j][q]);
+            double* slot = acc64 + ((i * 4 + j) * 4 + q) * kOzThreads + tid;
+            *slot = fma((double)acc[i][j][q], sc, *slot);
             acc[i][j][q] = 0.f;
           }
+    }
+    if (++ckb == nkb) {
+      ckb = 0;
+      ++cp;
     }
   }
   cp_async_wait<0>();
@@ -274,10 +286,10 @@ __global__ void __launch_bounds__(kOzThreads) oz_gemm_kernel(int M, int N, int k
   // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
   const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
+  for (int mt = 0; mt < 4; ++mt) {
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      const int i = m0 + wm * 32 + mt * 16 + g + 8 * half;
+      const int i = m0 + wm * 64 + mt * 16 + g + 8 * half;
       if (i >= M) continue;
       const int e_i = ea[i];
 #pragma unroll
@@ -294,12 +306,12 @@ __global__ void __launch_bounds__(kOzThreads) oz_gemm_kernel(int M, int N, int k
           } else if (e_i == kExpEmpty || f_j == kExpEmpty) {
             v = 0.0;
           } else {
-            v = alpha * ldexp(acc64[mt][nt][2 * half + cc], e_i + f_j);
+            v = alpha * ldexp(acc64[((mt * 4 + nt) * 4 + 2 * half + cc) * kOzThreads + tid], e_i + f_j);
           }
-          double* cp = C + i + (int64_t)j * ldc;
-          if (beta != 0.0) v = fma(beta, *cp, v);
+          double* cptr = C + i + (int64_t)j * ldc;
+          if (beta != 0.0) v = fma(beta, *cptr, v);
           if (i == j) v += diag_add;
-          *cp = v;
+          *cptr = v;
         }
       }
     }
@@ -372,8 +384,14 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
     const double shape[5] = {(double)m, (double)n, (double)k, (double)(uplo == LOWER), -1.0};
     prof_slot = gemm_prof_start(st, flops, shape);
   }
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemBytes);
+  });
+  QDWHP_CUDA_TRY(attr_err);
   dim3 grid(np / kOzBN, mp / kOzBM);
-  oz_gemm_kernel<<<grid, kOzThreads, 0, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc,
+  oz_gemm_kernel<<<grid, kOzThreads, kOzSmemBytes, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc,
                                                (int)uplo, diag_add);
   QDWHP_LAUNCH_CHECK();
   if (prof_slot >= 0) gemm_prof_stop(st, prof_slot);
