@@ -36,9 +36,8 @@ constexpr int kOzS = 9;          // digits per entry
 constexpr int kOzBeta = 6;       // bits per digit
 constexpr int kOzT = 11;         // keep digit pairs with s + t <= kOzT (1-based)
 constexpr int kOzKc = 4096;      // FP32-exact chunk: kOzKc * 63^2 < 2^24
-constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 32;
+constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 32;   // kOzBN: padding of op(B) (either tile divides it)
 constexpr int kOzLd = kOzBK + 8; // smem row stride (bf16): 80 bytes, conflict-free ldmatrix
-constexpr int kOzStages = 3;
 constexpr int kOzThreads = 256;
 constexpr int kExpEmpty = -2000000000;   // no entry seen yet (row of zeros)
 constexpr int kExpNonfinite = 1 << 20;   // a NaN or Inf in the row
@@ -165,28 +164,39 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One CTA: a kOzBM x kOzBN tile of C.  8 warps as 2 (rows) x 4 (columns), warp tile 64 x 32 =
-// 4 x 4 mma tiles of 16 x 8 (16 mma per 6 ldmatrix.x4 per 16-deep step).  The exact FP32
-// digit products live in registers; their FP64 sums live in shared memory, one column of 64
-// doubles per thread (index f * 256 + thread), read and written only by that thread.
-constexpr size_t kOzSmemStages = (size_t)kOzStages * (kOzBM + kOzBN) * kOzLd * sizeof(unsigned short);
-constexpr size_t kOzSmemBytes = kOzSmemStages + (size_t)64 * kOzThreads * sizeof(double);
+// One CTA: a 128 x BN tile of C, 8 warps of (16 MT) x 32 (MT x 4 mma tiles of 16 x 8):
+//   MT = 4: 2 x 4 warps, BN = 128 (16 mma per 6 ldmatrix.x4 per 16-deep step), 3 stages;
+//   MT = 2: 4 x 2 warps, BN = 64 (more CTAs for narrow products; two CTAs fit an SM), 3 stages.
+// The exact FP32 digit products live in registers; their FP64 sums live in shared memory,
+// 16 MT doubles per thread at index f * 256 + thread, touched only by that thread.
+template <int MT>
+struct OzCfg {
+  static constexpr int kWarpsM = kOzBM / (16 * MT);
+  static constexpr int kWarpsN = 8 / kWarpsM;
+  static constexpr int kBN = kWarpsN * 32;
+  static constexpr int kStages = 3;
+  static constexpr size_t kSmemStages = (size_t)kStages * (kOzBM + kBN) * kOzLd * sizeof(unsigned short);
+  static constexpr size_t kSmemBytes = kSmemStages + (size_t)16 * MT * kOzThreads * sizeof(double);
+};
 
+template <int MT>
 __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, int k_pad, int rows_a_pad,
                                                                 int rows_b_pad, const unsigned short* __restrict__ Asl,
                                                                 const unsigned short* __restrict__ Bsl,
                                                                 const int* __restrict__ ea,
                                                                 const int* __restrict__ eb, double alpha, double beta,
                                                                 double* C, int64_t ldc, int uplo, double diag_add) {
+  using Cfg = OzCfg<MT>;
+  constexpr int BN = Cfg::kBN, STAGES = Cfg::kStages;
   extern __shared__ __align__(128) unsigned char oz_smem[];
   unsigned short* sA = reinterpret_cast<unsigned short*>(oz_smem);
-  unsigned short* sB = sA + (size_t)kOzStages * kOzBM * kOzLd;
-  double* acc64 = reinterpret_cast<double*>(oz_smem + kOzSmemStages);
+  unsigned short* sB = sA + (size_t)STAGES * kOzBM * kOzLd;
+  double* acc64 = reinterpret_cast<double*>(oz_smem + Cfg::kSmemStages);
   const int bm = blockIdx.y, bn = blockIdx.x;
-  const int m0 = bm * kOzBM, n0 = bn * kOzBN;
+  const int m0 = bm * kOzBM, n0 = bn * BN;
   if (uplo == LOWER && m0 + kOzBM <= n0) return;   // tile strictly above the diagonal
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 1, wn = warp >> 1;
+  const int wm = warp % Cfg::kWarpsM, wn = warp / Cfg::kWarpsM;
   const int nkb = k_pad / kOzBK;
   const int npairs = c_pairs.npairs;
   const int total = npairs * nkb;
@@ -198,12 +208,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
     const unsigned short* As = Asl + (size_t)c_pairs.s[lp] * slice_a + (size_t)m0 * k_pad + lkb * kOzBK;
     const unsigned short* Bs = Bsl + (size_t)c_pairs.t[lp] * slice_b + (size_t)n0 * k_pad + lkb * kOzBK;
     unsigned short* da = sA + (size_t)buf * kOzBM * kOzLd;
-    unsigned short* db = sB + (size_t)buf * kOzBN * kOzLd;
+    unsigned short* db = sB + (size_t)buf * BN * kOzLd;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < 2; ++q) {   // A: 128 rows x 4 chunks of 16 bytes
       const int c = tid + kOzThreads * q;
       const int row = c >> 2, ch = c & 3;
       cp_async16(da + row * kOzLd + ch * 8, As + (size_t)row * k_pad + ch * 8);
+    }
+#pragma unroll
+    for (int q = 0; q < BN / 64; ++q) {   // B: BN rows x 4 chunks
+      const int c = tid + kOzThreads * q;
+      const int row = c >> 2, ch = c & 3;
       cp_async16(db + row * kOzLd + ch * 8, Bs + (size_t)row * k_pad + ch * 8);
     }
     if (++lkb == nkb) {
@@ -212,36 +227,36 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
     }
   };
 
-  float acc[4][4][4];
+  float acc[MT][4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 #pragma unroll 8
-  for (int f = 0; f < 64; ++f) acc64[f * kOzThreads + tid] = 0.0;
+  for (int f = 0; f < 16 * MT; ++f) acc64[f * kOzThreads + tid] = 0.0;
 
 #pragma unroll
-  for (int st = 0; st < kOzStages - 1; ++st) {
+  for (int st = 0; st < STAGES - 1; ++st) {
     if (st < total) load_next(st);
     cp_async_commit();
   }
   int cp = 0, ckb = 0;   // (pair, K block) being computed
   for (int step = 0; step < total; ++step) {
-    cp_async_wait<kOzStages - 2>();
+    cp_async_wait<STAGES - 2>();
     __syncthreads();
-    if (step + kOzStages - 1 < total) load_next((step + kOzStages - 1) % kOzStages);
+    if (step + STAGES - 1 < total) load_next((step + STAGES - 1) % STAGES);
     cp_async_commit();
-    const int buf = step % kOzStages;
+    const int buf = step % STAGES;
     const unsigned short* a_s = sA + (size_t)buf * kOzBM * kOzLd;
-    const unsigned short* b_s = sB + (size_t)buf * kOzBN * kOzLd;
+    const unsigned short* b_s = sB + (size_t)buf * BN * kOzLd;
 #pragma unroll
     for (int kk = 0; kk < kOzBK; kk += 16) {
-      unsigned af[4][4];
+      unsigned af[MT][4];
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt) {
-        const int row = wm * 64 + mt * 16 + (lane & 15);
+      for (int mt = 0; mt < MT; ++mt) {
+        const int row = wm * 16 * MT + mt * 16 + (lane & 15);
         const int col = kk + ((lane >> 4) << 3);
         ldmatrix_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], a_s + row * kOzLd + col);
       }
@@ -258,7 +273,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
         bfr[2 * np + 1][1] = r3;
       }
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt)
+      for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
     }
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
     if (ckb == nkb - 1 || ((ckb + 1) % (kOzKc / kOzBK)) == 0) {
       const double sc = c_pairs.scale[cp];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < MT; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -286,10 +301,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
   // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
   const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
-  for (int mt = 0; mt < 4; ++mt) {
+  for (int mt = 0; mt < MT; ++mt) {
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      const int i = m0 + wm * 64 + mt * 16 + g + 8 * half;
+      const int i = m0 + wm * 16 * MT + mt * 16 + g + 8 * half;
       if (i >= M) continue;
       const int e_i = ea[i];
 #pragma unroll
@@ -316,6 +331,25 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
       }
     }
   }
+}
+
+template <int MT>
+qdwhp_status launch_oz(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
+                       const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta, double* C,
+                       int64_t ldc, Uplo uplo, double diag_add) {
+  using Cfg = OzCfg<MT>;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Cfg::kSmemBytes);
+  });
+  QDWHP_CUDA_TRY(attr_err);
+  dim3 grid(np / Cfg::kBN, mp / kOzBM);
+  oz_gemm_kernel<MT><<<grid, kOzThreads, Cfg::kSmemBytes, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha,
+                                                                beta, C, ldc, (int)uplo, diag_add);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
 }
 
 int ceil_to(int64_t a, int b) { return (int)(((a + b - 1) / b) * b); }
@@ -384,16 +418,15 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
     const double shape[5] = {(double)m, (double)n, (double)k, (double)(uplo == LOWER), -1.0};
     prof_slot = gemm_prof_start(st, flops, shape);
   }
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemBytes);
-  });
-  QDWHP_CUDA_TRY(attr_err);
-  dim3 grid(np / kOzBN, mp / kOzBM);
-  oz_gemm_kernel<<<grid, kOzThreads, kOzSmemBytes, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc,
-                                               (int)uplo, diag_add);
-  QDWHP_LAUNCH_CHECK();
+  // 128 x 128 tiles when they fill the GPU twice over, else 128 x 64 (twice the CTAs)
+  int dev = 0, sms = kNumSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t big_tiles = (int64_t)(mp / kOzBM) * (np / 128) / (uplo == LOWER ? 2 : 1);
+  if (big_tiles >= 2 * sms) {
+    QDWHP_TRY(launch_oz<4>(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add));
+  } else {
+    QDWHP_TRY(launch_oz<2>(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add));
+  }
   if (prof_slot >= 0) gemm_prof_stop(st, prof_slot);
   return QDWHP_OK;
 }
