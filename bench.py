@@ -399,17 +399,18 @@ def run_eig_large(args):
     frac = args.fraction
     A, lam, k = I.eig_clustered_device(16384, 3000, frac)
     n = A.shape[0]
-    o = Q.default_opts()
+    prec = precision_code(Q, args.precision)
+    o = Q.default_opts(precision=prec)
     ws = Q.workspace(Q.lib().qdwhp_eig_workspace_bytes(n, __import__("ctypes").byref(o)))
     for _ in range(args.warmup):
-        r = Q.eig(A, k=k, ws=ws)
+        r = Q.eig(A, k=k, ws=ws, precision=prec)
     torch.cuda.synchronize()
     ms = []
     Q.profile_begin()
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = Q.eig(A, k=k, ws=ws)
+        r = Q.eig(A, k=k, ws=ws, precision=prec)
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -422,7 +423,8 @@ def run_eig_large(args):
     fl = 3 * (n ** 3 + n ** 3 / 3 + 2 * n ** 3) + 4 / 3 * n ** 3 + 4 * n * n * ell + 2 * n * ell ** 2 + 9 * ell ** 3 \
         + 2 * n * ell * k
     t = statistics.median(ms) / 1e3
-    print(json.dumps({"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})", "ell": ell,
+    print(json.dumps({"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})",
+                      "precision": args.precision, "ell": ell,
                       "ms_median": 1e3 * t, "solves_per_s": 1 / t, "alg_tflops": fl / t / 1e12,
                       "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9,
                       "gemm_share": prof["gemm_ms"] / sum(ms), "lam_err": err, "resid": res,

@@ -221,6 +221,7 @@ void carve_dc(Arena& ar, int64_t cap, DcWs& w) {
   w.W = ar.take<double>(c2);
   w.f.Vall = ar.take<double>(c2);
   w.f.T = ar.take<double>((size_t)ceil_div(cap, kQRNB) * kQRNB * kQRNB);
+  w.f.To = ar.take<double>(qr_to_elems(cap));
   w.f.tau = ar.take<double>(cap);
   w.f.diagR = ar.take<double>(cap);
   w.qr_scratch = ar.take<double>(qr_scratch_elems(cap, cap));

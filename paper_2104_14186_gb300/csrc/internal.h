@@ -96,14 +96,17 @@ qdwhp_status trsm_right_lower(cudaStream_t st, bool trans, int64_t m, int64_t n,
 
 // ---- qr.cu ----
 constexpr int kQRNB = 32;
+constexpr int kQROuter = 256;
 struct QRFactors {
   double* Vall = nullptr;   // m x n explicit reflectors (unit diagonal, zeros above), ld = m
   double* T = nullptr;      // nblocks x kQRNB x kQRNB upper-triangular block factors
+  double* To = nullptr;     // qr_to_elems(n): the same for the kQROuter-wide outer blocks
   double* tau = nullptr;    // n
   double* diagR = nullptr;  // n: R_ii
   int64_t m = 0, n = 0;
 };
 size_t qr_scratch_elems(int64_t m, int64_t n);
+size_t qr_to_elems(int64_t n);
 // Householder QR of A (m x n, m >= n) in place: R in the upper triangle of A.
 qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f,
                    double* scratch);

@@ -81,6 +81,7 @@ void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w, bool n
     w.S = ar.take<double>((size_t)mm * n);
     w.qf.Vall = ar.take<double>((size_t)mm * n);
     w.qf.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+    w.qf.To = ar.take<double>(qr_to_elems(n));
     w.qf.tau = ar.take<double>(n);
     w.qf.diagR = ar.take<double>(n);
     w.qr_scratch = ar.take<double>(qr_scratch_elems(mm, n));
@@ -243,6 +244,7 @@ QDWHP_API size_t qdwhp_qr_workspace_bytes(int64_t m, int64_t n) {
   ar.dry = true;
   ar.take<double>((size_t)m * n);
   ar.take<double>((size_t)ceil_div(std::max<int64_t>(n, 1), kQRNB) * kQRNB * kQRNB);
+  ar.take<double>(qr_to_elems(n));
   ar.take<double>(n);
   ar.take<double>(n);
   ar.take<double>(qr_scratch_elems(m, n));
@@ -260,6 +262,7 @@ QDWHP_API qdwhp_status qdwhp_qr_f64(int64_t m, int64_t n, double* A, int64_t lda
   QRFactors f;
   f.Vall = ar.take<double>((size_t)m * n);
   f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+  f.To = ar.take<double>(qr_to_elems(n));
   f.tau = ar.take<double>(n);
   f.diagR = ar.take<double>(n);
   double* scratch = ar.take<double>(qr_scratch_elems(m, n));

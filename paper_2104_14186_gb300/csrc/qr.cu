@@ -5,6 +5,10 @@
 // count-to-threshold subspace.  Reflectors follow the LAPACK convention
 // H = I - tau v v^T with v_1 = 1, and each kQRNB-wide panel is
 // accumulated into the compact WY form Q_p = I - V T V^T (T upper triangular).
+// Two levels: a panel updates only the rest of its 256-column outer block; the outer
+// block's T (merged from its eight panel T's through the Gram matrix G = V^T V:
+// T_{1:q+1} = [T_{1:q}, -T_{1:q} G(1:q, q+1) T_{q+1}; 0, T_{q+1}]) then updates the
+// trailing matrix and forms Q with products of inner dimension 256.
 //
 // One SM does only a few FP64 flops per clock on this part, so a panel factored by
 // a single CTA would be ~100x slower than the chip.  The panel kernel is therefore
@@ -27,6 +31,8 @@ namespace qdwhp {
 namespace {
 
 constexpr int NB = kQRNB;          // panel width (32)
+constexpr int NBO = kQROuter;      // outer block width (256 = 8 panels)
+constexpr size_t kQRSplitCap = size_t(4) << 20;   // split-K scratch of the trailing products (doubles)
 constexpr int kPanelThreads = 256;
 constexpr int kPanelCTAs = 96;
 constexpr int kMinRowsPerCTA = 64;
@@ -251,12 +257,41 @@ qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
 
 }  // namespace
 
+// Split-K scratch of the trailing products: non-decreasing in n, so a scratch sized for n
+// serves every narrower product.
+size_t qr_splitk_elems(int64_t n) { return std::min((size_t)16 * NBO * std::max<int64_t>(n, 1), kQRSplitCap); }
+
+size_t qr_to_elems(int64_t n) { return (size_t)ceil_div(std::max<int64_t>(n, 1), NBO) * NBO * NBO; }
+
 size_t qr_scratch_elems(int64_t m, int64_t n) {
-  const size_t wn = (size_t)NB * std::max<int64_t>(n, 1);
-  size_t splitk = gemm_splitk_ws_elems(NB, std::max<int64_t>(n, 1));
-  return 2 * wn + splitk + 2 * (size_t)kPanelCTAs * kPartStride + (size_t)(kPanelCTAs + 1) * NB * NB + 2 * NB + 64;
+  const size_t wn = (size_t)NBO * std::max<int64_t>(n, 1);
+  return 2 * wn + qr_splitk_elems(n) + 2 * (size_t)kPanelCTAs * kPartStride + (size_t)(kPanelCTAs + 1) * NB * NB +
+         2 * NB + (size_t)NBO * NBO + (size_t)NBO * NB + 64;
   (void)m;
 }
+
+namespace {
+
+// T of the outer block starting at column jo (jbo columns) from its panels' T's.
+qdwhp_status build_outer_T(cudaStream_t st, const QRFactors& f, int64_t jo, int jbo, double* G, double* tmp) {
+  const int64_t m = f.m, Ro = m - jo;
+  const double* Vo = f.Vall + jo + jo * m;
+  double* To = f.To + (size_t)(jo / NBO) * NBO * NBO;
+  QDWHP_TRY(set_matrix(st, NBO, NBO, 0.0, 0.0, To, NBO));
+  if (jbo > NB) QDWHP_TRY(gemm(st, true, false, jbo, jbo, Ro, 1.0, Vo, m, Vo, m, 0.0, G, NBO));
+  for (int c0 = 0; c0 < jbo; c0 += NB) {
+    const int jb = std::min(NB, jbo - c0);
+    const double* Tq = f.T + (size_t)((jo + c0) / NB) * NB * NB;
+    QDWHP_TRY(copy_matrix(st, jb, jb, Tq, NB, To + c0 + (size_t)c0 * NBO, NBO));
+    if (c0 > 0) {
+      QDWHP_TRY(gemm(st, false, false, c0, jb, c0, 1.0, To, NBO, G + (size_t)c0 * NBO, NBO, 0.0, tmp, NBO));
+      QDWHP_TRY(gemm(st, false, false, c0, jb, jb, -1.0, tmp, NBO, Tq, NB, 0.0, To + (size_t)c0 * NBO, NBO));
+    }
+  }
+  return QDWHP_OK;
+}
+
+}  // namespace
 
 qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f, double* scratch) {
   if (m < n || n < 0) return QDWHP_ERR_ARG;
@@ -264,36 +299,56 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
   f.n = n;
   if (n == 0) return QDWHP_OK;
   double* W = scratch;
-  double* W2 = W + (size_t)NB * n;
-  const size_t splitk_elems = gemm_splitk_ws_elems(NB, n);
-  double* splitk = W2 + (size_t)NB * n;
+  double* W2 = W + (size_t)NBO * n;
+  const size_t splitk_elems = qr_splitk_elems(n);
+  double* splitk = W2 + (size_t)NBO * n;
   double* part = splitk + splitk_elems;
   double* gram = part + 2 * (size_t)kPanelCTAs * kPartStride;
   double* row_slot = gram + (size_t)(kPanelCTAs + 1) * NB * NB;
-  for (int64_t j = 0; j < n; j += NB) {
-    const int jb = (int)std::min<int64_t>(NB, n - j);
-    const int64_t R = m - j;
-    PanelArgs pa;
-    pa.R = (int)R;
-    pa.jb = jb;
-    pa.P = A + j + j * lda;
-    pa.lda = lda;
-    pa.V = f.Vall + j + j * m;
-    pa.ldv = m;
-    pa.T = f.T + (size_t)(j / NB) * NB * NB;
-    pa.tau = f.tau + j;
-    pa.diagR = f.diagR + j;
-    pa.part = part;
-    pa.gram = gram;
-    pa.row_slot = row_slot;
-    QDWHP_TRY(launch_panel(st, pa));
-    const int64_t nc = n - j - jb;
+  double* G = row_slot + 2 * NB;
+  double* tmp = G + (size_t)NBO * NBO;
+  for (int64_t jo = 0; jo < n; jo += NBO) {
+    const int jbo = (int)std::min<int64_t>(NBO, n - jo);
+    for (int64_t j = jo; j < jo + jbo; j += NB) {
+      const int jb = (int)std::min<int64_t>(NB, n - j);
+      const int64_t R = m - j;
+      PanelArgs pa;
+      pa.R = (int)R;
+      pa.jb = jb;
+      pa.P = A + j + j * lda;
+      pa.lda = lda;
+      pa.V = f.Vall + j + j * m;
+      pa.ldv = m;
+      pa.T = f.T + (size_t)(j / NB) * NB * NB;
+      pa.tau = f.tau + j;
+      pa.diagR = f.diagR + j;
+      pa.part = part;
+      pa.gram = gram;
+      pa.row_slot = row_slot;
+      QDWHP_TRY(launch_panel(st, pa));
+      // the outer block's V is zero above each panel's diagonal
+      if (j > jo) QDWHP_TRY(set_matrix(st, j - jo, jb, 0.0, 0.0, f.Vall + jo + j * m, m));
+      const int64_t nc = jo + jbo - j - jb;   // the rest of the outer block
+      if (nc > 0) {
+        double* C = A + j + (j + jb) * lda;
+        // W = V^T C ; W2 = T^T W ; C -= V W2
+        QDWHP_TRY(gemm(st, true, false, jb, nc, R, 1.0, pa.V, m, C, lda, 0.0, W, jb, FULL, 0.0, splitk,
+                       splitk_elems));
+        QDWHP_TRY(gemm(st, true, false, jb, nc, jb, 1.0, pa.T, NB, W, jb, 0.0, W2, jb));
+        QDWHP_TRY(gemm(st, false, false, R, nc, jb, -1.0, pa.V, m, W2, jb, 1.0, C, lda));
+      }
+    }
+    QDWHP_TRY(build_outer_T(st, f, jo, jbo, G, tmp));
+    const int64_t nc = n - jo - jbo;   // trailing columns: one update with the outer block
     if (nc > 0) {
-      double* C = A + j + (j + jb) * lda;
-      // W = V^T C ; W2 = T^T W ; C -= V W2
-      QDWHP_TRY(gemm(st, true, false, jb, nc, R, 1.0, pa.V, m, C, lda, 0.0, W, jb, FULL, 0.0, splitk, splitk_elems));
-      QDWHP_TRY(gemm(st, true, false, jb, nc, jb, 1.0, pa.T, NB, W, jb, 0.0, W2, jb));
-      QDWHP_TRY(gemm(st, false, false, R, nc, jb, -1.0, pa.V, m, W2, jb, 1.0, C, lda));
+      const int64_t Ro = m - jo;
+      const double* Vo = f.Vall + jo + jo * m;
+      const double* To = f.To + (size_t)(jo / NBO) * NBO * NBO;
+      double* C = A + jo + (jo + jbo) * lda;
+      QDWHP_TRY(gemm(st, true, false, jbo, nc, Ro, 1.0, Vo, m, C, lda, 0.0, W, jbo, FULL, 0.0, splitk,
+                     splitk_elems));
+      QDWHP_TRY(gemm(st, true, false, jbo, nc, jbo, 1.0, To, NBO, W, jbo, 0.0, W2, jbo));
+      QDWHP_TRY(gemm(st, false, false, Ro, nc, jbo, -1.0, Vo, m, W2, jbo, 1.0, C, lda));
     }
   }
   return QDWHP_OK;
@@ -301,25 +356,27 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
 
 namespace {
 
-// C(j:, :) -= V_p (T_p (V_p^T C(j:, :))) for blocks p = last_block .. 0, i.e. C := Q C restricted to
-// the first last_block + 1 block reflectors.
+// C(jo:, :) -= V_o (T_o (V_o^T C(jo:, :))) for the outer blocks from the one holding panel
+// block last_block down to 0, i.e. C := Q C restricted to those reflectors (the extra panels of
+// the last outer block act on rows that are zero in the orgqr use and belong to Q otherwise).
 qdwhp_status apply_blocks(cudaStream_t st, const QRFactors& f, int64_t last_block, double* C, int64_t ncols,
                           int64_t ldc, double* scratch) {
   const int64_t m = f.m, n = f.n;
   double* W = scratch;
-  double* W2 = W + (size_t)NB * ncols;
-  const size_t splitk_elems = gemm_splitk_ws_elems(NB, ncols);
-  double* splitk = W2 + (size_t)NB * ncols;
-  for (int64_t p = last_block; p >= 0; --p) {
-    const int64_t j = p * NB;
-    const int jb = (int)std::min<int64_t>(NB, n - j);
-    const int64_t R = m - j;
-    const double* V = f.Vall + j + j * m;
-    const double* T = f.T + (size_t)p * NB * NB;
-    double* Cj = C + j;
-    QDWHP_TRY(gemm(st, true, false, jb, ncols, R, 1.0, V, m, Cj, ldc, 0.0, W, jb, FULL, 0.0, splitk, splitk_elems));
-    QDWHP_TRY(gemm(st, false, false, jb, ncols, jb, 1.0, T, NB, W, jb, 0.0, W2, jb));
-    QDWHP_TRY(gemm(st, false, false, R, ncols, jb, -1.0, V, m, W2, jb, 1.0, Cj, ldc));
+  double* W2 = W + (size_t)NBO * ncols;
+  const size_t splitk_elems = qr_splitk_elems(ncols);
+  double* splitk = W2 + (size_t)NBO * ncols;
+  for (int64_t po = (last_block * NB) / NBO; po >= 0; --po) {
+    const int64_t jo = po * NBO;
+    const int jbo = (int)std::min<int64_t>(NBO, n - jo);
+    const int64_t Ro = m - jo;
+    const double* Vo = f.Vall + jo + jo * m;
+    const double* To = f.To + (size_t)po * NBO * NBO;
+    double* Cj = C + jo;
+    QDWHP_TRY(gemm(st, true, false, jbo, ncols, Ro, 1.0, Vo, m, Cj, ldc, 0.0, W, jbo, FULL, 0.0, splitk,
+                   splitk_elems));
+    QDWHP_TRY(gemm(st, false, false, jbo, ncols, jbo, 1.0, To, NBO, W, jbo, 0.0, W2, jbo));
+    QDWHP_TRY(gemm(st, false, false, Ro, ncols, jbo, -1.0, Vo, m, W2, jbo, 1.0, Cj, ldc));
   }
   return QDWHP_OK;
 }

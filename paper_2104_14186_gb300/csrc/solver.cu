@@ -168,6 +168,7 @@ void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   w.X = ar.take<double>((size_t)n * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+  w.f.To = ar.take<double>(qr_to_elems(n));
   w.f.tau = ar.take<double>(n);
   w.f.diagR = ar.take<double>(n);
   w.qr_scratch = ar.take<double>(qr_scratch_elems(n, n));
@@ -387,6 +388,7 @@ void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, b
   w.X = ar.take<double>((size_t)m * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
+  w.f.To = ar.take<double>(qr_to_elems(n));
   w.f.tau = ar.take<double>(n);
   w.f.diagR = ar.take<double>(n);
   w.qr_scratch = ar.take<double>(qr_scratch_elems(n, n));
