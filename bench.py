@@ -286,7 +286,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
-    if args.precision == "emulated":
+    if args.precision in ("emulated", "mixed-emulated"):
         line["all_products_fp64_equivalent"] = line["roofline"]
         line["roofline"] = emulated_roofline(Q, total_ms, bf16 if bf16 else 1.9e3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -303,16 +303,17 @@ def run_ours(args):
 
 
 def precision_code(Q, name):
-    return {"fp64": Q.FP64, "mixed": Q.MIXED, "emulated": Q.FP64_EMULATED}[name]
+    return {"fp64": Q.FP64, "mixed": Q.MIXED, "emulated": Q.FP64_EMULATED, "mixed-emulated": Q.MIXED_EMULATED}[name]
 
 
-DTYPES = {"fp64": "f64", "mixed": "f32+f64", "emulated": "f64 (bf16 Ozaki digit products + f64 sums)"}
-OZ_PAIRS = 53          # digit products per emulated FP64 product
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "emulated": "f64 (bf16 Ozaki digit products + f64 sums)",
+          "mixed-emulated": "f32 + f64 (bf16 Ozaki digit products + f64 sums)"}
+OZ_PAIRS = 60          # digit products per emulated FP64 product
 
 
 def emulated_roofline(Q, total_ms, bf16_peak):
     """Roofline of the emulated-product kernel from the per-GEMM records (split slot -1):
-    its own arithmetic is BF16 tensor work, 53 digit products of the padded shape."""
+    its own arithmetic is BF16 tensor work, 60 digit products of the padded shape."""
     recs = [r for r in Q.profile_records() if r[4] < 0]
     if not recs:
         return None
@@ -321,7 +322,7 @@ def emulated_roofline(Q, total_ms, bf16_peak):
     bf16_flops = sum(OZ_PAIRS * 2.0 * pad(r[0], 128) * pad(r[1], 64) * pad(r[2], 32) for r in recs)
     fp64_flops = sum((r[1] * (r[1] + 1) * r[2]) if r[3] else 2.0 * r[0] * r[1] * r[2] for r in recs)
     achieved = bf16_flops / (ms / 1e3) / 1e12
-    return {"kernel": "oz_gemm_kernel (FP64 products as 53 exact BF16 digit products, mma.sync m16n8k16)",
+    return {"kernel": "oz_gemm_kernel (FP64 products as 60 exact BF16 digit products, mma.sync m16n8k16)",
             "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
             "frac": achieved / bf16_peak, "traffic": None,
             "peak_source": "measured bf16 dense burst (cuBLAS), of measured",
@@ -554,7 +555,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "mixed", "emulated"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "emulated", "mixed-emulated"], default="fp64")
     ap.add_argument("--refine", type=int, default=0, help="FP64 refinement steps on Q2 (SVD)")
     ap.add_argument("--kernel", choices=["gemm"], default=None,
                     help="time one building block in isolation instead of the full solve")

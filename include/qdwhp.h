@@ -52,7 +52,7 @@ typedef enum {
 } qdwhp_status;
 
 typedef enum { QDWHP_LARGEST = 0, QDWHP_SMALLEST = 1 } qdwhp_side;
-typedef enum { QDWHP_FP64 = 0, QDWHP_MIXED = 1, QDWHP_FP64_EMULATED = 2 } qdwhp_precision;
+typedef enum { QDWHP_FP64 = 0, QDWHP_MIXED = 1, QDWHP_FP64_EMULATED = 2, QDWHP_MIXED_EMULATED = 3 } qdwhp_precision;
 
 /* Options.  Fill with qdwhp_default_opts() and change what you need. */
 typedef struct {
@@ -61,8 +61,8 @@ typedef struct {
   int32_t side;           /* qdwhp_side (EIG only; SVD always returns the largest) */
   int32_t precision;      /* qdwhp_precision: QDWHP_FP64; QDWHP_MIXED (every Cholesky-based QDWH step
                              but the last in FP32; all else FP64); QDWHP_FP64_EMULATED (every product
-                             with m, n >= 128 and k >= 256 by qdwhp_gemm_f64_emulated's scheme, the
-                             rest native FP64) */
+                             with m, n >= 128 and k >= 64 by qdwhp_gemm_f64_emulated's scheme, the
+                             rest native FP64); QDWHP_MIXED_EMULATED (both) */
   double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
   int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */
   int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
@@ -228,10 +228,10 @@ QDWHP_API qdwhp_status qdwhp_gemm_f64(int transa, int transb, int64_t m, int64_t
 /*
  * The same product, FP64-accurate, computed on the BF16 tensor cores by the Ozaki splitting
  * scheme (Ozaki, Ogita, Oishi, Rump 2012): each row of op(A) and column of op(B) is scaled
- * by a power of two and cut into nine 6-bit digits; the 53 digit products with
- * s + t <= 11 are exact in FP32 (inner dimension chunks of 4096) and summed in FP64.  The
- * error is normwise, relative to the largest entry of each row of op(A) and column of op(B):
- * about 2^-54 of those, plus FP64 rounding of the 53-term sum.  Not part of the paper.
+ * by a power of two and cut into nine 6-bit digits; the 60 digit products with
+ * s + t <= 12 are exact in FP32 and summed in FP64.  The error is normwise, relative to the
+ * largest entry of each row of op(A) and column of op(B): about 2^-54 of those, plus FP64
+ * rounding of the sum.  Not part of the paper.
  *   workspace/ws_bytes: at least qdwhp_gemm_f64_emulated_workspace_bytes(m, n, k), 16-byte
  *   aligned.  A NaN or Inf in a row of op(A) or a column of op(B) makes that row or column
  *   of the result NaN.

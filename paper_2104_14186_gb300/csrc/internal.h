@@ -20,14 +20,14 @@ size_t gemm_splitk_ws_elems(int64_t m, int64_t n);
 
 // ---- ozaki.cu ----
 // FP64 GEMM emulated on the BF16 tensor cores (Ozaki splitting: 9 six-bit digits per entry,
-// exact digit products in FP32, FP64 accumulation).  Same operation as gemm(); needs
+// the 60 digit pairs with s + t <= 12, exact in FP32, FP64 accumulation).  Same operation as gemm(); needs
 // gemm_ozaki_ws_bytes(m, n, k) bytes of scratch (16-byte aligned).
 size_t gemm_ozaki_ws_bytes(int64_t m, int64_t n, int64_t k);
 qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                         const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                         int64_t ldc, Uplo uplo, double diag_add, void* ws, size_t ws_bytes);
 // Per host thread: while a scratch is installed, gemm() routes products with m, n >= 128 and
-// k >= 256 whose scratch fits to gemm_ozaki (the QDWHP_FP64_EMULATED solves install it).
+// k >= 64 whose scratch fits to gemm_ozaki (the emulated-precision solves install it).
 struct EmulationScope {
   EmulationScope(void* ws, size_t bytes);
   ~EmulationScope();

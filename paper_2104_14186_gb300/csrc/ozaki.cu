@@ -13,10 +13,13 @@
 // where every digit product D^A_s D^B_t is an exact integer matrix product: each term is
 // < 2^12 in magnitude, so a sum over K <= 4096 terms stays below 2^24 and is exact in the
 // FP32 accumulators of mma.sync m16n8k16 (bf16 x bf16 -> f32).  Each such product is scaled
-// by its power of two and added into FP64 accumulators.  The pairs with s + t <= 11 are
-// kept (53 of the 81): the first dropped level contributes at most
-// 9 K 63^2 2^-72 2^(e_i + f_j), below the rounding of an FP64 dot product of length K.
-// Longer K is cut into chunks of 4096 with an FP64 flush after each.
+// by its power of two and added into FP64 accumulators.  The pairs with s + t <= 12 are
+// kept (60 of the 81).  The dropped pairs are a bias, not noise, where the digit products
+// share a sign (a sum of squares): at most 6 K 63^2 2^-78 2^(e_i + f_j), below FP64 rounding
+// for the K of this library (at s + t <= 11 it reached 1e-13 relative at K = 16384).  Pairs
+// of one level s + t share the scale 2^(-6 (s + t)), so they share an FP32 accumulator as
+// long as it holds at most 4224 digit products (exact); it is flushed into FP64 when the
+// level changes or the budget would be exceeded.
 //
 // Layout: digit slices are stored as [slice][row][k_pad] bfloat16 with K contiguous (op(A)
 // rows, op(B) columns), zero-padded to the CTA tile; the GEMM streams a (slice pair, K block)
@@ -34,8 +37,9 @@ namespace {
 
 constexpr int kOzS = 9;          // digits per entry
 constexpr int kOzBeta = 6;       // bits per digit
-constexpr int kOzT = 11;         // keep digit pairs with s + t <= kOzT (1-based)
-constexpr int kOzKc = 4096;      // FP32-exact chunk: kOzKc * 63^2 < 2^24
+constexpr int kOzT = 12;         // keep digit pairs with s + t <= kOzT (1-based)
+constexpr int kOzBudget = 4224;  // FP32 exactness: at most this many digit products (each
+                                 // < 2^12 in magnitude) in one accumulator: 4224 * 63^2 < 2^24
 constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 32;   // kOzBN: padding of op(B) (either tile divides it)
 constexpr int kOzLd = kOzBK + 8; // smem row stride (bf16): 80 bytes, conflict-free ldmatrix
 constexpr int kOzThreads = 256;
@@ -46,6 +50,7 @@ struct PairTable {
   int npairs;
   unsigned char s[kOzS * kOzS];
   unsigned char t[kOzS * kOzS];
+  unsigned char lev[kOzS * kOzS];
   double scale[kOzS * kOzS];
 };
 __constant__ PairTable c_pairs;
@@ -243,6 +248,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
     cp_async_commit();
   }
   int cp = 0, ckb = 0;   // (pair, K block) being computed
+  int terms = 0;         // digit products in the FP32 accumulators since the last flush
   for (int step = 0; step < total; ++step) {
     cp_async_wait<STAGES - 2>();
     __syncthreads();
@@ -277,8 +283,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
     }
-    // flush the exact FP32 digit product into FP64 at the end of a pair's K range or chunk
-    if (ckb == nkb - 1 || ((ckb + 1) % (kOzKc / kOzBK)) == 0) {
+    // flush the exact FP32 sums into FP64 when the next step changes level or would exceed
+    // the exactness budget (the same decision in every thread)
+    terms += kOzBK;
+    int np_ = cp, nkb_ = ckb + 1;
+    if (nkb_ == nkb) {
+      nkb_ = 0;
+      ++np_;
+    }
+    if (np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || terms + kOzBK > kOzBudget) {
+      terms = 0;
       const double sc = c_pairs.scale[cp];
 #pragma unroll
       for (int i = 0; i < MT; ++i)
@@ -369,6 +383,7 @@ qdwhp_status upload_pairs() {
         if (tt < 1 || tt > kOzS) continue;
         t.s[p] = (unsigned char)(s - 1);
         t.t[p] = (unsigned char)(tt - 1);
+        t.lev[p] = (unsigned char)lev;
         t.scale[p] = ldexp(1.0, -kOzBeta * lev);
         ++p;
       }

@@ -295,6 +295,10 @@ qdwhp_status build_outer_T(cudaStream_t st, const QRFactors& f, int64_t jo, int 
 
 qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f, double* scratch) {
   if (m < n || n < 0) return QDWHP_ERR_ARG;
+  // Householder products stay native FP64 in every precision mode: V is unit lower
+  // trapezoidal and the coefficient columns span many magnitudes, where the emulated
+  // product's normwise (row/column-scaled) error is far above FP64's componentwise one.
+  EmulationScope native_products(nullptr, 0);
   f.m = m;
   f.n = n;
   if (n == 0) return QDWHP_OK;
@@ -361,6 +365,7 @@ namespace {
 // the last outer block act on rows that are zero in the orgqr use and belong to Q otherwise).
 qdwhp_status apply_blocks(cudaStream_t st, const QRFactors& f, int64_t last_block, double* C, int64_t ncols,
                           int64_t ldc, double* scratch) {
+  EmulationScope native_products(nullptr, 0);   // as in geqrf
   const int64_t m = f.m, n = f.n;
   double* W = scratch;
   double* W2 = W + (size_t)NBO * ncols;

@@ -69,6 +69,13 @@ constexpr int64_t kKrylovMaxCols = 2048;
 // normalised off-diagonal inner products (computed in double-double) down to ~2u.
 constexpr double kJacobiTight = 4.5e-16;
 
+// Precision modes: Cholesky-based steps but the last in FP32, and/or the FP64 products
+// emulated on the BF16 tensor cores.
+bool fp32_steps(const qdwhp_opts& o) { return o.precision == QDWHP_MIXED || o.precision == QDWHP_MIXED_EMULATED; }
+bool emulated_products(const qdwhp_opts& o) {
+  return o.precision == QDWHP_FP64_EMULATED || o.precision == QDWHP_MIXED_EMULATED;
+}
+
 struct Common {
   // small-problem and control buffers shared by both drivers
   LanczosState* lst = nullptr;
@@ -158,13 +165,13 @@ struct EigWs {
   bool has_dc = false;   // n > kDcMin: Rayleigh-Ritz problems may need divide and conquer
   DcWs dc;               // its own buffers; the large ones are lent from the above at run time
   int dc_nodes = 0;      // splits of the last divide-and-conquer solve
-  char* emu = nullptr;   // QDWHP_FP64_EMULATED: scratch of the emulated products
+  char* emu = nullptr;   // emulated FP64 products: their scratch
   size_t emu_bytes = 0;
 };
 
 void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   carve_common(ar, n, n, o.lanczos_steps, w.c);
-  carve_qdwh(ar, n, n, false, w.q, o.precision == QDWHP_MIXED);
+  carve_qdwh(ar, n, n, false, w.q, fp32_steps(o));
   w.X = ar.take<double>((size_t)n * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
@@ -177,7 +184,7 @@ void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   w.S3 = ar.take<double>((size_t)n * n);
   w.has_dc = n > kDcMin;
   if (w.has_dc) carve_dc_own(ar, n, w.dc);
-  if (o.precision == QDWHP_FP64_EMULATED) {
+  if (emulated_products(o)) {
     w.emu_bytes = gemm_ozaki_ws_bytes(n, n, n);
     w.emu = ar.take<char>(w.emu_bytes);
   }
@@ -306,7 +313,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     QDWHP_TRY(axpby(st, n, n, (1.0 - s) * eps_side / absmu, A, lda, 0.0, w.X, n, -((1.0 - s) * t / absmu + s)));
     QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
     int n_qr = 0, n_chol = 0, n_f32 = 0;
-    QDWHP_TRY(run_schedule(st, n, n, w.X, n, hs.sched, o.precision == QDWHP_MIXED, w.q, &n_qr, &n_chol, &n_f32));
+    QDWHP_TRY(run_schedule(st, n, n, w.X, n, hs.sched, fp32_steps(o), w.q, &n_qr, &n_chol, &n_f32));
     inf.it_f32 = n_f32;
     // Step 3: QR of (r(A~) + I) / 2.
     QDWHP_TRY(axpby(st, n, n, 0.5, w.X, n, 0.0, w.X, n, 0.5));
@@ -378,13 +385,13 @@ struct SvdWs {
   double* Vj = nullptr;   // n x n capacity
   double* W = nullptr;    // n x n capacity: gathered V~
   double* At = nullptr;   // transposed input when m < n
-  char* emu = nullptr;    // QDWHP_FP64_EMULATED: scratch of the emulated products
+  char* emu = nullptr;    // emulated FP64 products: their scratch
   size_t emu_bytes = 0;
 };
 
 void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
   carve_common(ar, m, n, o.lanczos_steps, w.c);
-  carve_qdwh(ar, m, n, true, w.q, o.precision == QDWHP_MIXED);
+  carve_qdwh(ar, m, n, true, w.q, fp32_steps(o));
   w.X = ar.take<double>((size_t)m * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
@@ -396,7 +403,7 @@ void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, b
   w.Vj = ar.take<double>((size_t)n * n);
   w.W = ar.take<double>((size_t)n * n);
   if (need_transpose) w.At = ar.take<double>((size_t)m * n);
-  if (o.precision == QDWHP_FP64_EMULATED) {
+  if (emulated_products(o)) {
     const int64_t d = std::max(m, n);
     w.emu_bytes = gemm_ozaki_ws_bytes(d, d, d);
     w.emu = ar.take<char>(w.emu_bytes);
@@ -466,7 +473,7 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     QDWHP_TRY(axpby(st, m, n, 1.0 / alpha, A, lda, 0.0, w.X, m));
     QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
     int n_f32 = 0;
-    QDWHP_TRY(run_schedule(st, m, n, w.X, m, hs.sched, o.precision == QDWHP_MIXED, w.q, &inf.it_qr, &inf.it_chol,
+    QDWHP_TRY(run_schedule(st, m, n, w.X, m, hs.sched, fp32_steps(o), w.q, &inf.it_qr, &inf.it_chol,
                            &n_f32));
     inf.it_f32 = n_f32;
     // Step 3: QR of I - X^T X.
@@ -546,7 +553,8 @@ bool opts_valid(const qdwhp_opts& o) {
          o.guard >= 0.0 && o.guard < 1.0 && o.max_retries >= 0 && o.jacobi_max_sweeps >= 1 &&
          o.refine_steps >= 0 && o.refine_steps <= 64 &&
          (o.side == QDWHP_LARGEST || o.side == QDWHP_SMALLEST) &&
-         (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED || o.precision == QDWHP_FP64_EMULATED);
+         (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED || o.precision == QDWHP_FP64_EMULATED ||
+          o.precision == QDWHP_MIXED_EMULATED);
 }
 
 }  // namespace

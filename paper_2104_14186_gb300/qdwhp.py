@@ -29,7 +29,7 @@ STATUS_NAMES = {
     -5: "ERR_NONFINITE", -6: "ERR_TIMEOUT", -7: "ERR_CUDA", -8: "ERR_QUEUE_FULL", -9: "ERR_COUNT", 1: "PENDING",
 }
 LARGEST, SMALLEST = 0, 1
-FP64, MIXED, FP64_EMULATED = 0, 1, 2
+FP64, MIXED, FP64_EMULATED, MIXED_EMULATED = 0, 1, 2, 3
 
 
 class Opts(C.Structure):

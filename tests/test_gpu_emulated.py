@@ -3,7 +3,7 @@
 The emulated GEMM is checked against its definition (the numpy FP64 product) with the
 scheme's error bound: the inputs are rounded to 54 bits relative to the largest entry of
 each row of op(A) and column of op(B), digit pairs below 2^-66 of those are dropped, and the
-53 exact partial products are summed in FP64.  The solvers in QDWHP_FP64_EMULATED mode must
+60 exact partial products are summed in FP64.  The solvers in QDWHP_FP64_EMULATED mode must
 meet the plain-FP64 tolerances: |lambda - lambda*| <= 1e-12 ||A||_2,
 ||V^T V - I||_F <= 5e-15 n, residuals <= 1e-13."""
 
@@ -42,7 +42,7 @@ def emulation_bound(opA, opB, alpha, beta, C0):
     colmax = absB.max(axis=0, initial=0.0)[None, :]
     trunc = abs(alpha) * 2.0 ** -52 * (rowmax * absB.sum(axis=0)[None, :] + colmax * absA.sum(axis=1)[:, None])
     dropped = abs(alpha) * 1e-16 * k * rowmax * colmax
-    # (4 k + 64) u |A||B|: the FP64 reference's own rounding plus the 53-term FP64 sum
+    # (4 k + 64) u |A||B|: the FP64 reference's own rounding plus the FP64 sum of the digit products
     return (4 * k + 64) * U64 * scale + trunc + dropped + 1e-300
 
 
@@ -104,4 +104,16 @@ def test_emulated_svd(Q, m, n, frac, seed):
     mt = O.svd_metrics(q.A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), q.sigma[: q.k])
     assert mt["sigma_err"] <= 1e-12, mt
     assert mt["orthU"] <= 5e-15 * n and mt["orthV"] <= 5e-15 * n, mt
+    assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-13, mt
+
+
+def test_mixed_emulated_svd_refined_meets_fp64_tolerances(Q):
+    """FP32 Cholesky steps, emulated FP64 products elsewhere and 6 FP64 subspace-refinement
+    steps: the SVD workload (4096 x 4096, top 5 %) at the plain-FP64 tolerances."""
+    q = I.svd_logspaced(4096, 4096, 2000, 0.05)
+    r = Q.svd(dev(q.A), k=q.k, precision=Q.MIXED_EMULATED, refine_steps=6)
+    assert r.info["it_f32"] == 2
+    mt = O.svd_metrics(q.A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), q.sigma[: q.k])
+    assert mt["sigma_err"] <= 1e-12, mt
+    assert mt["orthU"] <= 5e-15 * 4096 and mt["orthV"] <= 5e-15 * 4096, mt
     assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-13, mt
