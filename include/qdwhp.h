@@ -61,7 +61,7 @@ typedef struct {
   int32_t side;           /* qdwhp_side (EIG only; SVD always returns the largest) */
   int32_t precision;      /* qdwhp_precision: QDWHP_FP64; QDWHP_MIXED (every Cholesky-based QDWH step
                              but the last in FP32; all else FP64); QDWHP_FP64_EMULATED (every product
-                             with m, n >= 128 and k >= 64 by qdwhp_gemm_f64_emulated's scheme, the
+                             with m, n >= 128 and k >= 256 by qdwhp_gemm_f64_emulated's scheme, the
                              rest native FP64); QDWHP_MIXED_EMULATED (both) */
   double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
   int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */

@@ -222,7 +222,7 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
   if (m == 0 || n == 0) return QDWHP_OK;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return QDWHP_ERR_ARG;
-  if (t_emu_ws != nullptr && m >= 128 && n >= 128 && k >= 64 && gemm_ozaki_ws_bytes(m, n, k) <= t_emu_bytes)
+  if (t_emu_ws != nullptr && m >= 128 && n >= 128 && k >= 256 && gemm_ozaki_ws_bytes(m, n, k) <= t_emu_bytes)
     return gemm_ozaki(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, t_emu_ws,
                       t_emu_bytes);
   const int M = (int)m, N = (int)n, K = (int)k;

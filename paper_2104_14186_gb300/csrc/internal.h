@@ -27,7 +27,7 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
                         const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                         int64_t ldc, Uplo uplo, double diag_add, void* ws, size_t ws_bytes);
 // Per host thread: while a scratch is installed, gemm() routes products with m, n >= 128 and
-// k >= 64 whose scratch fits to gemm_ozaki (the emulated-precision solves install it).
+// k >= 256 whose scratch fits to gemm_ozaki (the emulated-precision solves install it).
 struct EmulationScope {
   EmulationScope(void* ws, size_t bytes);
   ~EmulationScope();
