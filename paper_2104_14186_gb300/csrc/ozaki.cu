@@ -12,7 +12,7 @@
 //     C_ij = 2^(e_i + f_j) sum_{s,t} 2^(-6 (s + t)) (D^A_s D^B_t)_ij ,
 // where every digit product D^A_s D^B_t is an exact integer matrix product: each term is
 // < 2^12 in magnitude, so a sum over K <= 4096 terms stays below 2^24 and is exact in the
-// FP32 accumulators of mma.sync m16n8k16 (bf16 x bf16 -> f32).  Each such product is scaled
+// FP32 accumulators of the tensor cores (bf16 x bf16 -> f32).  Each such product is scaled
 // by its power of two and added into FP64 accumulators.  The pairs with s + t <= 12 are
 // kept (60 of the 81).  The dropped pairs are a bias, not noise, where the digit products
 // share a sign (a sum of squares): at most 6 K 63^2 2^-78 2^(e_i + f_j), below FP64 rounding
@@ -22,8 +22,8 @@
 // level changes or the budget would be exceeded.
 //
 // Layout: digit slices are stored as [slice][row][k_pad] bfloat16 with K contiguous (op(A)
-// rows, op(B) columns), zero-padded to the CTA tile; the GEMM streams a (slice pair, K block)
-// sequence through a 3-stage cp.async pipeline and ldmatrix.
+// rows, op(B) columns), zero-padded to the 128 x 64 tile; the product kernel (tcgen05, below)
+// streams a (slice pair, K block) sequence through a 4-stage ring in shared memory.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -40,9 +40,8 @@ constexpr int kOzBeta = 6;       // bits per digit
 constexpr int kOzT = 12;         // keep digit pairs with s + t <= kOzT (1-based)
 constexpr int kOzBudget = 4224;  // FP32 exactness: at most this many digit products (each
                                  // < 2^12 in magnitude) in one accumulator: 4224 * 63^2 < 2^24
-constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 32;   // kOzBN: padding of op(B) (either tile divides it)
-constexpr int kOzLd = kOzBK + 8; // smem row stride (bf16): 80 bytes, conflict-free ldmatrix
-constexpr int kOzThreads = 256;
+constexpr int kOzBM = 128, kOzBN = 128;   // row padding of the op(A) and op(B) digit slices
+constexpr int kOzKPad = 64;               // K padding of the digit slices (one K block)
 constexpr int kExpEmpty = -2000000000;   // no entry seen yet (row of zeros)
 constexpr int kExpNonfinite = 1 << 20;   // a NaN or Inf in the row
 
@@ -154,77 +153,114 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-__device__ __forceinline__ void ldmatrix_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(s));
+// ---- tcgen05 (UMMA) digit-product kernel ----
+//
+// The same 60 exact digit products on the 5th-generation tensor cores: one thread issues
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16) reading both operands
+// from shared memory through matrix descriptors (K-major, 128-byte swizzle: 8-row atoms of
+// 1024 bytes, 16-byte chunk c of row r stored at chunk c ^ (r % 8)), with the FP32 sums in
+// tensor memory.  Tensor memory holds two 128-column accumulators: the sums of one level run
+// are read back (tcgen05.ld) and added into the FP64 registers while the next run's MMAs
+// accumulate into the other.  Operand tiles (128 rows x 64 K per operand) arrive by cp.async
+// into a 4-stage ring; a stage is refilled once the mbarrier its MMAs committed to has fired.
+// Every mbarrier wait is bounded; on a timeout the tile is written as NaN and err is set.
+constexpr int kUmN = 128;
+constexpr int kUmBK = 64;
+constexpr int kUmStages = 4;
+constexpr int kUmThreads = 256;
+constexpr uint32_t kUmTileBytes = 128 * kUmBK * 2;              // 16 KB per operand
+constexpr uint32_t kUmStageBytes = 2 * kUmTileBytes;
+constexpr size_t kUmSmemBytes = (size_t)kUmStages * kUmStageBytes + 1024;
+constexpr int kUmSpin = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t sw128_off(int r, int ch) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4));
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// shared-memory matrix descriptor: start >> 4, leading byte offset 16 (unused with swizzle),
+// stride byte offset 1024 (next 8-row atom), descriptor version 1, 128-byte swizzle
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// One CTA: a 128 x BN tile of C, 8 warps of (16 MT) x 32 (MT x 4 mma tiles of 16 x 8):
-//   MT = 4: 2 x 4 warps, BN = 128 (16 mma per 6 ldmatrix.x4 per 16-deep step), 3 stages;
-//   MT = 2: 4 x 2 warps, BN = 64 (more CTAs for narrow products; two CTAs fit an SM), 3 stages.
-// The exact FP32 digit products live in registers; their FP64 sums live in shared memory,
-// 16 MT doubles per thread at index f * 256 + thread, touched only by that thread.
-template <int MT>
-struct OzCfg {
-  static constexpr int kWarpsM = kOzBM / (16 * MT);
-  static constexpr int kWarpsN = 8 / kWarpsM;
-  static constexpr int kBN = kWarpsN * 32;
-  static constexpr int kStages = 3;
-  static constexpr size_t kSmemStages = (size_t)kStages * (kOzBM + kBN) * kOzLd * sizeof(unsigned short);
-  static constexpr size_t kSmemBytes = kSmemStages + (size_t)16 * MT * kOzThreads * sizeof(double);
-};
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kUmSpin; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
-template <int MT>
-__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, int k_pad, int rows_a_pad,
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+               : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(kUmThreads, 1) oz_umma_kernel(int M, int N, int k_pad, int rows_a_pad,
                                                                 int rows_b_pad, const unsigned short* __restrict__ Asl,
                                                                 const unsigned short* __restrict__ Bsl,
-                                                                const int* __restrict__ ea,
-                                                                const int* __restrict__ eb, double alpha, double beta,
-                                                                double* C, int64_t ldc, int uplo, double diag_add) {
-  using Cfg = OzCfg<MT>;
-  constexpr int BN = Cfg::kBN, STAGES = Cfg::kStages;
-  extern __shared__ __align__(128) unsigned char oz_smem[];
-  unsigned short* sA = reinterpret_cast<unsigned short*>(oz_smem);
-  unsigned short* sB = sA + (size_t)STAGES * kOzBM * kOzLd;
-  double* acc64 = reinterpret_cast<double*>(oz_smem + Cfg::kSmemStages);
-  const int bm = blockIdx.y, bn = blockIdx.x;
-  const int m0 = bm * kOzBM, n0 = bn * BN;
-  if (uplo == LOWER && m0 + kOzBM <= n0) return;   // tile strictly above the diagonal
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp % Cfg::kWarpsM, wn = warp / Cfg::kWarpsM;
-  const int nkb = k_pad / kOzBK;
+                                                                const int* __restrict__ ea, const int* __restrict__ eb,
+                                                                double alpha, double beta, double* C, int64_t ldc,
+                                                                int uplo, double diag_add, int* err) {
+  extern __shared__ unsigned char um_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)um_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t bar_stage[kUmStages];
+  __shared__ __align__(8) uint64_t bar_run[2];
+  __shared__ __align__(8) uint64_t bar_done;
+  __shared__ int s_abort;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kUmN;
+  if (uplo == LOWER && m0 + 128 <= n0) return;   // tile strictly above the diagonal
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nkb = k_pad / kUmBK;
   const int npairs = c_pairs.npairs;
   const int total = npairs * nkb;
   const size_t slice_a = (size_t)rows_a_pad * k_pad, slice_b = (size_t)rows_b_pad * k_pad;
+  const uint32_t sbase = smem_addr(smem);
 
-  // the (pair, K block) of the next stage to load, advanced incrementally
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(2 * kUmN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kUmStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_stage[s])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_run[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_run[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_done)));
+    s_abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
   int lp = 0, lkb = 0;
-  auto load_next = [&](int buf) {
-    const unsigned short* As = Asl + (size_t)c_pairs.s[lp] * slice_a + (size_t)m0 * k_pad + lkb * kOzBK;
-    const unsigned short* Bs = Bsl + (size_t)c_pairs.t[lp] * slice_b + (size_t)n0 * k_pad + lkb * kOzBK;
-    unsigned short* da = sA + (size_t)buf * kOzBM * kOzLd;
-    unsigned short* db = sB + (size_t)buf * BN * kOzLd;
+  auto load_next = [&](int stage) {
+    const unsigned short* As = Asl + (size_t)c_pairs.s[lp] * slice_a + (size_t)m0 * k_pad + lkb * kUmBK;
+    const unsigned short* Bs = Bsl + (size_t)c_pairs.t[lp] * slice_b + (size_t)n0 * k_pad + lkb * kUmBK;
+    unsigned char* dA = smem + (size_t)stage * kUmStageBytes;
+    unsigned char* dB = dA + kUmTileBytes;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {   // A: 128 rows x 4 chunks of 16 bytes
-      const int c = tid + kOzThreads * q;
-      const int row = c >> 2, ch = c & 3;
-      cp_async16(da + row * kOzLd + ch * 8, As + (size_t)row * k_pad + ch * 8);
-    }
-#pragma unroll
-    for (int q = 0; q < BN / 64; ++q) {   // B: BN rows x 4 chunks
-      const int c = tid + kOzThreads * q;
-      const int row = c >> 2, ch = c & 3;
-      cp_async16(db + row * kOzLd + ch * 8, Bs + (size_t)row * k_pad + ch * 8);
+    for (int q = 0; q < 4; ++q) {   // 128 rows x 8 chunks of 16 bytes per operand
+      const int c = tid + kUmThreads * q;
+      const int r = c >> 3, ch = c & 7;
+      cp_async16(dA + sw128_off(r, ch), As + (size_t)r * k_pad + ch * 8);
+      cp_async16(dB + sw128_off(r, ch), Bs + (size_t)r * k_pad + ch * 8);
     }
     if (++lkb == nkb) {
       lkb = 0;
@@ -232,136 +268,149 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(int M, int N, in
     }
   };
 
-  float acc[MT][4][4];
+  // FP64 sums: row (warp % 4) * 32 + lane, columns (warp / 4) * 64 + [0, 64)
+  double acc64[64];
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+  for (int j = 0; j < 64; ++j) acc64[j] = 0.0;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t col_base = (uint32_t)((warp >> 2) * 64);
+  auto flush = [&](int r, double sc) -> bool {
+    if (!mbar_wait(smem_addr(&bar_run[r & 1]), (uint32_t)((r >> 1) & 1))) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int h = 0; h < 2; ++h) {
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_base + (uint32_t)((r & 1) * kUmN) + col_base + (uint32_t)(32 * h), v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-#pragma unroll 8
-  for (int f = 0; f < 16 * MT; ++f) acc64[f * kOzThreads + tid] = 0.0;
+      for (int j = 0; j < 32; ++j) acc64[32 * h + j] = fma((double)__uint_as_float(v[j]), sc, acc64[32 * h + j]);
+    }
+    return true;
+  };
 
 #pragma unroll
-  for (int st = 0; st < STAGES - 1; ++st) {
+  for (int st = 0; st < kUmStages - 1; ++st) {
     if (st < total) load_next(st);
     cp_async_commit();
   }
-  int cp = 0, ckb = 0;   // (pair, K block) being computed
-  int terms = 0;         // digit products in the FP32 accumulators since the last flush
+  const uint32_t idesc =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUmN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  int cp = 0, ckb = 0, terms = 0, run = 0;
+  bool run_first = true;
+  int pending = -1;
+  double pending_scale = 0.0;
+  bool ok = true;
   for (int step = 0; step < total; ++step) {
-    cp_async_wait<STAGES - 2>();
+    const int stage = step % kUmStages;
+    cp_async_wait<kUmStages - 2>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (step + STAGES - 1 < total) load_next((step + STAGES - 1) % STAGES);
-    cp_async_commit();
-    const int buf = step % STAGES;
-    const unsigned short* a_s = sA + (size_t)buf * kOzBM * kOzLd;
-    const unsigned short* b_s = sB + (size_t)buf * BN * kOzLd;
-#pragma unroll
-    for (int kk = 0; kk < kOzBK; kk += 16) {
-      unsigned af[MT][4];
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt) {
-        const int row = wm * 16 * MT + mt * 16 + (lane & 15);
-        const int col = kk + ((lane >> 4) << 3);
-        ldmatrix_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], a_s + row * kOzLd + col);
-      }
-      unsigned bfr[4][2];
-#pragma unroll
-      for (int np = 0; np < 2; ++np) {
-        const int nrow = wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3);
-        const int col = kk + (((lane >> 3) & 1) << 3);
-        unsigned r0, r1, r2, r3;
-        ldmatrix_x4(r0, r1, r2, r3, b_s + nrow * kOzLd + col);
-        bfr[2 * np][0] = r0;
-        bfr[2 * np][1] = r1;
-        bfr[2 * np + 1][0] = r2;
-        bfr[2 * np + 1][1] = r3;
-      }
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (s_abort) {
+      ok = false;
+      break;
     }
-    // flush the exact FP32 sums into FP64 when the next step changes level or would exceed
-    // the exactness budget (the same decision in every thread)
-    terms += kOzBK;
+    terms += kUmBK;
     int np_ = cp, nkb_ = ckb + 1;
     if (nkb_ == nkb) {
       nkb_ = 0;
       ++np_;
     }
-    if (np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || terms + kOzBK > kOzBudget) {
+    const bool run_ends = np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || terms + kUmBK > kOzBudget;
+    if (tid == 0) {
+      const uint32_t a0 = sbase + (uint32_t)stage * kUmStageBytes, b0 = a0 + kUmTileBytes;
+      const uint32_t dcol = tmem + (uint32_t)((run & 1) * kUmN);
+#pragma unroll
+      for (int kk = 0; kk < kUmBK / 16; ++kk) {
+        const uint64_t da = umma_desc_sw128(a0 + 32 * kk), db = umma_desc_sw128(b0 + 32 * kk);
+        const uint32_t accum = (run_first && kk == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+            "l"(da), "l"(db), "r"(idesc), "r"(accum));
+      }
+      umma_commit(smem_addr(&bar_stage[stage]));
+      if (run_ends) umma_commit(smem_addr(&bar_run[run & 1]));
+    }
+    run_first = false;
+    if (pending >= 0) {
+      if (!flush(pending, pending_scale)) {
+        s_abort = 1;
+        ok = false;
+      }
+      pending = -1;
+    }
+    if (run_ends) {
+      pending = run;
+      pending_scale = c_pairs.scale[cp];
+      ++run;
+      run_first = true;
       terms = 0;
-      const double sc = c_pairs.scale[cp];
-#pragma unroll
-      for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            double* slot = acc64 + ((i * 4 + j) * 4 + q) * kOzThreads + tid;
-            *slot = fma((double)acc[i][j][q], sc, *slot);
-            acc[i][j][q] = 0.f;
-          }
     }
-    if (++ckb == nkb) {
-      ckb = 0;
-      ++cp;
-    }
-  }
-  cp_async_wait<0>();
-
-  // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
-  const int g = lane >> 2, t4 = lane & 3;
-#pragma unroll
-  for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int i = m0 + wm * 16 * MT + mt * 16 + g + 8 * half;
-      if (i >= M) continue;
-      const int e_i = ea[i];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int j = n0 + wn * 32 + nt * 8 + 2 * t4 + cc;
-          if (j >= N) continue;
-          if (uplo == LOWER && i < j) continue;
-          const int f_j = eb[j];
-          double v;
-          if (e_i == kExpNonfinite || f_j == kExpNonfinite) {
-            v = __longlong_as_double(0x7ff8000000000000ll);
-          } else if (e_i == kExpEmpty || f_j == kExpEmpty) {
-            v = 0.0;
-          } else {
-            v = alpha * ldexp(acc64[((mt * 4 + nt) * 4 + 2 * half + cc) * kOzThreads + tid], e_i + f_j);
-          }
-          double* cptr = C + i + (int64_t)j * ldc;
-          if (beta != 0.0) v = fma(beta, *cptr, v);
-          if (i == j) v += diag_add;
-          *cptr = v;
+    const int nxt = step + kUmStages - 1;
+    if (nxt < total) {
+      if (step >= 1) {
+        const int prev = step - 1;
+        if (!mbar_wait(smem_addr(&bar_stage[prev % kUmStages]), (uint32_t)((prev / kUmStages) & 1))) {
+          s_abort = 1;
+          ok = false;
         }
       }
+      load_next(nxt % kUmStages);
     }
+    cp_async_commit();
+    cp = np_;
+    ckb = nkb_;
+  }
+  cp_async_wait<0>();
+  // all MMAs issued so far have finished before tensor memory is read or released
+  if (tid == 0) umma_commit(smem_addr(&bar_done));
+  if (!mbar_wait(smem_addr(&bar_done), 0)) ok = false;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok && pending >= 0 && !flush(pending, pending_scale)) ok = false;
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (s_abort) ok = false;
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kUmN));
+  if (!ok && lane == 0) atomicExch(err, 1);
+
+  // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
+  const int i = m0 + (warp & 3) * 32 + lane;
+  if (i >= M) return;
+  const int e_i = ea[i];
+#pragma unroll
+  for (int c = 0; c < 64; ++c) {
+    const int j = n0 + (int)col_base + c;
+    if (j >= N || (uplo == LOWER && i < j)) continue;
+    const int f_j = eb[j];
+    double v;
+    if (!ok || e_i == kExpNonfinite || f_j == kExpNonfinite) {
+      v = __longlong_as_double(0x7ff8000000000000ll);
+    } else if (e_i == kExpEmpty || f_j == kExpEmpty) {
+      v = 0.0;
+    } else {
+      v = alpha * ldexp(acc64[c], e_i + f_j);
+    }
+    double* cptr = C + i + (int64_t)j * ldc;
+    if (beta != 0.0) v = fma(beta, *cptr, v);
+    if (i == j) v += diag_add;
+    *cptr = v;
   }
 }
 
-template <int MT>
-qdwhp_status launch_oz(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
-                       const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta, double* C,
-                       int64_t ldc, Uplo uplo, double diag_add) {
-  using Cfg = OzCfg<MT>;
+qdwhp_status launch_umma(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
+                         const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta, double* C,
+                         int64_t ldc, Uplo uplo, double diag_add, int* err) {
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)Cfg::kSmemBytes);
+    attr_err = cudaFuncSetAttribute(oz_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
   });
   QDWHP_CUDA_TRY(attr_err);
-  dim3 grid(np / Cfg::kBN, mp / kOzBM);
-  oz_gemm_kernel<MT><<<grid, kOzThreads, Cfg::kSmemBytes, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha,
-                                                                beta, C, ldc, (int)uplo, diag_add);
+  dim3 grid(np / kUmN, mp / 128);
+  oz_umma_kernel<<<grid, kUmThreads, kUmSmemBytes, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C,
+                                                         ldc, (int)uplo, diag_add, err);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }
@@ -397,8 +446,8 @@ qdwhp_status upload_pairs() {
 
 size_t gemm_ozaki_ws_bytes(int64_t m, int64_t n, int64_t k) {
   if (m <= 0 || n <= 0 || k <= 0) return 0;
-  const size_t mp = ceil_to(m, kOzBM), np = ceil_to(n, kOzBN), kp = ceil_to(k, kOzBK);
-  return (size_t)kOzS * (mp + np) * kp * 2 + (mp + np) * sizeof(int) + 1024;
+  const size_t mp = ceil_to(m, kOzBM), np = ceil_to(n, kOzBN), kp = ceil_to(k, kOzKPad);
+  return (size_t)kOzS * (mp + np) * kp * 2 + (mp + np + 4) * sizeof(int) + 1024;
 }
 
 qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
@@ -410,11 +459,12 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
   if (k == 0) return gemm(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add);
   if (ws == nullptr || ws_bytes < gemm_ozaki_ws_bytes(m, n, k)) return QDWHP_ERR_NOMEM;
   QDWHP_TRY(upload_pairs());
-  const int mp = ceil_to(m, kOzBM), np = ceil_to(n, kOzBN), kp = ceil_to(k, kOzBK);
+  const int mp = ceil_to(m, kOzBM), np = ceil_to(n, kOzBN), kp = ceil_to(k, kOzKPad);
   unsigned short* Asl = (unsigned short*)ws;
   unsigned short* Bsl = Asl + (size_t)kOzS * mp * kp;
   int* ea = (int*)(Bsl + (size_t)kOzS * np * kp);
   int* eb = ea + mp;
+  int* err = eb + np;   // set by the tcgen05 kernel if a bounded wait gave up (its tile is then NaN)
   // exponents: op(A) rows (r contiguous iff A is not transposed), op(B) columns (j contiguous
   // iff B is transposed)
   oz_init_exp_kernel<<<ceil_div(mp + np, 256), 256, 0, st>>>(mp + np, ea);
@@ -433,15 +483,7 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
     const double shape[5] = {(double)m, (double)n, (double)k, (double)(uplo == LOWER), -1.0};
     prof_slot = gemm_prof_start(st, flops, shape);
   }
-  // 128 x 128 tiles when they fill the GPU twice over, else 128 x 64 (twice the CTAs)
-  int dev = 0, sms = kNumSMs;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t big_tiles = (int64_t)(mp / kOzBM) * (np / 128) / (uplo == LOWER ? 2 : 1);
-  if (big_tiles >= 2 * sms) {
-    QDWHP_TRY(launch_oz<4>(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add));
-  } else {
-    QDWHP_TRY(launch_oz<2>(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add));
-  }
+  QDWHP_TRY(launch_umma(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add, err));
   if (prof_slot >= 0) gemm_prof_stop(st, prof_slot);
   return QDWHP_OK;
 }
