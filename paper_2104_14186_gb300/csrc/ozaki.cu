@@ -24,6 +24,8 @@
 // Layout: digit slices are stored as [slice][row][k_pad] bfloat16 with K contiguous (op(A)
 // rows, op(B) columns), zero-padded to the 128 x 64 tile; the product kernel (tcgen05, below)
 // streams a (slice pair, K block) sequence through a 4-stage ring in shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -415,6 +417,284 @@ qdwhp_status launch_umma(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, 
   return QDWHP_OK;
 }
 
+// ---- warp-specialised TMA + tcgen05 digit-product kernel ----
+//
+// Warp 8 (one thread) feeds a 4-stage ring with TMA (cp.async.bulk.tensor, 128-byte swizzle
+// written by the copy engine, each stage's "full" mbarrier counting the bytes) and issues the
+// MMAs of a stage as soon as it is full; each stage's MMAs commit to its "empty" mbarrier, which
+// releases the stage to the next copy.  A level run (digit pairs of one level, at most 66 K
+// blocks) accumulates into one of two 128-column TMEM buffers and commits to that buffer's
+// "run done" mbarrier.  Warps 0-7 only flush: for each run they wait on "run done", read the
+// FP32 sums (tcgen05.ld), add them into their FP64 registers and arrive on the buffer's "free"
+// mbarrier, which the issuing thread waits on before reusing the buffer two runs later.  The
+// flush warps derive the run schedule from the pair table (no per-step synchronisation).
+constexpr int kWsThreads = 288;
+constexpr int kWsRunSteps = kOzBudget / kUmBK;   // K blocks per run at most (exact FP32 sums)
+
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (int it = 0; it < kUmSpin; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+    oz_umma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                      int k_pad, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
+                      double* C, int64_t ldc, int uplo, double diag_add, int* err) {
+  extern __shared__ unsigned char ws_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)ws_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t bar_full[kUmStages], bar_empty[kUmStages];
+  __shared__ __align__(8) uint64_t bar_run[2], bar_free[2], bar_done;
+  __shared__ int s_abort;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kUmN;
+  if (uplo == LOWER && m0 + 128 <= n0) return;   // tile strictly above the diagonal
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nkb = k_pad / kUmBK;
+  const int npairs = c_pairs.npairs;
+  const int total = npairs * nkb;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"(2 * kUmN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 256) {
+    for (int s = 0; s < kUmStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_empty[s])));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_run[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&bar_free[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_done)));
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  volatile int* abort_flag = &s_abort;
+  bool ok = true;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      const uint32_t sbase = smem_addr(smem);
+      int lp = 0, lkb = 0;
+      auto issue_load = [&](int stage) {
+        const uint32_t bar = smem_addr(&bar_full[stage]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kUmStageBytes)
+                     : "memory");
+        const uint32_t dA = sbase + (uint32_t)stage * kUmStageBytes;
+        tma_load_3d(dA, &mapA, lkb * kUmBK, m0, (int)c_pairs.s[lp], bar);
+        tma_load_3d(dA + kUmTileBytes, &mapB, lkb * kUmBK, n0, (int)c_pairs.t[lp], bar);
+        if (++lkb == nkb) {
+          lkb = 0;
+          ++lp;
+        }
+      };
+      for (int st = 0; st < kUmStages - 1 && st < total; ++st) issue_load(st);
+      const uint32_t idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUmN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      int cp = 0, ckb = 0, steps_in_run = 0, run = 0;
+      bool run_first = true;
+      for (int step = 0; step < total && ok; ++step) {
+        const int stage = step % kUmStages;
+        if (!mbar_wait_or_abort(smem_addr(&bar_full[stage]), (uint32_t)((step / kUmStages) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        if (run_first && run >= 2 &&
+            !mbar_wait_or_abort(smem_addr(&bar_free[run & 1]), (uint32_t)(((run >> 1) - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = sbase + (uint32_t)stage * kUmStageBytes, b0 = a0 + kUmTileBytes;
+        const uint32_t dcol = tmem + (uint32_t)((run & 1) * kUmN);
+#pragma unroll
+        for (int kk = 0; kk < kUmBK / 16; ++kk) {
+          const uint64_t da = umma_desc_sw128(a0 + 32 * kk), db = umma_desc_sw128(b0 + 32 * kk);
+          const uint32_t accum = (run_first && kk == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+              "l"(da), "l"(db), "r"(idesc), "r"(accum));
+        }
+        umma_commit(smem_addr(&bar_empty[stage]));
+        ++steps_in_run;
+        int np_ = cp, nkb_ = ckb + 1;
+        if (nkb_ == nkb) {
+          nkb_ = 0;
+          ++np_;
+        }
+        const bool run_ends = np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || steps_in_run >= kWsRunSteps;
+        if (run_ends) {
+          umma_commit(smem_addr(&bar_run[run & 1]));
+          ++run;
+          run_first = true;
+          steps_in_run = 0;
+        } else {
+          run_first = false;
+        }
+        const int nxt = step + kUmStages - 1;
+        if (nxt < total) {
+          if (step >= 1 && !mbar_wait_or_abort(smem_addr(&bar_empty[(step - 1) % kUmStages]),
+                                               (uint32_t)(((step - 1) / kUmStages) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          issue_load(nxt % kUmStages);
+        }
+        cp = np_;
+        ckb = nkb_;
+      }
+      if (!ok) *abort_flag = 1;
+      umma_commit(smem_addr(&bar_done));   // every MMA issued so far
+    }
+    __syncwarp();
+  } else {
+    // flush warps: row (warp % 4) * 32 + lane, columns (warp / 4) * 64 + [0, 64)
+    double acc64[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc64[j] = 0.0;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t col_base = (uint32_t)((warp >> 2) * 64);
+    int run = 0;
+    for (int p = 0; p < npairs && ok;) {
+      int q = p;
+      while (q < npairs && c_pairs.lev[q] == c_pairs.lev[p]) ++q;   // pairs [p, q) share a level
+      const int level_steps = (q - p) * nkb;
+      const double sc = c_pairs.scale[p];
+      for (int done = 0; done < level_steps && ok; done += kWsRunSteps, ++run) {
+        if (!mbar_wait_or_abort(smem_addr(&bar_run[run & 1]), (uint32_t)((run >> 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)((run & 1) * kUmN) + col_base + (uint32_t)(32 * h), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc64[32 * h + j] = fma((double)__uint_as_float(v[j]), sc, acc64[32 * h + j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_free[run & 1])) : "memory");
+      }
+      p = q;
+    }
+    if (!ok) *abort_flag = 1;
+    if (!mbar_wait_or_abort(smem_addr(&bar_done), 0, abort_flag)) ok = false;
+    // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
+    __syncwarp();
+    const bool good = ok && !*abort_flag;
+    const int i = m0 + (warp & 3) * 32 + lane;
+    if (i < M) {
+      const int e_i = ea[i];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) {
+        const int j = n0 + (int)col_base + c;
+        if (j >= N || (uplo == LOWER && i < j)) continue;
+        const int f_j = eb[j];
+        double v;
+        if (!good || e_i == kExpNonfinite || f_j == kExpNonfinite) {
+          v = __longlong_as_double(0x7ff8000000000000ll);
+        } else if (e_i == kExpEmpty || f_j == kExpEmpty) {
+          v = 0.0;
+        } else {
+          v = alpha * ldexp(acc64[c], e_i + f_j);
+        }
+        double* cptr = C + i + (int64_t)j * ldc;
+        if (beta != 0.0) v = fma(beta, *cptr, v);
+        if (i == j) v += diag_add;
+        *cptr = v;
+      }
+    }
+    if (!good && lane == 0) atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kUmN));
+}
+
+// Tensor maps of the digit slices: [slice][rows_pad][k_pad] bfloat16 seen as a 3-D tensor
+// (k innermost), box 64 x 128 x 1 with the 128-byte swizzle the MMA descriptors expect.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+qdwhp_status slice_map(CUtensorMap* map, const unsigned short* base, int rows_pad, int k_pad) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) {
+    set_error_message("cuTensorMapEncodeTiled is not available from the driver");
+    return QDWHP_ERR_CUDA;
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)kOzS};
+  const cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * k_pad * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)kUmBK, 128u, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error_message("cuTensorMapEncodeTiled rejected a digit-slice tensor map");
+    return QDWHP_ERR_CUDA;
+  }
+  return QDWHP_OK;
+}
+
+qdwhp_status launch_umma_ws(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
+                            const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta,
+                            double* C, int64_t ldc, Uplo uplo, double diag_add, int* err) {
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(oz_umma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
+  });
+  QDWHP_CUDA_TRY(attr_err);
+  CUtensorMap mapA, mapB;
+  QDWHP_TRY(slice_map(&mapA, Asl, mp, kp));
+  QDWHP_TRY(slice_map(&mapB, Bsl, np, kp));
+  dim3 grid(np / kUmN, mp / 128);
+  oz_umma_ws_kernel<<<grid, kWsThreads, kUmSmemBytes, st>>>(mapA, mapB, (int)m, (int)n, kp, ea, eb, alpha, beta, C,
+                                                            ldc, (int)uplo, diag_add, err);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
 int ceil_to(int64_t a, int b) { return (int)(((a + b - 1) / b) * b); }
 
 std::once_flag g_pairs_once;
@@ -483,7 +763,7 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
     const double shape[5] = {(double)m, (double)n, (double)k, (double)(uplo == LOWER), -1.0};
     prof_slot = gemm_prof_start(st, flops, shape);
   }
-  QDWHP_TRY(launch_umma(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add, err));
+  QDWHP_TRY(launch_umma_ws(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add, err));
   if (prof_slot >= 0) gemm_prof_stop(st, prof_slot);
   return QDWHP_OK;
 }
