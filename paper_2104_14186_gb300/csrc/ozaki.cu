@@ -43,7 +43,7 @@ constexpr int kOzT = 12;         // keep digit pairs with s + t <= kOzT (1-based
 constexpr int kOzBudget = 4224;  // FP32 exactness: at most this many digit products (each
                                  // < 2^12 in magnitude) in one accumulator: 4224 * 63^2 < 2^24
 constexpr int kOzBM = 128, kOzBN = 128;   // row padding of the op(A) and op(B) digit slices
-constexpr int kOzKPad = 64;               // K padding of the digit slices (one K block)
+constexpr int kOzKPad = 128;              // K padding of the digit slices (one K block)
 constexpr int kExpEmpty = -2000000000;   // no entry seen yet (row of zeros)
 constexpr int kExpNonfinite = 1 << 20;   // a NaN or Inf in the row
 
@@ -147,58 +147,32 @@ __global__ void oz_split_kernel(int rows, int k, int rows_pad, int k_pad, const 
 
 // ---- the digit-product GEMM ----
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 // ---- tcgen05 (UMMA) digit-product kernel ----
 //
-// The same 60 exact digit products on the 5th-generation tensor cores: one thread issues
-// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16) reading both operands
-// from shared memory through matrix descriptors (K-major, 128-byte swizzle: 8-row atoms of
-// 1024 bytes, 16-byte chunk c of row r stored at chunk c ^ (r % 8)), with the FP32 sums in
-// tensor memory.  Tensor memory holds two 128-column accumulators: the sums of one level run
-// are read back (tcgen05.ld) and added into the FP64 registers while the next run's MMAs
-// accumulate into the other.  Operand tiles (128 rows x 64 K per operand) arrive by cp.async
-// into a 4-stage ring; a stage is refilled once the mbarrier its MMAs committed to has fired.
-// Every mbarrier wait is bounded; on a timeout the tile is written as NaN and err is set.
+// The 60 exact digit products run on the 5th-generation tensor cores as
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16).  Both operands are
+// read from shared memory through matrix descriptors: K-major, 128-byte swizzle, i.e. 8-row
+// atoms of 1024 bytes with 16-byte chunk c of row r stored at chunk c ^ (r % 8), which is the
+// layout the TMA engine writes for a 64 x 128 box with the 128-byte swizzle.  The FP32 sums live
+// in tensor memory (two 128-column accumulators), and every mbarrier wait is bounded: on a
+// timeout the tile is written as NaN and err is set.
 constexpr int kUmN = 128;
-constexpr int kUmBK = 64;
-constexpr int kUmStages = 4;
-constexpr int kUmThreads = 256;
-constexpr uint32_t kUmTileBytes = 128 * kUmBK * 2;              // 16 KB per operand
+constexpr int kUmAtomK = 64;                                    // K of one 128-byte swizzle atom row
+constexpr int kUmBK = 128;                                      // K per stage: two atoms per operand
+constexpr int kUmStages = 3;
+constexpr uint32_t kUmAtomBytes = 128 * kUmAtomK * 2;           // 16 KB: 128 rows x 64 K
+constexpr uint32_t kUmTileBytes = 128 * kUmBK * 2;              // 32 KB per operand and stage
 constexpr uint32_t kUmStageBytes = 2 * kUmTileBytes;
 constexpr size_t kUmSmemBytes = (size_t)kUmStages * kUmStageBytes + 1024;
 constexpr int kUmSpin = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint32_t sw128_off(int r, int ch) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4));
-}
-
 // shared-memory matrix descriptor: start >> 4, leading byte offset 16 (unused with swizzle),
 // stride byte offset 1024 (next 8-row atom), descriptor version 1, 128-byte swizzle
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kUmSpin; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -212,218 +186,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
                : "r"(taddr));
 }
 
-__global__ void __launch_bounds__(kUmThreads, 1) oz_umma_kernel(int M, int N, int k_pad, int rows_a_pad,
-                                                                int rows_b_pad, const unsigned short* __restrict__ Asl,
-                                                                const unsigned short* __restrict__ Bsl,
-                                                                const int* __restrict__ ea, const int* __restrict__ eb,
-                                                                double alpha, double beta, double* C, int64_t ldc,
-                                                                int uplo, double diag_add, int* err) {
-  extern __shared__ unsigned char um_smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)um_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t bar_stage[kUmStages];
-  __shared__ __align__(8) uint64_t bar_run[2];
-  __shared__ __align__(8) uint64_t bar_done;
-  __shared__ int s_abort;
-  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kUmN;
-  if (uplo == LOWER && m0 + 128 <= n0) return;   // tile strictly above the diagonal
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nkb = k_pad / kUmBK;
-  const int npairs = c_pairs.npairs;
-  const int total = npairs * nkb;
-  const size_t slice_a = (size_t)rows_a_pad * k_pad, slice_b = (size_t)rows_b_pad * k_pad;
-  const uint32_t sbase = smem_addr(smem);
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                 "r"(2 * kUmN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    for (int s = 0; s < kUmStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_stage[s])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_run[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_run[1])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_done)));
-    s_abort = 0;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-
-  int lp = 0, lkb = 0;
-  auto load_next = [&](int stage) {
-    const unsigned short* As = Asl + (size_t)c_pairs.s[lp] * slice_a + (size_t)m0 * k_pad + lkb * kUmBK;
-    const unsigned short* Bs = Bsl + (size_t)c_pairs.t[lp] * slice_b + (size_t)n0 * k_pad + lkb * kUmBK;
-    unsigned char* dA = smem + (size_t)stage * kUmStageBytes;
-    unsigned char* dB = dA + kUmTileBytes;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {   // 128 rows x 8 chunks of 16 bytes per operand
-      const int c = tid + kUmThreads * q;
-      const int r = c >> 3, ch = c & 7;
-      cp_async16(dA + sw128_off(r, ch), As + (size_t)r * k_pad + ch * 8);
-      cp_async16(dB + sw128_off(r, ch), Bs + (size_t)r * k_pad + ch * 8);
-    }
-    if (++lkb == nkb) {
-      lkb = 0;
-      ++lp;
-    }
-  };
-
-  // FP64 sums: row (warp % 4) * 32 + lane, columns (warp / 4) * 64 + [0, 64)
-  double acc64[64];
-#pragma unroll
-  for (int j = 0; j < 64; ++j) acc64[j] = 0.0;
-  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-  const uint32_t col_base = (uint32_t)((warp >> 2) * 64);
-  auto flush = [&](int r, double sc) -> bool {
-    if (!mbar_wait(smem_addr(&bar_run[r & 1]), (uint32_t)((r >> 1) & 1))) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint32_t v[32];
-      tmem_ld32(tmem + lane_base + (uint32_t)((r & 1) * kUmN) + col_base + (uint32_t)(32 * h), v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc64[32 * h + j] = fma((double)__uint_as_float(v[j]), sc, acc64[32 * h + j]);
-    }
-    return true;
-  };
-
-#pragma unroll
-  for (int st = 0; st < kUmStages - 1; ++st) {
-    if (st < total) load_next(st);
-    cp_async_commit();
-  }
-  const uint32_t idesc =
-      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUmN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  int cp = 0, ckb = 0, terms = 0, run = 0;
-  bool run_first = true;
-  int pending = -1;
-  double pending_scale = 0.0;
-  bool ok = true;
-  for (int step = 0; step < total; ++step) {
-    const int stage = step % kUmStages;
-    cp_async_wait<kUmStages - 2>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (s_abort) {
-      ok = false;
-      break;
-    }
-    terms += kUmBK;
-    int np_ = cp, nkb_ = ckb + 1;
-    if (nkb_ == nkb) {
-      nkb_ = 0;
-      ++np_;
-    }
-    const bool run_ends = np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || terms + kUmBK > kOzBudget;
-    if (tid == 0) {
-      const uint32_t a0 = sbase + (uint32_t)stage * kUmStageBytes, b0 = a0 + kUmTileBytes;
-      const uint32_t dcol = tmem + (uint32_t)((run & 1) * kUmN);
-#pragma unroll
-      for (int kk = 0; kk < kUmBK / 16; ++kk) {
-        const uint64_t da = umma_desc_sw128(a0 + 32 * kk), db = umma_desc_sw128(b0 + 32 * kk);
-        const uint32_t accum = (run_first && kk == 0) ? 0u : 1u;
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-            "l"(da), "l"(db), "r"(idesc), "r"(accum));
-      }
-      umma_commit(smem_addr(&bar_stage[stage]));
-      if (run_ends) umma_commit(smem_addr(&bar_run[run & 1]));
-    }
-    run_first = false;
-    if (pending >= 0) {
-      if (!flush(pending, pending_scale)) {
-        s_abort = 1;
-        ok = false;
-      }
-      pending = -1;
-    }
-    if (run_ends) {
-      pending = run;
-      pending_scale = c_pairs.scale[cp];
-      ++run;
-      run_first = true;
-      terms = 0;
-    }
-    const int nxt = step + kUmStages - 1;
-    if (nxt < total) {
-      if (step >= 1) {
-        const int prev = step - 1;
-        if (!mbar_wait(smem_addr(&bar_stage[prev % kUmStages]), (uint32_t)((prev / kUmStages) & 1))) {
-          s_abort = 1;
-          ok = false;
-        }
-      }
-      load_next(nxt % kUmStages);
-    }
-    cp_async_commit();
-    cp = np_;
-    ckb = nkb_;
-  }
-  cp_async_wait<0>();
-  // all MMAs issued so far have finished before tensor memory is read or released
-  if (tid == 0) umma_commit(smem_addr(&bar_done));
-  if (!mbar_wait(smem_addr(&bar_done), 0)) ok = false;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok && pending >= 0 && !flush(pending, pending_scale)) ok = false;
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (s_abort) ok = false;
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kUmN));
-  if (!ok && lane == 0) atomicExch(err, 1);
-
-  // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
-  const int i = m0 + (warp & 3) * 32 + lane;
-  if (i >= M) return;
-  const int e_i = ea[i];
-#pragma unroll
-  for (int c = 0; c < 64; ++c) {
-    const int j = n0 + (int)col_base + c;
-    if (j >= N || (uplo == LOWER && i < j)) continue;
-    const int f_j = eb[j];
-    double v;
-    if (!ok || e_i == kExpNonfinite || f_j == kExpNonfinite) {
-      v = __longlong_as_double(0x7ff8000000000000ll);
-    } else if (e_i == kExpEmpty || f_j == kExpEmpty) {
-      v = 0.0;
-    } else {
-      v = alpha * ldexp(acc64[c], e_i + f_j);
-    }
-    double* cptr = C + i + (int64_t)j * ldc;
-    if (beta != 0.0) v = fma(beta, *cptr, v);
-    if (i == j) v += diag_add;
-    *cptr = v;
-  }
-}
-
-qdwhp_status launch_umma(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
-                         const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta, double* C,
-                         int64_t ldc, Uplo uplo, double diag_add, int* err) {
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(oz_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
-  });
-  QDWHP_CUDA_TRY(attr_err);
-  dim3 grid(np / kUmN, mp / 128);
-  oz_umma_kernel<<<grid, kUmThreads, kUmSmemBytes, st>>>((int)m, (int)n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C,
-                                                         ldc, (int)uplo, diag_add, err);
-  QDWHP_LAUNCH_CHECK();
-  return QDWHP_OK;
-}
-
 // ---- warp-specialised TMA + tcgen05 digit-product kernel ----
 //
-// Warp 8 (one thread) feeds a 4-stage ring with TMA (cp.async.bulk.tensor, 128-byte swizzle
+// Warp 8 (one thread) feeds a 3-stage ring (128-deep K per stage) with TMA (cp.async.bulk.tensor, 128-byte swizzle
 // written by the copy engine, each stage's "full" mbarrier counting the bytes) and issues the
 // MMAs of a stage as soon as it is full; each stage's MMAs commit to its "empty" mbarrier, which
-// releases the stage to the next copy.  A level run (digit pairs of one level, at most 66 K
-// blocks) accumulates into one of two 128-column TMEM buffers and commits to that buffer's
+// releases the stage to the next copy.  A level run (digit pairs of one level, at most 4224
+// digit products per accumulator) accumulates into one of two 128-column TMEM buffers and commits to that buffer's
 // "run done" mbarrier.  Warps 0-7 only flush: for each run they wait on "run done", read the
 // FP32 sums (tcgen05.ld), add them into their FP64 registers and arrive on the buffer's "free"
 // mbarrier, which the issuing thread waits on before reusing the buffer two runs later.  The
@@ -504,9 +273,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const uint32_t bar = smem_addr(&bar_full[stage]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kUmStageBytes)
                      : "memory");
-        const uint32_t dA = sbase + (uint32_t)stage * kUmStageBytes;
-        tma_load_3d(dA, &mapA, lkb * kUmBK, m0, (int)c_pairs.s[lp], bar);
-        tma_load_3d(dA + kUmTileBytes, &mapB, lkb * kUmBK, n0, (int)c_pairs.t[lp], bar);
+        const uint32_t dA = sbase + (uint32_t)stage * kUmStageBytes, dB = dA + kUmTileBytes;
+#pragma unroll
+        for (int at = 0; at < kUmBK / kUmAtomK; ++at) {
+          tma_load_3d(dA + at * kUmAtomBytes, &mapA, lkb * kUmBK + at * kUmAtomK, m0, (int)c_pairs.s[lp], bar);
+          tma_load_3d(dB + at * kUmAtomBytes, &mapB, lkb * kUmBK + at * kUmAtomK, n0, (int)c_pairs.t[lp], bar);
+        }
         if (++lkb == nkb) {
           lkb = 0;
           ++lp;
@@ -533,7 +305,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const uint32_t dcol = tmem + (uint32_t)((run & 1) * kUmN);
 #pragma unroll
         for (int kk = 0; kk < kUmBK / 16; ++kk) {
-          const uint64_t da = umma_desc_sw128(a0 + 32 * kk), db = umma_desc_sw128(b0 + 32 * kk);
+          // atom kk / 4, 32-byte K step kk % 4 inside it
+          const uint32_t off = (uint32_t)(kk / 4) * kUmAtomBytes + (uint32_t)(kk % 4) * 32;
+          const uint64_t da = umma_desc_sw128(a0 + off), db = umma_desc_sw128(b0 + off);
           const uint32_t accum = (run_first && kk == 0) ? 0u : 1u;
           asm volatile(
               "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -641,7 +415,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 }
 
 // Tensor maps of the digit slices: [slice][rows_pad][k_pad] bfloat16 seen as a 3-D tensor
-// (k innermost), box 64 x 128 x 1 with the 128-byte swizzle the MMA descriptors expect.
+// (k innermost), box 64 x 128 x 1 (one swizzle atom) with the 128-byte swizzle the MMA
+// descriptors expect.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -664,7 +439,7 @@ qdwhp_status slice_map(CUtensorMap* map, const unsigned short* base, int rows_pa
   }
   const cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)kOzS};
   const cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * k_pad * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)kUmBK, 128u, 1u};
+  const cuuint32_t box[3] = {(cuuint32_t)kUmAtomK, 128u, 1u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
