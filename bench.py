@@ -143,6 +143,27 @@ def dist_setup(args):
     return world, rank, local
 
 
+def replica_seed(rank):
+    """Each rank solves its own replica of the workload (independent problems, no collective)."""
+    return SEED + rank
+
+
+def max_over_ranks(value, world, device):
+    """The slowest rank's time (the contract's max-over-ranks), a no-op for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, steps, total_ms):
+    """Whole-job throughput: every rank's solves over the slowest rank's time."""
+    return world * steps / (total_ms / 1e3)
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -182,7 +203,7 @@ def run_ours(args):
     build.build()
     from paper_2104_14186_gb300 import qdwhp as Q
 
-    p = make_problem(SEED + rank)
+    p = make_problem(replica_seed(rank))
     A_host = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()
     A = A_host.to(dev)
     k = p.k
@@ -222,13 +243,8 @@ def run_ours(args):
     launches = Q.launch_count() - launches0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = aggregate_rate(world, args.steps, total_ms)
 
     # ---- end to end through the host-buffer API (H2D of A and D2H of sigma, U, V in the region) ----
     e2e_ms = []
@@ -239,12 +255,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         rh = Q.svd(A_host, k=k, ws=ws, device=dev, **sopts)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), world, dev)
     h2d = A_host.numel() * 8
     d2h = (rh.sigma.numel() + rh.U.numel() + rh.V.numel()) * 8
 
@@ -281,7 +292,7 @@ def run_ours(args):
             "gemm_share_of_step": prof["gemm_ms"] / total_ms if total_ms > 0 else None,
             "gemm_launches": prof["gemm_launches"],
         },
-        "e2e": {"value": world * args.steps / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": aggregate_rate(world, args.steps, e2e_total), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
