@@ -295,9 +295,10 @@ qdwhp_status build_outer_T(cudaStream_t st, const QRFactors& f, int64_t jo, int 
 
 qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f, double* scratch) {
   if (m < n || n < 0) return QDWHP_ERR_ARG;
-  // Householder products stay native FP64 in every precision mode: V is unit lower
+  // Householder updates C -= V W2 stay native FP64 in every precision mode: V is unit lower
   // trapezoidal and the coefficient columns span many magnitudes, where the emulated
-  // product's normwise (row/column-scaled) error is far above FP64's componentwise one.
+  // product's normwise (row/column-scaled) error is far above FP64's componentwise one.  Only
+  // the reduction W = V^T C of the outer blocks follows the caller's precision.
   EmulationScope native_products(nullptr, 0);
   f.m = m;
   f.n = n;
@@ -349,8 +350,12 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
       const double* Vo = f.Vall + jo + jo * m;
       const double* To = f.To + (size_t)(jo / NBO) * NBO * NBO;
       double* C = A + jo + (jo + jbo) * lda;
-      QDWHP_TRY(gemm(st, true, false, jbo, nc, Ro, 1.0, Vo, m, C, lda, 0.0, W, jbo, FULL, 0.0, splitk,
-                     splitk_elems));
+      {
+        // the reduction W = V^T C (rows of V^T: whole reflectors) may use the caller's emulation
+        EmulationScope reduction(native_products.prev_ws, native_products.prev_bytes);
+        QDWHP_TRY(gemm(st, true, false, jbo, nc, Ro, 1.0, Vo, m, C, lda, 0.0, W, jbo, FULL, 0.0, splitk,
+                       splitk_elems));
+      }
       QDWHP_TRY(gemm(st, true, false, jbo, nc, jbo, 1.0, To, NBO, W, jbo, 0.0, W2, jbo));
       QDWHP_TRY(gemm(st, false, false, Ro, nc, jbo, -1.0, Vo, m, W2, jbo, 1.0, C, lda));
     }
@@ -378,8 +383,11 @@ qdwhp_status apply_blocks(cudaStream_t st, const QRFactors& f, int64_t last_bloc
     const double* Vo = f.Vall + jo + jo * m;
     const double* To = f.To + (size_t)po * NBO * NBO;
     double* Cj = C + jo;
-    QDWHP_TRY(gemm(st, true, false, jbo, ncols, Ro, 1.0, Vo, m, Cj, ldc, 0.0, W, jbo, FULL, 0.0, splitk,
-                   splitk_elems));
+    {
+      EmulationScope reduction(native_products.prev_ws, native_products.prev_bytes);   // as in geqrf
+      QDWHP_TRY(gemm(st, true, false, jbo, ncols, Ro, 1.0, Vo, m, Cj, ldc, 0.0, W, jbo, FULL, 0.0, splitk,
+                     splitk_elems));
+    }
     QDWHP_TRY(gemm(st, false, false, jbo, ncols, jbo, 1.0, To, NBO, W, jbo, 0.0, W2, jbo));
     QDWHP_TRY(gemm(st, false, false, Ro, ncols, jbo, -1.0, Vo, m, W2, jbo, 1.0, Cj, ldc));
   }
