@@ -259,7 +259,14 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
         lo_raw, hi_raw = -(th_max + r_max), -(th_min - r_min)
     else:
         lo_raw, hi_raw = th_min - r_min, th_max + r_max
-    spread = max(hi_raw - lo_raw, 1e-300)
+    # Degenerate case: the spectrum is one point to rounding (n = 1, a multiple of the
+    # identity, the zero matrix).  mu would be 0 (Algorithm 1 scales by 1/|mu|), and every
+    # vector is an eigenvector: return the first k unit vectors and their Rayleigh quotients.
+    if hi_raw - lo_raw <= 16 * 2.0 ** -53 * max(abs(lo_raw), abs(hi_raw)):
+        V = np.eye(n)[:, :k]
+        lam = np.diag(A)[:k].astype(np.float64)
+        return EigResult(lam, V, 0, float(th_max), float(th_min), 0, {"degenerate": True})
+    spread = hi_raw - lo_raw
     lam_lo = lo_raw - 0.01 * spread
     lam_hi = hi_raw + 0.01 * spread
 
@@ -331,7 +338,8 @@ def qdwhp_svd(A: np.ndarray, opts: SvdOptions) -> SvdResult:
     _, _, th_max, r_max = lanczos_extremes_normal(A, opts.lanczos_steps, opts.seed)
     alpha = math.sqrt(max(th_max + r_max, 0.0))
     if alpha == 0.0:
-        raise RuntimeError("zero matrix")
+        # the zero matrix: every singular value is 0 and any orthonormal U, V serve
+        return SvdResult(np.zeros(k), np.eye(m)[:, :k], np.eye(n)[:, :k], 0, 0.0, 0.0, 0, {"degenerate": True})
     # Relative threshold s from the requested count.
     sig_hat = threshold_from_count_svd(A, k, opts.block_extra, opts.power_steps, opts.seed)
     s = max(sig_hat / alpha * (1.0 - 1e-10), opts.s_min)

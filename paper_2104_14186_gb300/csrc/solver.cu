@@ -37,6 +37,12 @@ void set_error_message(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", m
 
 namespace {
 
+// lambda[i] = A(i, i), i < k: the Rayleigh quotients of the first k unit vectors.
+__global__ void diag_copy_kernel(int k, const double* A, int64_t lda, double* lambda) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) lambda[i] = A[i + (int64_t)i * lda];
+}
+
 __global__ void index_scan_kernel(int n, const double* diagR, double tol, int* ind) {
   __shared__ int best;
   if (threadIdx.x == 0) best = n;
@@ -258,7 +264,19 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     lo_raw = th_min - r_min;
     hi_raw = th_max + r_max;
   }
-  const double spread = std::max(hi_raw - lo_raw, 1e-300);
+  // Degenerate case: the spectrum is one point to rounding (n = 1, a multiple of the identity,
+  // the zero matrix).  mu would be 0 (Algorithm 1 scales by 1/|mu|) and every vector is an
+  // eigenvector: the first k unit vectors and their Rayleigh quotients.
+  if (hi_raw - lo_raw <= 16 * 1.1102230246251565e-16 * std::max(std::fabs(lo_raw), std::fabs(hi_raw))) {
+    QDWHP_TRY(set_matrix(st, n, k, 0.0, 1.0, V, ldv));
+    diag_copy_kernel<<<ceil_div(k, 256), 256, 0, st>>>((int)k, A, lda, lambda);
+    QDWHP_LAUNCH_CHECK();
+    inf.ms_total = timer.stop();
+    inf.k = k;
+    if (info) *info = inf;
+    return QDWHP_OK;
+  }
+  const double spread = hi_raw - lo_raw;
   const double lam_lo = lo_raw - 0.01 * spread, lam_hi = hi_raw + 0.01 * spread;
 
   // Threshold for the requested count: block Krylov space of P = lam_hi I - A' from k + p
@@ -425,7 +443,17 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   QDWHP_TRY(sync_read(st, &hs.lst, w.c.lst, sizeof(LanczosState)));
   if (hs.nonfinite || hs.lst.nonfinite) return QDWHP_ERR_NONFINITE;
   const double alpha = std::sqrt(std::max(hs.lst.out[2] + hs.lst.out[3], 0.0));
-  if (!(alpha > 0.0)) return QDWHP_ERR_ARG;
+  if (!std::isfinite(alpha)) return QDWHP_ERR_NONFINITE;
+  if (!(alpha > 0.0)) {
+    // the zero matrix: every singular value is 0 and any orthonormal U, V serve
+    QDWHP_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * k, st));
+    QDWHP_TRY(set_matrix(st, m, k, 0.0, 1.0, U, ldu));
+    QDWHP_TRY(set_matrix(st, n, k, 0.0, 1.0, V, ldv));
+    inf.ms_total = timer.stop();
+    inf.k = k;
+    if (info) *info = inf;
+    return QDWHP_OK;
+  }
 
   // Relative threshold s from the k-th Ritz value of A^T A on span((A^T A)^(q+1) Om), Om of
   // k + p SplitMix64 columns (subspace iteration, each block orthonormalised before the next

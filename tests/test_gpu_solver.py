@@ -144,3 +144,34 @@ def test_svd_full_size_workload(Q):
     ref = O.qdwhp_svd(q.A, O.SvdOptions(k=q.k))
     check_svd(q, r, ref)
     assert r.info["it_chol"] == 3 and r.info["it_qr"] == 0
+
+
+def test_degenerate_inputs(Q):
+    """One-point spectra (n = 1, c I, the zero matrix) and the zero matrix's SVD, through the
+    C ABI, as the oracle defines them; k above the numerical rank reports QDWHP_ERR_COUNT."""
+    r = Q.eig(dev(np.array([[3.0]])), k=1)
+    assert r.lam.cpu().tolist() == [3.0] and r.V.cpu().tolist() == [[1.0]]
+    for c in (2.5, 0.0, -1e-3):
+        r = Q.eig(dev(c * np.eye(300)), k=30, side="smallest")
+        assert torch.all(r.lam == c) and torch.equal(r.V.cpu(), torch.eye(300, dtype=torch.float64)[:, :30])
+    s = Q.svd(dev(np.zeros((130, 100))), k=7)
+    assert torch.all(s.sigma == 0.0)
+    assert torch.equal(s.U.cpu(), torch.eye(130, dtype=torch.float64)[:, :7])
+    assert torch.equal(s.V.cpu(), torch.eye(100, dtype=torch.float64)[:, :7])
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((400, 100)) @ rng.standard_normal((100, 300))
+    with pytest.raises(Q.QdwhpError) as e:
+        Q.svd(dev(B), k=150)
+    assert e.value.status == -9
+
+
+@pytest.mark.parametrize("n,k,side", [(257, 257, "largest"), (200, 1, "smallest"), (2, 1, "largest")])
+def test_eig_count_extremes(Q, n, k, side):
+    """k = n (all eigenpairs through the partial solver), k = 1, and n = 2."""
+    rng = np.random.default_rng(n + k)
+    lam = rng.uniform(-1, 1, n)
+    A = I.symmetric_with_spectrum(lam, rng)
+    r = Q.eig(dev(A), k=k, side=side)
+    true = np.sort(lam)[::-1][:k] if side == "largest" else np.sort(lam)[:k]
+    m = O.eig_metrics(A, r.lam.cpu().numpy(), r.V.cpu().numpy(), true)
+    assert m["lam_err"] <= LAM_TOL and m["orth"] <= ORTH_TOL * n and m["resid"] <= RES_TOL, m

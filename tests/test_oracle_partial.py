@@ -173,3 +173,24 @@ def test_index_rule():
     R = np.diag([3.0, 1.0, 0.5, 0.009, 0.5, 1e-16])
     assert O.index_from_diag(R, float(G["index_tol"])) == 3
     assert O.index_from_diag(np.eye(4), 0.01) == 4
+
+
+def test_degenerate_spectra():
+    """Algorithm 1 divides by |mu|, which is 0 when the spectrum is one point (n = 1, a
+    multiple of the identity, the zero matrix): then every vector is an eigenvector and the
+    solver returns unit vectors with their Rayleigh quotients.  The zero matrix's singular
+    values are all 0 (Algorithm 2's alpha = 0)."""
+    r = O.qdwhp_eig(np.array([[3.0]]), O.EigOptions(k=1))
+    assert r.lam.tolist() == [3.0] and r.V.tolist() == [[1.0]]
+    for c in (2.5, 0.0, -1e-3):
+        r = O.qdwhp_eig(c * np.eye(20), O.EigOptions(k=5, side="smallest"))
+        assert np.all(r.lam == c) and np.array_equal(r.V, np.eye(20)[:, :5])
+    s = O.qdwhp_svd(np.zeros((10, 8)), O.SvdOptions(k=3))
+    assert np.all(s.sigma == 0.0)
+    assert np.linalg.norm(s.U.T @ s.U - np.eye(3)) == 0.0 and np.linalg.norm(s.V.T @ s.V - np.eye(3)) == 0.0
+    # k above the numerical rank: zero singular values are below every relative threshold
+    # (Algorithm 2 keeps sigma >= s alpha), so the solver reports the shortfall
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((40, 10)) @ rng.standard_normal((10, 30))
+    with pytest.raises(RuntimeError):
+        O.qdwhp_svd(B, O.SvdOptions(k=15))
