@@ -287,7 +287,9 @@ def run_ours(args):
         "roofline": {
             "kernel": "dgemm_kernel (FP64 DMMA mma.sync m8n8k4 tiles, all GEMM/SYRK/TRSM/QR-update launches)",
             "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            # DRAM bytes of one 4096^3 launch from the ncu capture in profiles/ (the kernel is unchanged)
+            "traffic": DGEMM_4096_TRAFFIC_BYTES, "traffic_launch": "dgemm_kernel<32,32,0,0> 4096^3",
             "peak_source": "measured bf16 dense burst x nominal FP64/BF16 ratio (1.25/2250), of measured",
             "gemm_share_of_step": prof["gemm_ms"] / total_ms if total_ms > 0 else None,
             "gemm_launches": prof["gemm_launches"],
@@ -320,6 +322,7 @@ def precision_code(Q, name):
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "emulated": "f64 (bf16 Ozaki digit products + f64 sums)",
           "mixed-emulated": "f32 + f64 (bf16 Ozaki digit products + f64 sums)"}
 OZ_PAIRS = 60          # digit products per emulated FP64 product
+DGEMM_4096_TRAFFIC_BYTES = 1.347e9   # dram read + write of one 4096^3 dgemm_kernel launch (ncu)
 
 
 def emulated_roofline(Q, total_ms, bf16_peak):
