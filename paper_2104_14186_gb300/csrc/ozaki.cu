@@ -15,15 +15,17 @@
 // FP32 accumulators of the tensor cores (bf16 x bf16 -> f32).  Each such product is scaled
 // by its power of two and added into FP64 accumulators.  The pairs with s + t <= 12 are
 // kept (60 of the 81).  The dropped pairs are a bias, not noise, where the digit products
-// share a sign (a sum of squares): at most 6 K 63^2 2^-78 2^(e_i + f_j), below FP64 rounding
-// for the K of this library (at s + t <= 11 it reached 1e-13 relative at K = 16384).  Pairs
+// share a sign (a sum of squares): at most 6 K 63^2 2^-78 2^(e_i + f_j), below the K u
+// 2^(e_i + f_j) rounding bound of an FP64 dot product of length K (one level fewer would put
+// 64 times more bias on Gram diagonals).  Pairs
 // of one level s + t share the scale 2^(-6 (s + t)), so they share an FP32 accumulator as
 // long as it holds at most 4224 digit products (exact); it is flushed into FP64 when the
 // level changes or the budget would be exceeded.
 //
 // Layout: digit slices are stored as [slice][row][k_pad] bfloat16 with K contiguous (op(A)
-// rows, op(B) columns), zero-padded to the 128 x 64 tile; the product kernel (tcgen05, below)
-// streams a (slice pair, K block) sequence through a 4-stage ring in shared memory.
+// rows, op(B) columns), zero-padded to 128-row, 128-deep blocks; the product kernel (TMA +
+// tcgen05, below) streams a (slice pair, K block) sequence through a 3-stage ring in shared
+// memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
