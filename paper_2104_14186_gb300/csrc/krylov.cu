@@ -210,10 +210,12 @@ __global__ void tridiag_extremes_kernel(LanczosState* stt) {
   if (lane == 0) {
     const double bm = fabs(stt->beta[m - 1]);
     const double shift = fmax(scale, 1e-300) * 1e-13;
+    // beta_{m-1} = 0 (an invariant subspace, e.g. a one-point spectrum): the Ritz values are
+    // exact, and the eigenvector estimate is not needed (for T = 0 it would divide by ~0)
     stt->out[0] = tmin;
-    stt->out[1] = bm * last_component(al, be, m, tmin - shift);
+    stt->out[1] = bm > 0.0 ? bm * last_component(al, be, m, tmin - shift) : 0.0;
     stt->out[2] = tmax;
-    stt->out[3] = bm * last_component(al, be, m, tmax + shift);
+    stt->out[3] = bm > 0.0 ? bm * last_component(al, be, m, tmax + shift) : 0.0;
   }
 }
 
