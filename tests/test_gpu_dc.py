@@ -106,3 +106,14 @@ def test_partial_eig_takes_divide_and_conquer(Q, frac, side):
     assert m["lam_err"] <= LAM_TOL, m
     assert m["orth"] <= ORTH_TOL * 2400, m
     assert m["resid"] <= RES_TOL, m
+
+
+@pytest.mark.parametrize("c", [0.0, 1.5])
+def test_syev_one_point_spectrum(Q, c):
+    """c I (and the zero matrix) through the divide-and-conquer solver: every eigenvalue c,
+    orthonormal vectors."""
+    n = 700
+    lam, V, info = Q.syev(dev(c * np.eye(n)))
+    lam, V = lam.cpu().numpy(), V.cpu().numpy()
+    assert np.max(np.abs(lam - c)) <= 1e-14 * max(1.0, abs(c))
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= ORTH_TOL * n
