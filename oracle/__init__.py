@@ -28,6 +28,10 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                          spectra, brute-force Jacobi
   full.split / qdwh_eig  pinned: rank(C) = #eigenvalues above sigma, C = V+ V+^T
                          on known spectra; all eigenpairs against constructed spectra
+  full.gesvd             the definition (all singular triplets); pinned: constructed
+                         singular values, residuals, the eigenvalues of A^T A
+  full.qdwh_svd          pinned: constructed singular values (to 1e-12 relative decades),
+                         m < n, rank-deficient and zero matrices, residual invariants
 """
 
 from .rng import splitmix64, uniform_pm1  # noqa: F401

@@ -1,4 +1,4 @@
-"""Full symmetric eigendecomposition: QDWH-EIG (Section 3.2), plain FP64.
+"""Full spectra: QDWH-EIG and QDWH-SVD (Section 3.2), plain FP64.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -13,6 +13,19 @@ the mean eigenvalue trace(A) / n, the polar decomposition starts from ell_0 = 1e
 (QR-based steps while c_k > 100), rank(C) = round(trace(C)), the bases come from
 Householder QR with column pivoting of C, and problems of order <= `leaf` go to the
 dense eigensolver.
+
+QDWH-SVD reaches, up to rounding, every singular triplet of A; `gesvd` is that
+definition (the LAPACK SVD as its one step).  `qdwh_svd` follows Section 3.2: the
+polar decomposition A = U_p H by QDWH, the symmetric eigendecomposition H = V Sigma V^T
+(here by `qdwh_eig`, the same spectral divide and conquer), and U = U_p V.  Readings
+(the paper does not fix them): A with m < n is solved as A^T with U and V swapped;
+alpha = ||A||_2; the polar decomposition starts from ell_0 = 1e-15, so its guarantee
+covers sigma_min / sigma_max >= 1e-15; an eigenvalue lambda of H taken negative by
+rounding gives sigma = |lambda| with the matching column of U negated (A v = lambda U_p v);
+and when the smallest sigma is at most 1e-14 alpha (numerically rank-deficient A, whose
+polar factor QDWH does not settle on the null directions), U is replaced by the
+orthonormal factor of its Householder QR with the signs of diag(R), which leaves the
+other columns unchanged to rounding and completes the null ones orthonormally.
 """
 
 from __future__ import annotations
@@ -23,6 +36,8 @@ import scipy.linalg as sla
 from .qdwh import qdwh_polar
 
 ELL0_SPLIT = 1e-15
+ELL0_SVD = 1e-15
+ORTH_FIX_SVD = 1e-14
 
 
 def syev(A: np.ndarray):
@@ -61,3 +76,35 @@ def qdwh_eig(A: np.ndarray, lo: float, hi: float, leaf: int = 64):
     l1, W1 = qdwh_eig(V1.T @ A @ V1, sigma, hi, leaf)
     l2, W2 = qdwh_eig(V2.T @ A @ V2, lo, sigma, leaf)
     return np.concatenate([l1, l2]), np.hstack([V1 @ W1, V2 @ W2])
+
+
+def gesvd(A: np.ndarray):
+    """All singular triplets of A, thin (p = min(m, n)): (sigma descending, U m x p, V n x p)."""
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    return s, U, Vt.T
+
+
+def qdwh_svd(A: np.ndarray, leaf: int = 64):
+    """QDWH-SVD (Section 3.2): A = U_p H, H = V Sigma V^T, U = U_p V.  Returns
+    (sigma descending, U, V, info) with info["orthonormalized"] set when U was completed
+    by its QR (numerically rank-deficient A)."""
+    m, n = A.shape
+    if m < n:
+        s, U, V, info = qdwh_svd(A.T, leaf)
+        return s, V, U, info
+    alpha = float(np.linalg.norm(A, 2))
+    if alpha == 0.0:
+        return np.zeros(n), np.eye(m, n), np.eye(n), {"orthonormalized": False, "zero": True}
+    Up, H, sched = qdwh_polar(A, alpha, ELL0_SVD)
+    lam, W = qdwh_eig(H, -0.01 * alpha, 1.01 * alpha, leaf)
+    order = np.argsort(-np.abs(lam), kind="stable")
+    lam, W = lam[order], W[:, order]
+    sigma = np.abs(lam)
+    sgn = np.where(lam < 0.0, -1.0, 1.0)
+    U = (Up @ W) * sgn[None, :]
+    fixed = bool(sigma[-1] <= ORTH_FIX_SVD * alpha)
+    if fixed:
+        Q, R = np.linalg.qr(U)
+        d = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+        U = Q * d[None, :]
+    return sigma, U, W, {"orthonormalized": fixed, "zero": False, "polar_steps": len(sched)}
