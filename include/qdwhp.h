@@ -164,6 +164,46 @@ QDWHP_API qdwhp_status qdwhp_syev_f64(const double* A, int64_t n, int64_t lda, d
                                       int64_t ldv, void* workspace, size_t ws_bytes, qdwhp_syev_info* info,
                                       void* stream);
 
+/*
+ * Full (thin) SVD by QDWH-SVD (Section 3.2): the polar decomposition A = U_p H by QDWH
+ * (eqs. practical-polar-qr and practical-polar-chol from ell_0 = 1e-15 on A / alpha, alpha
+ * the Lanczos estimate of ||A||_2), the symmetric eigendecomposition H = V Sigma V^T by the
+ * divide-and-conquer solver of qdwhp_syev_f64, and U = U_p V.  m < n is solved on A^T with
+ * U and V swapped (Section 4.2).  With p = min(m, n):
+ *   A: m x n, lda >= m, never modified.
+ *   precision: QDWHP_FP64, or QDWHP_FP64_EMULATED (products with m, n >= 128 and k >= 256
+ *      emulated on the BF16 tensor cores, as in qdwhp_gemm_f64_emulated); others are
+ *      QDWHP_ERR_ARG.
+ *   sigma: p doubles, descending.  U: m x p (ldu >= m), V: n x p (ldv >= n), orthonormal
+ *      columns (signs unspecified; a sign of U follows its column of V).
+ *   The guarantee covers sigma_min / sigma_max >= 1e-15 (the polar factor's ell_0).  If the
+ *   smallest computed sigma is at most 1e-14 alpha (numerically rank-deficient A), U is
+ *   replaced by the orthonormal factor of its Householder QR, signed by diag(R): the other
+ *   columns change only by rounding, the null ones become an orthonormal completion.
+ *   workspace/ws_bytes: at least qdwhp_gesvd_workspace_bytes(m, n, precision).
+ *   Errors: QDWHP_ERR_ARG, QDWHP_ERR_NOMEM, QDWHP_ERR_NONFINITE (A holds NaN/Inf),
+ *   QDWHP_ERR_NOT_CONVERGED, QDWHP_ERR_BREAKDOWN as for qdwhp_syev_f64.  The zero matrix
+ *   returns sigma = 0, U and V the leading unit vectors.  Synchronises `stream` (bounds,
+ *   the split points of the eigensolver, the smallest sigma).
+ */
+typedef struct {
+  int32_t it_qr;          /* QR-based polar steps (eq. practical-polar-qr) */
+  int32_t it_chol;        /* Cholesky-based polar steps (eq. practical-polar-chol) */
+  int32_t nodes;          /* spectral splits of the eigensolver on H */
+  int32_t leaves;
+  int32_t depth;
+  int32_t jacobi_sweeps;
+  int32_t orthonormalized; /* 1 if U was completed by its QR (numerically rank-deficient A) */
+  int32_t reserved;
+  double alpha;           /* the ||A||_2 estimate A was scaled by */
+  double max_offblock;    /* as in qdwhp_syev_info */
+  float ms_total;         /* device time (CUDA events) */
+} qdwhp_gesvd_info;
+QDWHP_API size_t qdwhp_gesvd_workspace_bytes(int64_t m, int64_t n, int32_t precision);
+QDWHP_API qdwhp_status qdwhp_gesvd_f64(const double* A, int64_t m, int64_t n, int64_t lda, int32_t precision,
+                                       double* sigma, double* U, int64_t ldu, double* V, int64_t ldv,
+                                       void* workspace, size_t ws_bytes, qdwhp_gesvd_info* info, void* stream);
+
 /* ---- Request queue (serving) and batched solves; not part of the paper's method ---- */
 
 /*

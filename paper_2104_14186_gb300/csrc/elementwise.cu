@@ -69,6 +69,21 @@ __global__ void copy_upper_kernel(int N, const double* A, int64_t lda, double* R
   }
 }
 
+// B (cols x rows) = A^T (rows x cols), through 32 x 33 shared tiles.
+__global__ void transpose_kernel(int rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = bx + threadIdx.x, j = by + k;
+    if (i < rows && j < cols) tile[k][threadIdx.x] = A[i + (int64_t)j * lda];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int i = by + threadIdx.x, j = bx + k;   // B(i, j) = A(j, i)
+    if (i < cols && j < rows) B[i + (int64_t)j * ldb] = tile[threadIdx.x][k];
+  }
+}
+
 // G = R^T for the upper triangle R of A (the strictly lower part of G is R's upper part).
 __global__ void copy_upper_t_kernel(int N, const double* A, int64_t lda, double* G, int64_t ldg) {
   const size_t total = (size_t)N * N;
@@ -207,6 +222,15 @@ qdwhp_status convert(cudaStream_t st, int64_t m, int64_t n, const float* X, int6
 qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* R, int64_t ldr) {
   if (n <= 0) return QDWHP_OK;
   copy_upper_kernel<<<grid_for((size_t)n * n), 256, 0, st>>>((int)n, A, lda, R, ldr);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status transpose(cudaStream_t st, int64_t rows, int64_t cols, const double* A, int64_t lda, double* B,
+                       int64_t ldb) {
+  if (rows <= 0 || cols <= 0) return QDWHP_OK;
+  dim3 grid(ceil_div(rows, 32), ceil_div(cols, 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>((int)rows, (int)cols, A, lda, B, ldb);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

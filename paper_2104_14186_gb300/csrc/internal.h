@@ -67,6 +67,9 @@ qdwhp_status copy_upper(cudaStream_t st, int64_t n, const double* A, int64_t lda
 qdwhp_status copy_upper_t(cudaStream_t st, int64_t n, const double* A, int64_t lda, double* G, int64_t ldg);
 // H := (H + H^T) / 2 (n x n).
 qdwhp_status symmetrize_avg(cudaStream_t st, int64_t n, double* H, int64_t ldh);
+// B (cols x rows, ld ldb) = A^T for A rows x cols (ld lda).
+qdwhp_status transpose(cudaStream_t st, int64_t rows, int64_t cols, const double* A, int64_t lda, double* B,
+                       int64_t ldb);
 // Fills the lower triangle's mirror: Y(i, j) = Y(j, i) for i < j (n x n).
 qdwhp_status symmetrize_from_lower(cudaStream_t st, int64_t n, double* Y, int64_t ldy);
 // Sum of kDiffParts partials -> out (device scalar); also checks finiteness of the sum.

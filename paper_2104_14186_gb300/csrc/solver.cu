@@ -53,21 +53,6 @@ __global__ void index_scan_kernel(int n, const double* diagR, double tol, int* i
   if (threadIdx.x == 0) *ind = best;
 }
 
-__global__ void transpose_kernel(int rows, int cols, const double* A, int64_t lda, double* B, int64_t ldb) {
-  // B (cols x rows) = A^T
-  __shared__ double tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int i = bx + threadIdx.x, j = by + k;
-    if (i < rows && j < cols) tile[k][threadIdx.x] = A[i + (int64_t)j * lda];
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int i = by + threadIdx.x, j = bx + k;   // B(i, j) = A(j, i)
-    if (i < cols && j < rows) B[i + (int64_t)j * ldb] = tile[threadIdx.x][k];
-  }
-}
-
 // Block Krylov bases of the count-to-threshold step wider than min(n / 8, this) keep only the
 // last block: a wider basis would make its Rayleigh-Ritz problem cost as much as the solve.
 constexpr int64_t kKrylovMaxCols = 2048;
@@ -689,9 +674,7 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
   EmulationScope emu_scope(w.emu, w.emu_bytes);
   if (m >= n) return svd_impl(A, m, n, lda, kk, *opts, sigma, U, ldu, V, ldv, w, info, st);
   // m < n: solve on A^T (n x m) and swap the roles of U and V (Section 4.2).
-  dim3 grid(ceil_div(m, 32), ceil_div(n, 32));
-  transpose_kernel<<<grid, dim3(32, 8), 0, st>>>((int)m, (int)n, A, lda, w.At, n);
-  QDWHP_LAUNCH_CHECK();
+  QDWHP_TRY(transpose(st, m, n, A, lda, w.At, n));
   return svd_impl(w.At, n, m, n, kk, *opts, sigma, V, ldv, U, ldu, w, info, st);
 }
 

@@ -69,6 +69,17 @@ class SyevInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class GesvdInfo(C.Structure):
+    _fields_ = [
+        ("it_qr", C.c_int32), ("it_chol", C.c_int32), ("nodes", C.c_int32), ("leaves", C.c_int32),
+        ("depth", C.c_int32), ("jacobi_sweeps", C.c_int32), ("orthonormalized", C.c_int32),
+        ("reserved", C.c_int32), ("alpha", C.c_double), ("max_offblock", C.c_double), ("ms_total", C.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class QdwhpError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = f"{where}: {STATUS_NAMES.get(status, status)}"
@@ -95,6 +106,9 @@ SIGNATURES = {
                             C.POINTER(Info), P]),
     "qdwhp_syev_workspace_bytes": (C.c_size_t, [I64]),
     "qdwhp_syev_f64": (C.c_int, [P, I64, I64, P, P, I64, P, C.c_size_t, C.POINTER(SyevInfo), P]),
+    "qdwhp_gesvd_workspace_bytes": (C.c_size_t, [I64, I64, C.c_int32]),
+    "qdwhp_gesvd_f64": (C.c_int, [P, I64, I64, I64, C.c_int32, P, P, I64, P, I64, P, C.c_size_t,
+                                  C.POINTER(GesvdInfo), P]),
     "qdwhp_gemm_f64_emulated_workspace_bytes": (C.c_size_t, [I64, I64, I64]),
     "qdwhp_gemm_f64_emulated": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P,
                                           C.c_size_t, P]),
@@ -242,6 +256,28 @@ def syev(A: torch.Tensor, ws: torch.Tensor | None = None, stream=None):
                               _stream(stream))
     _check(st, "qdwhp_syev_f64")
     return lam, Vt.t(), info.as_dict()
+
+
+def gesvd(A: torch.Tensor, precision: int = 0, ws: torch.Tensor | None = None, stream=None):
+    """qdwhp_gesvd_f64: all singular triplets (thin, p = min(m, n)) of the CUDA float64
+    matrix A by QDWH-SVD.  precision: FP64 or FP64_EMULATED.  Returns (sigma descending,
+    U m x p, V n x p, info dict)."""
+    m, n = A.shape
+    p = min(m, n)
+    Ac = _colmajor(A)
+    sig = torch.empty(p, dtype=torch.float64, device=A.device)
+    Ut = torch.empty(p, m, dtype=torch.float64, device=A.device)
+    Vt = torch.empty(p, n, dtype=torch.float64, device=A.device)
+    need = lib().qdwhp_gesvd_workspace_bytes(m, n, precision)
+    if need == 0:
+        raise QdwhpError(-1, "qdwhp_gesvd_workspace_bytes")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    info = GesvdInfo()
+    st = lib().qdwhp_gesvd_f64(_ptr(Ac), m, n, m, precision, _ptr(sig), _ptr(Ut), m, _ptr(Vt), n, _ptr(ws),
+                               ws.numel(), C.byref(info), _stream(stream))
+    _check(st, "qdwhp_gesvd_f64")
+    return sig, Ut.t(), Vt.t(), info.as_dict()
 
 
 def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws: torch.Tensor | None = None,

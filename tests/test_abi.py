@@ -103,3 +103,15 @@ def test_queue_argument_errors(lib):
     assert lib.qdwhp_queue_create(100, 2, None, C.byref(h)) == -1           # budget too small
     assert lib.qdwhp_poll(None, 1, None) == -1
     assert lib.qdwhp_queue_destroy(None) == -1
+
+
+def test_gesvd_argument_checks(lib):
+    """Sizes, pointers and precision are checked before anything is launched."""
+    assert lib.qdwhp_gesvd_workspace_bytes(300, 200, 0) > 0
+    assert lib.qdwhp_gesvd_workspace_bytes(200, 300, 2) > lib.qdwhp_gesvd_workspace_bytes(200, 300, 0)
+    assert lib.qdwhp_gesvd_workspace_bytes(300, 200, 1) == 0      # mixed is not offered
+    assert lib.qdwhp_gesvd_workspace_bytes(0, 200, 0) == 0
+    from paper_2104_14186_gb300 import qdwhp as Q
+    info = Q.GesvdInfo()
+    assert lib.qdwhp_gesvd_f64(None, 3, 3, 3, 0, None, None, 3, None, 3, None, 0, C.byref(info), None) == -1
+    assert C.sizeof(Q.GesvdInfo) == 56
