@@ -30,6 +30,9 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                          on known spectra; all eigenpairs against constructed spectra
   full.gesvd             the definition (all singular triplets); pinned: constructed
                          singular values, residuals, the eigenvalues of A^T A
+  zolo.*                 pinned: r = 1 equals the QDWH weights, Chebyshev alternation
+                         (2r + 2 points), composition law, spectral-map identity of both
+                         term forms, polar factor from the SVD, iteration counts
   full.qdwh_svd          pinned: constructed singular values (to 1e-12 relative decades),
                          m < n, rank-deficient and zero matrices, residual invariants
 """
@@ -44,4 +47,5 @@ from .partial import (  # noqa: F401
 from .jacobi import jacobi_eig  # noqa: F401
 from .full import syev  # noqa: F401
 from . import full  # noqa: F401
+from . import zolo  # noqa: F401
 from .metrics import eig_metrics, svd_metrics  # noqa: F401

@@ -39,6 +39,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .qdwh import dwh_schedule, qdwh_chol_step, qdwh_qr_step
+from .zolo import zolo_schedule, zolo_step
 from .rng import uniform_pm1
 
 # Stream ids of the two random draws of the method (XORed into the user seed).
@@ -59,6 +60,7 @@ class EigOptions:
     guard: float = 0.10         # minimum wanted width / spectral spread
     max_retries: int = 2
     seed: int = 1234
+    zolo_r: int = 0             # 0: QDWH steps; r >= 1: Zolo-PD of type (2r+1, 2r) until ell = 1
 
 
 @dataclass
@@ -72,6 +74,7 @@ class SvdOptions:
     s_min: float = 1e-15
     max_retries: int = 2
     seed: int = 1234
+    zolo_r: int = 0             # 0: QDWH steps; r >= 1: Zolo-PD of type (2r+1, 2r)
 
 
 @dataclass
@@ -205,7 +208,29 @@ def index_from_diag(R: np.ndarray, tol: float) -> int:
     return int(hits[0]) if hits.size else d.shape[0]
 
 
-def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float, iters: int, tol: float):
+def polar_iterations(X: np.ndarray, ell0: float, zolo_r: int, fixed_iters: int | None, c_qr: float):
+    """Step 2 of Algorithms 1 and 2: QDWH from ell0 (fixed_iters steps, or until |ell - 1| < 5 eps),
+    QR-based while c_k > c_qr; or, with zolo_r >= 1, Zolo-PD iterations of type (2 zolo_r + 1,
+    2 zolo_r) until |ell - 1| < 5 eps.  Returns (X, schedule, number of QR-formed steps or terms)."""
+    n_qr = 0
+    if zolo_r > 0:
+        sched = zolo_schedule(ell0, zolo_r)
+        for c, a, M, _, _ in sched:
+            X, q = zolo_step(X, c, a, M, c_qr)
+            n_qr += q
+        return X, sched, n_qr
+    sched = dwh_schedule(ell0, fixed_iters=fixed_iters)
+    for a, b, c, _, _ in sched:
+        if c > c_qr:
+            X = qdwh_qr_step(X, a, b, c)
+            n_qr += 1
+        else:
+            X = qdwh_chol_step(X, a, b, c)
+    return X, sched, n_qr
+
+
+def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float, iters: int, tol: float,
+              zolo_r: int = 0):
     """Algorithm 1 steps 1-6 for B = A' - t I with A' = eps_side * A, whose
     wanted eigenvalues lie on [mu, 0], mu = lam_lo - t <= lambda_min(B)."""
     n = A.shape[0]
@@ -214,10 +239,9 @@ def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float,
     # Step 1 scaling A := A/|mu| and step 2 shift A~ = (1-s) A - s I, applied to B.
     X = ((1.0 - s) * eps_side / absmu) * A
     X[np.diag_indices(n)] -= (1.0 - s) * t / absmu + s
-    # Step 2: QDWH iterations from ell_0 = s, Cholesky-based in all iterations (Section 4.1).
-    sched = dwh_schedule(s, fixed_iters=iters)
-    for a, b, c, _, _ in sched:
-        X = qdwh_chol_step(X, a, b, c)
+    # Step 2: QDWH iterations from ell_0 = s, Cholesky-based in all iterations (Section 4.1);
+    # or Zolo-PD iterations.
+    X, sched, _ = polar_iterations(X, s, zolo_r, iters, math.inf if zolo_r == 0 else 100.0)
     # Step 3: QR of (r(A~) + I) / 2.
     Bq = 0.5 * (X + np.eye(n))
     Qf, R = np.linalg.qr(Bq, mode="complete")
@@ -277,7 +301,7 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
 
     retries = 0
     while True:
-        theta, W, Q2, mu, info = _eig_core(A, eps_side, t, lam_lo, opts.s, opts.iters, opts.tol)
+        theta, W, Q2, mu, info = _eig_core(A, eps_side, t, lam_lo, opts.s, opts.iters, opts.tol, opts.zolo_r)
         lamp = eps_side * theta               # Ritz values of A'
         sel = np.nonzero(lamp <= t)[0]
         if sel.size >= k or retries >= opts.max_retries:
@@ -294,21 +318,14 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
     return EigResult(lam, V, Q2.shape[1], eps_side * t, eps_side * mu, retries, info)
 
 
-def qdwhp_svd_threshold(A: np.ndarray, s: float, alpha: float, tol: float = 0.01, c_qr: float = 100.0):
+def qdwhp_svd_threshold(A: np.ndarray, s: float, alpha: float, tol: float = 0.01, c_qr: float = 100.0,
+                        zolo_r: int = 0):
     """Algorithm 2 as printed, for m >= n: the singular triplets with sigma >= s alpha,
     alpha ~ ||A||_2.  Returns (sigma descending, U, V, info)."""
     n = A.shape[1]
     # Step 2: QDWH on A/alpha from ell_0 = s until |ell - 1| < 5 eps; QR-based steps
     # while c_k > c_qr (Section 4.2: the QR form for the first step when s is small).
-    X = A / alpha
-    sched = dwh_schedule(s)
-    n_qr = 0
-    for a, b, c, _, _ in sched:
-        if c > c_qr:
-            X = qdwh_qr_step(X, a, b, c)
-            n_qr += 1
-        else:
-            X = qdwh_chol_step(X, a, b, c)
+    X, sched, n_qr = polar_iterations(A / alpha, s, zolo_r, None, c_qr)
     # Step 3: QR of I - r(A~)^T r(A~).
     Bq = np.eye(n) - X.T @ X
     Qf, R = np.linalg.qr(Bq, mode="complete")
@@ -345,7 +362,7 @@ def qdwhp_svd(A: np.ndarray, opts: SvdOptions) -> SvdResult:
     s = max(sig_hat / alpha * (1.0 - 1e-10), opts.s_min)
     retries = 0
     while True:
-        sigma, U, V, info = qdwhp_svd_threshold(A, s, alpha, opts.tol, opts.c_qr)
+        sigma, U, V, info = qdwhp_svd_threshold(A, s, alpha, opts.tol, opts.c_qr, opts.zolo_r)
         if sigma.shape[0] >= k or retries >= opts.max_retries:
             break
         retries += 1
