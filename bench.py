@@ -207,7 +207,8 @@ def run_ours(args):
     A_host = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()
     A = A_host.to(dev)
     k = p.k
-    o = Q.default_opts()
+    sopts = {"precision": precision_code(Q, args.precision), "refine_steps": args.refine, "zolo_r": args.zolo}
+    o = Q.default_opts(**sopts)
     ws = Q.workspace(Q.lib().qdwhp_svd_workspace_bytes(M, N, __import__("ctypes").byref(o)), dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -217,7 +218,6 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    sopts = {"precision": precision_code(Q, args.precision), "refine_steps": args.refine}
     for _ in range(args.warmup):
         r = Q.svd(A, k=k, ws=ws, **sopts)
     torch.cuda.synchronize()
@@ -277,7 +277,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[args.precision],
-        "data": "synthetic", "config": dict(workload_config(k), precision=args.precision, refine_steps=args.refine),
+        "data": "synthetic", "config": dict(workload_config(k), precision=args.precision, refine_steps=args.refine,
+                                                  polar="zolo-pd r=%d" % args.zolo if args.zolo else "qdwh"),
         "accuracy": acc,
         "tflops": fl / (total_ms / args.steps / 1e3) / 1e12,
         "tflops_frac_of_fp64_peak": fl / (total_ms / args.steps / 1e3) / 1e12 / peak,
@@ -417,17 +418,17 @@ def run_eig_large(args):
     A, lam, k = I.eig_clustered_device(16384, 3000, frac)
     n = A.shape[0]
     prec = precision_code(Q, args.precision)
-    o = Q.default_opts(precision=prec)
+    o = Q.default_opts(precision=prec, zolo_r=args.zolo)
     ws = Q.workspace(Q.lib().qdwhp_eig_workspace_bytes(n, __import__("ctypes").byref(o)))
     for _ in range(args.warmup):
-        r = Q.eig(A, k=k, ws=ws, precision=prec)
+        r = Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
     torch.cuda.synchronize()
     ms = []
     Q.profile_begin()
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = Q.eig(A, k=k, ws=ws, precision=prec)
+        r = Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -441,7 +442,7 @@ def run_eig_large(args):
         + 2 * n * ell * k
     t = statistics.median(ms) / 1e3
     print(json.dumps({"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})",
-                      "precision": args.precision, "ell": ell,
+                      "precision": args.precision, "zolo_r": args.zolo, "ell": ell,
                       "ms_median": 1e3 * t, "solves_per_s": 1 / t, "alg_tflops": fl / t / 1e12,
                       "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9,
                       "gemm_share": prof["gemm_ms"] / sum(ms), "lam_err": err, "resid": res,
@@ -624,6 +625,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "mixed", "emulated", "mixed-emulated"], default="fp64")
     ap.add_argument("--refine", type=int, default=0, help="FP64 refinement steps on Q2 (SVD)")
+    ap.add_argument("--zolo", type=int, default=0, help="Zolo-PD of order r in place of the QDWH steps (0: QDWH)")
     ap.add_argument("--kernel", choices=["gemm"], default=None,
                     help="time one building block in isolation instead of the full solve")
     ap.add_argument("--single", action="store_true", help="one untimed solve (for profiler launch lists)")

@@ -77,12 +77,17 @@ typedef struct {
   uint64_t seed;          /* seed of the SplitMix64 start vectors */
   int32_t refine_steps;   /* SVD: FP64 subspace-iteration steps on Q2, Q2 <- orth(A^T A Q2), before the
                              projection (default 0; for QDWHP_MIXED they restore FP64-level vectors) */
+  int32_t zolo_r;         /* 0 (default): QDWH steps.  1..8: Zolo-PD iterations (the type (2r+1, 2r)
+                             Zolotarev variant of Section 3.1) from ell_0 = s_eig (EIG) or s (SVD)
+                             until ell_k = 1, each with one Gram matrix and r independent terms
+                             X (X^T X + c I)^{-1} (Cholesky-formed, or QR-formed when 1 / c > c_qr);
+                             iters_eig is then unused.  QDWHP_FP64 or QDWHP_FP64_EMULATED only. */
 } qdwhp_opts;
 
 /* Per-solve report (host struct, filled when the pointer is non-NULL). */
 typedef struct {
-  int32_t it_qr;          /* QR-based QDWH steps */
-  int32_t it_chol;        /* Cholesky-based QDWH steps */
+  int32_t it_qr;          /* QR-based QDWH steps (Zolo-PD: QR-formed terms) */
+  int32_t it_chol;        /* Cholesky-based QDWH steps (Zolo-PD: Cholesky-formed terms) */
   int32_t retries;
   int32_t jacobi_sweeps;
   int64_t ell;            /* captured subspace size (n - ind) */
@@ -96,6 +101,7 @@ typedef struct {
   float ms_total;         /* device time of the solve (CUDA events) */
   int32_t it_f32;         /* Cholesky-based steps run in FP32 (QDWHP_MIXED) */
   int32_t dc_nodes;       /* EIG: spectral splits of the Rayleigh-Ritz problem (0 = Jacobi alone) */
+  int32_t zolo_steps;     /* Zolo-PD iterations (0 with QDWH steps) */
 } qdwhp_info;
 
 QDWHP_API void qdwhp_default_opts(qdwhp_opts* opts);

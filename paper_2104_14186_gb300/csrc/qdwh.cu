@@ -7,6 +7,16 @@
 //   QR-based (eq. practical-polar-qr):
 //     [sqrt(c) X; I] = [Q1; Q2] R,  X <- (b/c) X + (1/sqrt(c)) (a - b/c) Q1 Q2^T.
 // Each step also reports ||X_k - X_{k-1}||_F (the Section 5 listing's diagnostic).
+//
+// Zolo-PD (the higher-order Zolotarev variant that Section 3.1 sets beside QDWH and the
+// conclusion leaves as future work; Nakatsukasa and Freund, SIAM Review 2016): iteration k
+// applies the best type (2r+1, 2r) rational approximation of sign on [ell_k, 1],
+//     X <- mhat (X + sum_j a_j X (X^T X + c_{2j-1} I)^{-1}),
+// with c_i = ell^2 sc^2(i K' / (2r+1); ell'), ell' = sqrt(1 - ell^2), K' = K(ell'), the
+// partial-fraction weights a_j and mhat normalising Z(1) = 1; ell_{k+1} = Z(ell_k).  One
+// Gram matrix X^T X serves every Cholesky-formed term; a term whose shift is small
+// (1 / c_{2j-1} > c_qr) is formed from [X; sqrt(c) I] = [Q1; Q2] R as Q1 Q2^T / sqrt(c).
+// r = 1 is the QDWH step.
 #include "internal.h"
 #include "qdwh.h"
 
@@ -56,7 +66,97 @@ __global__ void dwh_schedule_kernel(const double* ell0_dev, double ell0_host, in
   out->nsteps = n;
 }
 
+// Jacobi elliptic sn(u) and cn(u) of modulus k = sqrt(1 - kc^2), given the complementary
+// modulus kc, by the arithmetic-geometric mean (descending Landen) method of Abramowitz and
+// Stegun 16.4: a_0 = 1, b_0 = kc, c_0 = k; a_{i+1} = (a_i + b_i) / 2, b_{i+1} = sqrt(a_i b_i),
+// c_{i+1} = (a_i - b_i) / 2 until c_N / a_N < 2^-54; phi_N = 2^N a_N u and
+// phi_{i-1} = (phi_i + asin(c_i sin(phi_i) / a_i)) / 2; sn = sin(phi_0), cn = cos(phi_0).
+// Taking kc as the input keeps the method accurate when k is within rounding of 1.
+__device__ void elliptic_sn_cn(double u, double kc, double* sn, double* cn) {
+  constexpr int kAgmMax = 40;
+  double av[kAgmMax], cv[kAgmMax];
+  double a = 1.0, b = kc;
+  av[0] = 1.0;
+  cv[0] = sqrt((1.0 - kc) * (1.0 + kc));
+  int N = 0;
+  while (N + 1 < kAgmMax && cv[N] > 0x1.0p-54 * av[N]) {
+    const double an = 0.5 * (a + b), cn_next = 0.5 * (a - b);
+    b = sqrt(a * b);
+    a = an;
+    ++N;
+    av[N] = a;
+    cv[N] = cn_next;
+  }
+  double phi = ldexp(a * u, N);
+  for (int i = N; i >= 1; --i) phi = 0.5 * (phi + asin(cv[i] * sin(phi) / av[i]));
+  *sn = sin(phi);
+  *cn = cos(phi);
+}
+
+// Complete elliptic integral of the first kind K of the modulus whose complement is kc:
+// K = pi / (2 AGM(1, kc)).
+__device__ double elliptic_k_of_complement(double kc) {
+  double a = 1.0, b = kc;
+  for (int i = 0; i < 64 && fabs(a - b) > 0x1.0p-53 * a; ++i) {
+    const double an = 0.5 * (a + b);
+    b = sqrt(a * b);
+    a = an;
+  }
+  return 3.14159265358979323846 / (2.0 * a);
+}
+
+__global__ void zolo_schedule_kernel(double ell0, int r, double c_qr, ZoloSchedule* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double ell = ell0;
+  out->ell0 = ell0;
+  out->r = r;
+  int n = 0;
+  while (n < kMaxSteps && ell < 1.0 && fabs(ell - 1.0) >= 5.0 * 0x1.0p-52) {
+    // K' = K(ell'), whose complementary modulus is ell; c_i = ell^2 sc^2(i K' / (2r+1); ell').
+    // Past K'/2, sc(K' - v) = cn(v) / (ell sn(v)) keeps cn away from 0: c_i = cs^2(v).
+    const double Kp = elliptic_k_of_complement(ell);
+    const int d = 2 * r + 1;
+    double* c = out->c[n];
+    for (int i = 1; i <= 2 * r; ++i) {
+      double sn, cn;
+      if (2 * i <= d) {
+        elliptic_sn_cn(i * Kp / d, ell, &sn, &cn);
+        c[i - 1] = ell * ell * (sn / cn) * (sn / cn);
+      } else {
+        elliptic_sn_cn((d - i) * Kp / d, ell, &sn, &cn);
+        c[i - 1] = (cn / sn) * (cn / sn);
+      }
+    }
+    double mhat = 1.0, zl = ell;
+    for (int j = 0; j < r; ++j) {
+      const double codd = c[2 * j];
+      double num = 1.0, den = 1.0;
+      for (int k = 0; k < r; ++k) {
+        num *= codd - c[2 * k + 1];
+        if (k != j) den *= codd - c[2 * k];
+      }
+      out->a[n][j] = -num / den;
+      out->use_qr[n][j] = (1.0 / codd > c_qr) ? 1 : 0;
+      mhat *= (1.0 + codd) / (1.0 + c[2 * j + 1]);
+      zl *= (ell * ell + c[2 * j + 1]) / (ell * ell + codd);
+    }
+    out->mhat[n] = mhat;
+    const double nxt = fmin(mhat * zl, 1.0);
+    out->ell_after[n] = nxt;
+    ell = nxt;
+    ++n;
+  }
+  out->nsteps = n;
+}
+
 }  // namespace
+
+qdwhp_status zolo_schedule(cudaStream_t st, double ell0, int r, double c_qr, ZoloSchedule* out_dev) {
+  if (r < 1 || r > kZoloMaxR || !(ell0 > 0.0)) return QDWHP_ERR_ARG;
+  zolo_schedule_kernel<<<1, 32, 0, st>>>(ell0, r, c_qr, out_dev);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
 
 qdwhp_status dwh_schedule(cudaStream_t st, const double* ell0_dev, double ell0_host, int fixed_iters, double c_qr,
                           Schedule* out_dev) {
@@ -65,7 +165,7 @@ qdwhp_status dwh_schedule(cudaStream_t st, const double* ell0_dev, double ell0_h
   return QDWHP_OK;
 }
 
-void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w, bool need_f32) {
+void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w, bool need_f32, bool need_zolo) {
   w.m = m;
   w.n = n;
   w.Z = ar.take<double>((size_t)n * n);
@@ -85,6 +185,11 @@ void carve_qdwh(Arena& ar, int64_t m, int64_t n, bool need_qr, QdwhWs& w, bool n
     w.qf.tau = ar.take<double>(n);
     w.qf.diagR = ar.take<double>(n);
     w.qr_scratch = ar.take<double>(qr_scratch_elems(mm, n));
+  }
+  w.has_zolo = need_zolo;
+  if (need_zolo) {
+    w.G = ar.take<double>((size_t)n * n);
+    w.Acc = ar.take<double>((size_t)m * n);
   }
   w.has_f32 = need_f32;
   if (need_f32) {
@@ -123,6 +228,55 @@ qdwhp_status qr_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t l
   QDWHP_TRY(gemm(st, false, true, m, n, n, 1.0, w.S, mm, w.S + m, mm, 0.0, w.Y, m));
   QDWHP_TRY(axpby_diff(st, m, n, b / c, X, ldx, (a - b / c) / sc, w.Y, m, w.diff_parts));
   return reduce_parts(st, w.diff_parts, kDiffParts, w.diff + step);
+}
+
+// One Zolo-PD iteration (see the file header).
+qdwhp_status zolo_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, const ZoloSchedule& z,
+                       int step, QdwhWs& w, int* n_qr_terms, int* n_chol_terms) {
+  if (!w.has_zolo || !w.has_qr) return QDWHP_ERR_ARG;
+  const int r = z.r;
+  const int64_t mm = m + n;
+  bool any_chol = false;
+  for (int j = 0; j < r; ++j) any_chol |= !z.use_qr[step][j];
+  // G = X^T X (lower; the upper triangle held at 0 so that G + c I copies finite values),
+  // shared by the Cholesky-formed terms
+  if (any_chol) {
+    QDWHP_TRY(set_matrix(st, n, n, 0.0, 0.0, w.G, n));
+    QDWHP_TRY(gemm(st, true, false, n, n, m, 1.0, X, ldx, X, ldx, 0.0, w.G, n, LOWER));
+  }
+  QDWHP_TRY(copy_matrix(st, m, n, X, ldx, w.Acc, m));
+  for (int j = 0; j < r; ++j) {
+    const double cj = z.c[step][2 * j], aj = z.a[step][j];
+    if (z.use_qr[step][j]) {
+      // [X; sqrt(c) I] = [Q1; Q2] R:  X (X^T X + c I)^{-1} = Q1 Q2^T / sqrt(c)
+      const double sc = sqrt(cj);
+      QDWHP_TRY(copy_matrix(st, m, n, X, ldx, w.S, mm));
+      QDWHP_TRY(set_matrix(st, n, n, 0.0, sc, w.S + m, mm));
+      QDWHP_TRY(geqrf(st, mm, n, w.S, mm, w.qf, w.qr_scratch));
+      QDWHP_TRY(orgqr_columns(st, w.qf, 0, n, w.S, mm, w.qr_scratch));
+      QDWHP_TRY(gemm(st, false, true, m, n, n, aj / sc, w.S, mm, w.S + m, mm, 1.0, w.Acc, m));
+      ++*n_qr_terms;
+    } else {
+      // G + c I = L L^T:  X (G + c I)^{-1} = (X L^{-T}) L^{-1}
+      QDWHP_TRY(axpby(st, n, n, 1.0, w.G, n, 0.0, w.Z, n, cj));
+      QDWHP_TRY(potrf(st, n, w.Z, n, w.Linv, w.scratch, w.fail));
+      QDWHP_TRY(copy_matrix(st, m, n, X, ldx, w.Y, m));
+      QDWHP_TRY(trsm_right_lower(st, true, m, n, w.Y, m, w.Z, n, w.Linv, w.scratch));
+      QDWHP_TRY(trsm_right_lower(st, false, m, n, w.Y, m, w.Z, n, w.Linv, w.scratch));
+      QDWHP_TRY(axpby(st, m, n, aj, w.Y, m, 1.0, w.Acc, m));
+      ++*n_chol_terms;
+    }
+  }
+  // X <- mhat Acc, with ||X_new - X_old||_F^2
+  QDWHP_TRY(axpby_diff(st, m, n, 0.0, X, ldx, z.mhat[step], w.Acc, m, w.diff_parts));
+  return reduce_parts(st, w.diff_parts, kDiffParts, w.diff + step);
+}
+
+qdwhp_status run_zolo(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t ldx, const ZoloSchedule& z,
+                      QdwhWs& w, int* n_qr_terms, int* n_chol_terms) {
+  *n_qr_terms = *n_chol_terms = 0;
+  for (int i = 0; i < z.nsteps; ++i) QDWHP_TRY(zolo_step(st, m, n, X, ldx, z, i, w, n_qr_terms, n_chol_terms));
+  return QDWHP_OK;
 }
 
 qdwhp_status chol_step_f32(cudaStream_t st, int64_t m, int64_t n, double a, double b, double c, QdwhWs& w,

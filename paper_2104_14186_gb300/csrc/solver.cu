@@ -72,6 +72,7 @@ struct Common {
   LanczosState* lst = nullptr;
   JacobiState* jst = nullptr;
   Schedule* sched = nullptr;
+  ZoloSchedule* zsched = nullptr;
   int* ints = nullptr;        // [0] ind, [1] count, [2..] spare
   unsigned* nonfinite = nullptr;
   double* vals = nullptr;     // n
@@ -86,6 +87,7 @@ struct HostScalars {
   LanczosState lst;
   JacobiState jst;
   Schedule sched;
+  ZoloSchedule zsched;
   int ints[4];
   unsigned nonfinite;
 };
@@ -94,6 +96,7 @@ void carve_common(Arena& ar, int64_t m, int64_t n, int steps, Common& c) {
   c.lst = ar.take<LanczosState>(1);
   c.jst = ar.take<JacobiState>(1);
   c.sched = ar.take<Schedule>(1);
+  c.zsched = ar.take<ZoloSchedule>(1);
   c.ints = ar.take<int>(8);
   c.nonfinite = ar.take<unsigned>(4);
   c.vals = ar.take<double>(std::max<int64_t>(n, 1));
@@ -162,7 +165,7 @@ struct EigWs {
 
 void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   carve_common(ar, n, n, o.lanczos_steps, w.c);
-  carve_qdwh(ar, n, n, false, w.q, fp32_steps(o));
+  carve_qdwh(ar, n, n, o.zolo_r > 0, w.q, fp32_steps(o), o.zolo_r > 0);
   w.X = ar.take<double>((size_t)n * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
@@ -297,9 +300,17 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   QDWHP_TRY(small_sym_eig(st, width, lam_lo, lam_hi, o.seed, w, o.jacobi_max_sweeps, hs, &sweeps, true));
   QDWHP_TRY(select_sort(st, width, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
   QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
-  QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
+  // Step 2's polar iterations: QDWH (iters_eig Cholesky-based steps from ell_0 = s) or
+  // Zolo-PD of order zolo_r until ell_k = 1.
+  const bool zolo = o.zolo_r > 0;
+  if (zolo) {
+    QDWHP_TRY(zolo_schedule(st, o.s_eig, o.zolo_r, o.c_qr, w.c.zsched));
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.zsched, w.c.zsched, sizeof(ZoloSchedule), cudaMemcpyDeviceToHost, st));
+  } else {
+    QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.sched, w.c.sched, sizeof(Schedule), cudaMemcpyDeviceToHost, st));
+  }
   double theta_k = 0.0;
-  QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.sched, w.c.sched, sizeof(Schedule), cudaMemcpyDeviceToHost, st));
   QDWHP_TRY(sync_read(st, &theta_k, w.S1, sizeof(double)));
   double t = theta_k + 1e-10 * spread;
   t = std::max(t, lam_lo + o.guard * (lam_hi - lam_lo));
@@ -316,8 +327,14 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     QDWHP_TRY(axpby(st, n, n, (1.0 - s) * eps_side / absmu, A, lda, 0.0, w.X, n, -((1.0 - s) * t / absmu + s)));
     QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
     int n_qr = 0, n_chol = 0, n_f32 = 0;
-    QDWHP_TRY(run_schedule(st, n, n, w.X, n, hs.sched, fp32_steps(o), w.q, &n_qr, &n_chol, &n_f32));
+    if (zolo) {
+      QDWHP_TRY(run_zolo(st, n, n, w.X, n, hs.zsched, w.q, &n_qr, &n_chol));
+    } else {
+      QDWHP_TRY(run_schedule(st, n, n, w.X, n, hs.sched, fp32_steps(o), w.q, &n_qr, &n_chol, &n_f32));
+    }
     inf.it_f32 = n_f32;
+    inf.it_qr = n_qr;
+    inf.it_chol = n_chol;
     // Step 3: QR of (r(A~) + I) / 2.
     QDWHP_TRY(axpby(st, n, n, 0.5, w.X, n, 0.0, w.X, n, 0.5));
     QDWHP_TRY(geqrf(st, n, n, w.X, n, w.f, w.qr_scratch));
@@ -330,10 +347,12 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     QDWHP_CUDA_TRY(cudaMemcpyAsync(diffs, w.q.diff, sizeof(double) * kMaxSteps, cudaMemcpyDeviceToHost, st));
     QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
     if (fail) return QDWHP_ERR_BREAKDOWN;
-    for (int i = 0; i < hs.sched.nsteps && i < 12; ++i) {
+    const int nsteps = zolo ? hs.zsched.nsteps : hs.sched.nsteps;
+    for (int i = 0; i < nsteps && i < 12; ++i) {
       inf.conv[i] = std::sqrt(diffs[i]);
-      inf.ell_k[i] = hs.sched.ell_after[i];
+      inf.ell_k[i] = zolo ? hs.zsched.ell_after[i] : hs.sched.ell_after[i];
     }
+    inf.zolo_steps = zolo ? nsteps : 0;
     const int ind = hs.ints[0];
     ell = n - ind;
     count = 0;
@@ -365,8 +384,6 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   QDWHP_TRY(gather_columns(st, ell, k, w.S3, ell, w.c.order, nullptr, w.S2, ell));
   QDWHP_TRY(gemm(st, false, false, n, k, ell, 1.0, w.q.Y, n, w.S2, ell, 0.0, V, ldv));
   inf.ms_total = timer.stop();
-  inf.it_chol = hs.sched.nsteps;
-  inf.it_qr = 0;
   inf.retries = retries;
   inf.ell = ell;
   inf.k = k;
@@ -394,7 +411,7 @@ struct SvdWs {
 
 void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
   carve_common(ar, m, n, o.lanczos_steps, w.c);
-  carve_qdwh(ar, m, n, true, w.q, fp32_steps(o));
+  carve_qdwh(ar, m, n, true, w.q, fp32_steps(o), o.zolo_r > 0);
   w.X = ar.take<double>((size_t)m * n);
   w.f.Vall = ar.take<double>((size_t)n * n);
   w.f.T = ar.take<double>((size_t)ceil_div(n, kQRNB) * kQRNB * kQRNB);
@@ -480,14 +497,24 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   int64_t ell = 0;
   int count = 0;
   for (;;) {
-    QDWHP_TRY(dwh_schedule(st, nullptr, s, 0, o.c_qr, w.c.sched));
-    QDWHP_TRY(sync_read(st, &hs.sched, w.c.sched, sizeof(Schedule)));
-    // Step 2: QDWH on A / alpha from ell_0 = s.
+    const bool zolo = o.zolo_r > 0;
+    if (zolo) {
+      QDWHP_TRY(zolo_schedule(st, s, o.zolo_r, o.c_qr, w.c.zsched));
+      QDWHP_TRY(sync_read(st, &hs.zsched, w.c.zsched, sizeof(ZoloSchedule)));
+    } else {
+      QDWHP_TRY(dwh_schedule(st, nullptr, s, 0, o.c_qr, w.c.sched));
+      QDWHP_TRY(sync_read(st, &hs.sched, w.c.sched, sizeof(Schedule)));
+    }
+    // Step 2: QDWH (or Zolo-PD) on A / alpha from ell_0 = s.
     QDWHP_TRY(axpby(st, m, n, 1.0 / alpha, A, lda, 0.0, w.X, m));
     QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
     int n_f32 = 0;
-    QDWHP_TRY(run_schedule(st, m, n, w.X, m, hs.sched, fp32_steps(o), w.q, &inf.it_qr, &inf.it_chol,
-                           &n_f32));
+    if (zolo) {
+      QDWHP_TRY(run_zolo(st, m, n, w.X, m, hs.zsched, w.q, &inf.it_qr, &inf.it_chol));
+    } else {
+      QDWHP_TRY(run_schedule(st, m, n, w.X, m, hs.sched, fp32_steps(o), w.q, &inf.it_qr, &inf.it_chol,
+                             &n_f32));
+    }
     inf.it_f32 = n_f32;
     // Step 3: QR of I - X^T X.
     double* B = w.q.Z;
@@ -502,10 +529,12 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     QDWHP_CUDA_TRY(cudaMemcpyAsync(diffs, w.q.diff, sizeof(double) * kMaxSteps, cudaMemcpyDeviceToHost, st));
     QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
     if (fail) return QDWHP_ERR_BREAKDOWN;
-    for (int i = 0; i < hs.sched.nsteps && i < 12; ++i) {
+    const int nsteps = zolo ? hs.zsched.nsteps : hs.sched.nsteps;
+    for (int i = 0; i < nsteps && i < 12; ++i) {
       inf.conv[i] = std::sqrt(diffs[i]);
-      inf.ell_k[i] = hs.sched.ell_after[i];
+      inf.ell_k[i] = zolo ? hs.zsched.ell_after[i] : hs.sched.ell_after[i];
     }
+    inf.zolo_steps = zolo ? nsteps : 0;
     const int ind = hs.ints[0];
     ell = n - ind;
     count = 0;
@@ -564,7 +593,8 @@ bool opts_valid(const qdwhp_opts& o) {
   return o.s_eig > 0.0 && o.s_eig < 1.0 && o.iters_eig >= 1 && o.iters_eig <= kMaxSteps && o.tol > 0.0 &&
          o.c_qr > 0.0 && o.block_extra >= 0 && o.power_steps >= 0 && o.power_steps <= 16 && o.lanczos_steps >= 1 &&
          o.guard >= 0.0 && o.guard < 1.0 && o.max_retries >= 0 && o.jacobi_max_sweeps >= 1 &&
-         o.refine_steps >= 0 && o.refine_steps <= 64 &&
+         o.refine_steps >= 0 && o.refine_steps <= 64 && o.zolo_r >= 0 && o.zolo_r <= kZoloMaxR &&
+         (o.zolo_r == 0 || o.precision == QDWHP_FP64 || o.precision == QDWHP_FP64_EMULATED) &&
          (o.side == QDWHP_LARGEST || o.side == QDWHP_SMALLEST) &&
          (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED || o.precision == QDWHP_FP64_EMULATED ||
           o.precision == QDWHP_MIXED_EMULATED);
@@ -596,6 +626,7 @@ QDWHP_API void qdwhp_default_opts(qdwhp_opts* o) {
   o->jacobi_max_sweeps = 30;
   o->seed = 1234;
   o->refine_steps = 0;
+  o->zolo_r = 0;
 }
 
 QDWHP_API const char* qdwhp_status_string(qdwhp_status s) {

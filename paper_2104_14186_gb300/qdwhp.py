@@ -38,7 +38,7 @@ class Opts(C.Structure):
         ("s_eig", C.c_double), ("iters_eig", C.c_int32), ("lanczos_steps", C.c_int32), ("tol", C.c_double),
         ("c_qr", C.c_double), ("block_extra", C.c_int32), ("power_steps", C.c_int32), ("guard", C.c_double),
         ("max_retries", C.c_int32), ("jacobi_max_sweeps", C.c_int32), ("seed", C.c_uint64),
-        ("refine_steps", C.c_int32),
+        ("refine_steps", C.c_int32), ("zolo_r", C.c_int32),
     ]
 
 
@@ -47,12 +47,12 @@ class Info(C.Structure):
         ("it_qr", C.c_int32), ("it_chol", C.c_int32), ("retries", C.c_int32), ("jacobi_sweeps", C.c_int32),
         ("ell", C.c_int64), ("k", C.c_int64), ("t", C.c_double), ("mu", C.c_double), ("s", C.c_double),
         ("alpha", C.c_double), ("ell_k", C.c_double * 12), ("conv", C.c_double * 12), ("ms_total", C.c_float),
-        ("it_f32", C.c_int32), ("dc_nodes", C.c_int32),
+        ("it_f32", C.c_int32), ("dc_nodes", C.c_int32), ("zolo_steps", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("ell_k", "conv")}
-        n = self.it_qr + self.it_chol
+        n = self.zolo_steps if self.zolo_steps else self.it_qr + self.it_chol
         d["ell_k"] = list(self.ell_k)[:n]
         d["conv"] = list(self.conv)[:n]
         return d

@@ -115,3 +115,31 @@ def test_gesvd_argument_checks(lib):
     info = Q.GesvdInfo()
     assert lib.qdwhp_gesvd_f64(None, 3, 3, 3, 0, None, None, 3, None, 3, None, 0, C.byref(info), None) == -1
     assert C.sizeof(Q.GesvdInfo) == 56
+
+
+def test_struct_offsets_match_c_compiler(tmp_path):
+    """sizeof and offsetof of every struct the binding mirrors, from gcc on the header."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2104_14186_gb300 import qdwhp as Q
+    structs = {"qdwhp_opts": Q.Opts, "qdwhp_info": Q.Info, "qdwhp_syev_info": Q.SyevInfo,
+               "qdwhp_gesvd_info": Q.GesvdInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qdwhp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                               text=True).stdout.split("\n") if line)
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
