@@ -513,12 +513,12 @@ def run_batched(args):
     sizes = I.batch_sizes(args.count, 4000)
     As = [I.eig_uniform_device(int(n), 4000 + i, 0.10)[0] for i, n in enumerate(sizes)]
     prec = precision_code(Q, args.precision)
-    Q.eig_batched(As[:8], 0.10, concurrency=args.concurrency, precision=prec)    # warm-up
+    Q.eig_batched(As[:8], 0.10, concurrency=args.concurrency, precision=prec, zolo_r=args.zolo)    # warm-up
     torch.cuda.synchronize()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        res, sts = Q.eig_batched(As, 0.10, concurrency=args.concurrency, precision=prec)
+        res, sts = Q.eig_batched(As, 0.10, concurrency=args.concurrency, precision=prec, zolo_r=args.zolo)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         assert all(s == 0 for s in sts), sts
@@ -533,7 +533,7 @@ def run_batched(args):
         worst_lam = max(worst_lam, torch.max(torch.abs(r.lam - true)).item())
         worst_res = max(worst_res, (torch.linalg.norm(A @ r.V - r.V * r.lam[None, :]) / torch.linalg.norm(A)).item())
     print(json.dumps({"workload": f"batched QDWHpartial-EIG: {args.count} matrices, n in [64, 1024], top 10 %",
-                      "precision": args.precision, "concurrency": args.concurrency,
+                      "precision": args.precision, "zolo_r": args.zolo, "concurrency": args.concurrency,
                       "solves_per_s": args.count / t, "ms_per_batch": 1e3 * t, "alg_tflops_lower_bound": fl / t / 1e12,
                       "max_lam_err": worst_lam, "max_resid": worst_res}), flush=True)
 
