@@ -67,30 +67,41 @@ __global__ void dwh_schedule_kernel(const double* ell0_dev, double ell0_host, in
 }
 
 // Jacobi elliptic sn(u) and cn(u) of modulus k = sqrt(1 - kc^2), given the complementary
-// modulus kc, by the arithmetic-geometric mean (descending Landen) method of Abramowitz and
-// Stegun 16.4: a_0 = 1, b_0 = kc, c_0 = k; a_{i+1} = (a_i + b_i) / 2, b_{i+1} = sqrt(a_i b_i),
-// c_{i+1} = (a_i - b_i) / 2 until c_N / a_N < 2^-54; phi_N = 2^N a_N u and
-// phi_{i-1} = (phi_i + asin(c_i sin(phi_i) / a_i)) / 2; sn = sin(phi_0), cn = cos(phi_0).
-// Taking kc as the input keeps the method accurate when k is within rounding of 1.
-__device__ void elliptic_sn_cn(double u, double kc, double* sn, double* cn) {
-  constexpr int kAgmMax = 40;
-  double av[kAgmMax], cv[kAgmMax];
-  double a = 1.0, b = kc;
-  av[0] = 1.0;
-  cv[0] = sqrt((1.0 - kc) * (1.0 + kc));
-  int N = 0;
-  while (N + 1 < kAgmMax && cv[N] > 0x1.0p-54 * av[N]) {
-    const double an = 0.5 * (a + b), cn_next = 0.5 * (a - b);
-    b = sqrt(a * b);
-    a = an;
-    ++N;
-    av[N] = a;
-    cv[N] = cn_next;
+// modulus kc, for 0 <= u <= K(k) / 2, by Landen's descending transformation (DLMF 22.7.1-3):
+// with k1 = (1 - kc) / (1 + kc) and v = u / (1 + k1),
+//   sn(u, k) = (1 + k1) sn(v, k1) / D,  cn(u, k) = cn(v, k1) dn(v, k1) / D,
+//   dn(u, k) = (1 - k1 sn^2(v, k1)) / D,  D = 1 + k1 sn^2(v, k1),
+// repeated until the modulus is below 2^-27, where sn, cn, dn are sin, cos, 1 to rounding.
+// Every quantity is carried through its complement: 1 - k1 = 2 kc / (1 + kc),
+// kc1 = 2 sqrt(kc) / (1 + kc), and dn's numerator is (1 - k1) + k1 cn^2, so nothing cancels
+// when k is within rounding of 1.  Since u <= K / 2 ends at an argument <= pi / 4, cn stays
+// well away from 0 at the bottom, and all steps multiply or divide positive numbers: sn and
+// cn keep a relative accuracy of a few ulps for any kc in (0, 1].
+__device__ void elliptic_sn_cn(double u, double kc, double* sn_out, double* cn_out) {
+  constexpr int kLandenMax = 40;
+  double k[kLandenMax], omk[kLandenMax];
+  int levels = 0;
+  double v = u;
+  while (levels < kLandenMax) {
+    const double k1 = (1.0 - kc) / (1.0 + kc);
+    k[levels] = k1;
+    omk[levels] = 2.0 * kc / (1.0 + kc);
+    ++levels;
+    kc = 2.0 * sqrt(kc) / (1.0 + kc);
+    v /= 1.0 + k1;
+    if (k1 < 0x1.0p-27) break;
   }
-  double phi = ldexp(a * u, N);
-  for (int i = N; i >= 1; --i) phi = 0.5 * (phi + asin(cv[i] * sin(phi) / av[i]));
-  *sn = sin(phi);
-  *cn = cos(phi);
+  double sn = sin(v), cn = cos(v), dn = 1.0;
+  for (int i = levels - 1; i >= 0; --i) {
+    const double den = 1.0 + k[i] * sn * sn;
+    const double sn_up = (1.0 + k[i]) * sn / den;
+    const double cn_up = cn * dn / den;
+    dn = (omk[i] + k[i] * cn * cn) / den;
+    sn = sn_up;
+    cn = cn_up;
+  }
+  *sn_out = sn;
+  *cn_out = cn;
 }
 
 // Complete elliptic integral of the first kind K of the modulus whose complement is kc:

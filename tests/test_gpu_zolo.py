@@ -30,11 +30,14 @@ def dev(x):
 
 
 def check_schedule(info, ell0, r):
+    """The device's ell_k (Landen-transformation elliptic functions, accurate to a few ulps)
+    against the oracle's (scipy's, whose relative error grows to ~1e-11 at ell = 1e-3 as the
+    parameter 1 - ell^2 nears 1): agreement to 1e-10."""
     sched = Z.zolo_schedule(ell0, r)
     assert info["zolo_steps"] == len(sched), (info, len(sched))
     ref = np.array([s[4] for s in sched])
     got = np.array(info["ell_k"])
-    assert np.all(np.abs(got - ref) <= 1e-12 * ref), (got, ref)
+    assert np.all(np.abs(got - ref) <= 1e-10 * ref), (got, ref)
     assert abs(got[-1] - 1.0) < 5 * 2.0 ** -52
 
 
@@ -42,7 +45,8 @@ def check_schedule(info, ell0, r):
 @pytest.mark.parametrize("side", ["largest", "smallest"])
 def test_eig_zolo(Q, r, side):
     """n = 512, 10 %: r = 1 reproduces QDWH's three steps, r = 2, 3 take two; at r = 3 the
-    first term's shift is small enough (1 / c_1 > 100) to use the QR form."""
+    first iteration's first shift is small enough (1 / c_1 > 100) for the QR form, every
+    other term is Cholesky-formed."""
     p = I.eig_uniform(512, 1000 + r, 0.10, side)
     res = Q.eig(dev(p.A), k=p.k, side=side, zolo_r=r)
     true = np.sort(p.lam)[::-1][: p.k] if side == "largest" else np.sort(p.lam)[: p.k]
@@ -50,7 +54,8 @@ def test_eig_zolo(Q, r, side):
     assert m["lam_err"] <= 1e-12 and m["orth"] <= 5e-15 * 512 and m["resid"] <= 1e-13, m
     check_schedule(res.info, 0.2, r)
     assert res.info["zolo_steps"] == (3 if r == 1 else 2)
-    assert res.info["it_qr"] == (2 if r == 3 else 0), res.info
+    assert res.info["it_qr"] == (1 if r == 3 else 0), res.info
+    assert res.info["it_chol"] == (3 if r == 1 else 2 * r - res.info["it_qr"]), res.info
 
 
 @pytest.mark.parametrize("r,frac,decades", [(2, 0.05, 12.0), (4, 0.25, 12.0), (8, 0.25, 12.0)])
@@ -81,3 +86,19 @@ def test_zolo_emulated_and_option_checks(Q):
     with pytest.raises(Q.QdwhpError) as e:
         Q.eig(dev(p.A), k=p.k, zolo_r=9)
     assert e.value.status == -1
+
+
+def test_r1_schedule_matches_qdwh_at_small_threshold(Q):
+    """A threshold near 1e-12 (top 90 % of 13.5 decades): Zolo-PD with r = 1 must follow
+    QDWH's ell_k, whose weights are algebraic (Section 3.1), to 1e-13 relative.  This pins the
+    device's elliptic functions where the modulus is within 1e-24 of 1."""
+    q = I.svd_logspaced(500, 400, 61, 0.90, 13.5)
+    rz = Q.svd(dev(q.A), k=q.k, zolo_r=1)
+    rq = Q.svd(dev(q.A), k=q.k)
+    assert rz.info["s"] == rq.info["s"] and rz.info["s"] < 1e-11, (rz.info["s"], rq.info["s"])
+    ez, eq = np.array(rz.info["ell_k"]), np.array(rq.info["ell_k"])
+    assert ez.size == eq.size >= 5, (ez, eq)
+    assert np.all(np.abs(ez - eq) <= 1e-13 * eq), (ez, eq)
+    for r in (rz, rq):
+        mt = O.svd_metrics(q.A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), q.sigma[: q.k])
+        assert mt["sigma_err"] <= 1e-12, mt
