@@ -89,16 +89,19 @@ def test_zolo_emulated_and_option_checks(Q):
 
 
 def test_r1_schedule_matches_qdwh_at_small_threshold(Q):
-    """A threshold near 1e-12 (top 90 % of 13.5 decades): Zolo-PD with r = 1 must follow
-    QDWH's ell_k, whose weights are algebraic (Section 3.1), to 1e-13 relative.  This pins the
-    device's elliptic functions where the modulus is within 1e-24 of 1."""
-    q = I.svd_logspaced(500, 400, 61, 0.90, 13.5)
-    rz = Q.svd(dev(q.A), k=q.k, zolo_r=1)
-    rq = Q.svd(dev(q.A), k=q.k)
-    assert rz.info["s"] == rq.info["s"] and rz.info["s"] < 1e-11, (rz.info["s"], rq.info["s"])
+    """The 20 largest singular values log-spaced from 1 to 1e-9 above 380 in [1e-11, 1e-10]:
+    the threshold for k = 20 is near 1e-9, and Zolo-PD with r = 1 must follow QDWH's ell_k,
+    whose weights are algebraic (Section 3.1), to 1e-13 relative.  This pins the device's
+    elliptic functions where the modulus is within 1e-18 of 1."""
+    rng = np.random.default_rng(61)
+    sig = np.concatenate([np.logspace(0.0, -9.0, 20), np.logspace(-10.0, -11.0, 380)])
+    A = I.general_with_singular_values(500, sig, rng)
+    rz = Q.svd(dev(A), k=20, zolo_r=1)
+    rq = Q.svd(dev(A), k=20)
+    assert rz.info["s"] == rq.info["s"] and rz.info["s"] < 1e-8, (rz.info["s"], rq.info["s"])
     ez, eq = np.array(rz.info["ell_k"]), np.array(rq.info["ell_k"])
     assert ez.size == eq.size >= 5, (ez, eq)
     assert np.all(np.abs(ez - eq) <= 1e-13 * eq), (ez, eq)
     for r in (rz, rq):
-        mt = O.svd_metrics(q.A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), q.sigma[: q.k])
+        mt = O.svd_metrics(A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), sig[:20])
         assert mt["sigma_err"] <= 1e-12, mt
