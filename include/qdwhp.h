@@ -143,7 +143,9 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
  * Full symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG,
  * Section 3.2, eq. pdeig): A - sigma I = U_p H, the projector (I + U_p) / 2 splits the
  * spectrum at sigma (the mean eigenvalue), and the two Rayleigh-Ritz blocks are split
- * again until they are small enough for one-sided Jacobi.  The same solver handles the
+ * again until they are small enough for one-sided Jacobi.  The split point is an estimate of
+ * the median eigenvalue from the Gauss quadrature of 30 Lanczos steps on the block, or the
+ * mean eigenvalue when that estimate has no interior point or splits one-sidedly.  The same solver handles the
  * Rayleigh-Ritz problems of qdwhp_eig when they are large.
  *   A: n x n symmetric (both triangles stored; the average of A and A^T is used), lda >= n,
  *      never modified.
@@ -164,6 +166,7 @@ typedef struct {
   int32_t jacobi_sweeps;  /* largest sweep count of a leaf */
   double max_offblock;    /* largest ||Q2^T M Q1||_F / ||M - sigma I||_2 of a split */
   float ms_total;         /* device time (CUDA events) */
+  int32_t median_splits;  /* splits made at the Lanczos-quadrature median (the others at the mean) */
 } qdwhp_syev_info;
 QDWHP_API size_t qdwhp_syev_workspace_bytes(int64_t n);
 QDWHP_API qdwhp_status qdwhp_syev_f64(const double* A, int64_t n, int64_t lda, double* lambda, double* V,
@@ -200,7 +203,7 @@ typedef struct {
   int32_t depth;
   int32_t jacobi_sweeps;
   int32_t orthonormalized; /* 1 if U was completed by its QR (numerically rank-deficient A) */
-  int32_t reserved;
+  int32_t median_splits;  /* as in qdwhp_syev_info */
   double alpha;           /* the ||A||_2 estimate A was scaled by */
   double max_offblock;    /* as in qdwhp_syev_info */
   float ms_total;         /* device time (CUDA events) */

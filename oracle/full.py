@@ -9,7 +9,11 @@ second, structural oracle: write A - sigma I = U_p H (eq. pdeig), so that
 C = (I + U_p) / 2 = V_+ V_+^T projects onto the eigenvectors with eigenvalues above
 sigma; take orthonormal bases of range(C) and of its complement, project A on each
 (Rayleigh-Ritz) and recurse.  Readings (the paper does not fix them): the split point is
-the mean eigenvalue trace(A) / n, the polar decomposition starts from ell_0 = 1e-15
+an estimate of the median eigenvalue from the Gauss quadrature of 30 Lanczos steps on A
+(`quadrature_median`, a midpoint between two nodes), then the mean eigenvalue trace(A) / n
+and the middle of [lo, hi], the first whose split is two-sided and resolved
+(trace(C) - ||C||_F^2 <= 0.05, C being a projector to rounding); the polar decomposition
+starts from ell_0 = 1e-15
 (QR-based steps while c_k > 100), rank(C) = round(trace(C)), the bases come from
 Householder QR with column pivoting of C, and problems of order <= `leaf` go to the
 dense eigensolver.
@@ -33,11 +37,17 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
+from scipy.linalg import eigh_tridiagonal
+
+from .partial import lanczos_tridiagonal
 from .qdwh import qdwh_polar
 
 ELL0_SPLIT = 1e-15
 ELL0_SVD = 1e-15
 ORTH_FIX_SVD = 1e-14
+UNRESOLVED = 0.05
+SLQ_STEPS = 30
+SLQ_SEED = 4242
 
 
 def syev(A: np.ndarray):
@@ -61,6 +71,39 @@ def split(A: np.ndarray, sigma: float, alpha: float):
     return r, Q[:, :r], Q[:, r:], C
 
 
+def quadrature_nodes_weights(alpha: np.ndarray, beta: np.ndarray):
+    """Gauss quadrature of the Lanczos tridiagonal (Golub-Welsch): nodes = eigenvalues of T
+    (ascending), weights = squared first components of its eigenvectors."""
+    m = alpha.shape[0]
+    if m == 1:
+        return alpha.copy(), np.ones(1)
+    theta, S = eigh_tridiagonal(alpha, beta[: m - 1])
+    return theta, S[0] ** 2
+
+
+def quadrature_median(A: np.ndarray, seed: int = SLQ_SEED):
+    """Split point near the median eigenvalue of symmetric A, or None.  With the quadrature
+    nodes ascending and c_j the cumulative (normalised) weights, j* is the first node with
+    c_j >= 1/2.  Nodes converge onto clusters, so the candidates are the midpoints beside
+    theta_j*: of theta_{j*-1} and theta_j* (predicting a fraction c_{j*-1} at or below it)
+    and of theta_j* and theta_{j*+1} (predicting c_j*).  The candidate whose prediction lies
+    strictly inside (0, 1) and nearest 1/2 is returned."""
+    n = A.shape[0]
+    alpha, beta = lanczos_tridiagonal(lambda x: A @ x, n, SLQ_STEPS, seed)
+    theta, w = quadrature_nodes_weights(alpha, beta)
+    c = np.cumsum(w / np.sum(w))
+    j = int(min(np.searchsorted(c, 0.5), theta.shape[0] - 1))
+    cands = []
+    if j > 0:
+        cands.append((0.5 * (theta[j - 1] + theta[j]), c[j - 1]))
+    if j + 1 < theta.shape[0]:
+        cands.append((0.5 * (theta[j] + theta[j + 1]), c[j]))
+    cands = [x for x in cands if 1e-12 < x[1] < 1.0 - 1e-12]
+    if not cands:
+        return None
+    return float(min(cands, key=lambda x: abs(x[1] - 0.5))[0])
+
+
 def qdwh_eig(A: np.ndarray, lo: float, hi: float, leaf: int = 64):
     """All eigenpairs of symmetric A with spectrum in [lo, hi] by recursive spectral
     splitting (Section 3.2).  Returns (lam, V), unordered."""
@@ -68,10 +111,15 @@ def qdwh_eig(A: np.ndarray, lo: float, hi: float, leaf: int = 64):
     n = A.shape[0]
     if n <= leaf or hi - lo <= 1e-14 * max(abs(lo), abs(hi), 1e-300):
         return np.linalg.eigh(A)
-    sigma = min(max(np.trace(A) / n, lo), hi)
-    alpha = max(sigma - lo, hi - sigma)
-    r, V1, V2, _ = split(A, sigma, alpha)
-    if r in (0, n):
+    med = quadrature_median(A)
+    cands = ([med] if med is not None else []) + [np.trace(A) / n, 0.5 * (lo + hi)]
+    for cand in cands:
+        sigma = min(max(cand, lo), hi)
+        alpha = max(sigma - lo, hi - sigma)
+        r, V1, V2, C = split(A, sigma, alpha)
+        if 0 < r < n and np.trace(C) - np.sum(C * C) <= UNRESOLVED:
+            break
+    else:
         return np.linalg.eigh(A)
     l1, W1 = qdwh_eig(V1.T @ A @ V1, sigma, hi, leaf)
     l2, W2 = qdwh_eig(V2.T @ A @ V2, lo, sigma, leaf)

@@ -100,12 +100,10 @@ class SvdResult:
     info: dict = field(default_factory=dict)
 
 
-def lanczos_extremes(matvec, n: int, steps: int, seed: int):
-    """Lanczos with full reorthogonalisation (Algorithm 1 step 1).
-
-    Returns (theta_min, res_min, theta_max, res_max): the extreme Ritz values of
-    the tridiagonal T and their residual norms beta_m |s_{m,i}|.
-    """
+def lanczos_tridiagonal(matvec, n: int, steps: int, seed: int):
+    """Lanczos with full reorthogonalisation (classical Gram-Schmidt, twice) from the
+    SplitMix64 start vector.  Returns (alpha (m,), beta (m,)): the diagonal and off-diagonal of
+    the m x m tridiagonal T, beta[m-1] being the norm of the last residual (0 at a breakdown)."""
     steps = max(1, min(steps, n))
     q = uniform_pm1(seed ^ STREAM_LANCZOS, n)
     Q = np.zeros((n, steps), dtype=np.float64)
@@ -117,7 +115,6 @@ def lanczos_extremes(matvec, n: int, steps: int, seed: int):
         w = matvec(Q[:, j])
         alpha[j] = Q[:, j] @ w
         Qj = Q[:, : j + 1]
-        # classical Gram-Schmidt against every Lanczos vector, twice
         w = w - Qj @ (Qj.T @ w)
         w = w - Qj @ (Qj.T @ w)
         beta[j] = np.linalg.norm(w)
@@ -128,7 +125,18 @@ def lanczos_extremes(matvec, n: int, steps: int, seed: int):
             beta[j] = 0.0
             break
         Q[:, j + 1] = w / beta[j]
-    T = np.diag(alpha[:m]) + np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
+    return alpha[:m], beta[:m]
+
+
+def lanczos_extremes(matvec, n: int, steps: int, seed: int):
+    """Lanczos with full reorthogonalisation (Algorithm 1 step 1).
+
+    Returns (theta_min, res_min, theta_max, res_max): the extreme Ritz values of
+    the tridiagonal T and their residual norms beta_m |s_{m,i}|.
+    """
+    alpha, beta = lanczos_tridiagonal(matvec, n, steps, seed)
+    m = alpha.shape[0]
+    T = np.diag(alpha) + np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
     theta, S = np.linalg.eigh(T)
     res = abs(beta[m - 1]) * np.abs(S[m - 1, :])
     return theta[0], res[0], theta[-1], res[-1]

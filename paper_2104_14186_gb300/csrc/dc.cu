@@ -1,7 +1,9 @@
 // Symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG, Section 3.2).
 //
 // A node holds a symmetric matrix M (order nl) whose spectrum lies in [lo, hi].  It picks a
-// split point sigma (the mean eigenvalue, trace / nl), computes the polar factor U_p of
+// split point sigma near the median of its spectrum (a midpoint of Gauss quadrature nodes of
+// 30 Lanczos steps on M; then the mean eigenvalue trace / nl and the middle of [lo, hi] if a
+// split is one-sided or leaves an eigenvalue unresolved), computes the polar factor U_p of
 // (M - sigma I) / alpha with alpha = max(sigma - lo, hi - sigma) >= ||M - sigma I||_2 by QDWH
 // (eqs. practical-polar-qr / practical-polar-chol, ell_0 = kDcEll0, so QR-based steps first),
 // and forms the projector P = (I + U_p) / 2 onto the eigenvectors with eigenvalues above sigma
@@ -28,6 +30,9 @@ namespace qdwhp {
 namespace {
 
 constexpr uint64_t kStreamSplit = 0x44435350ull;   // "DCSP"
+constexpr uint64_t kStreamSlq = 0x44435351ull;     // "DCSQ"
+constexpr int kSlqSteps = 30;
+constexpr double kUnresolved = 0.05;
 constexpr double kJacobiTightDc = 4.5e-16;
 constexpr double kJacobiValues = 1e-9;
 constexpr int kMaxDepth = 64;
@@ -125,35 +130,66 @@ qdwhp_status node(Ctx& c, int64_t c0, int64_t nl, size_t moff, double lo, double
   // a leaf, a (numerically) single point, or a runaway recursion: Jacobi
   if (nl <= kDcLeaf || hi - lo <= 1e-14 * c.scale || depth >= kMaxDepth) return leaf(c, c0, nl, moff, lo, hi);
 
-  // split point: the mean eigenvalue
+  // Split point: near the median of the spectrum, from the Gauss quadrature of a short
+  // Lanczos run on M (Golub-Welsch), so that graded spectra split evenly.  A candidate is
+  // kept when its split is two-sided and resolved: P = (I + U_p) / 2 is a projector to
+  // rounding, trace(P) - ||P||_F^2 = sum p (1 - p) <= kUnresolved (an eigenvalue within the
+  // polar resolution ell_0 of sigma gives p ~ 1/2).  Otherwise the next candidate: the mean
+  // eigenvalue trace(M) / nl, then the middle of [lo, hi].
+  const uint64_t slq_seed = c.seed ^ kStreamSlq ^ ((uint64_t)(c.node_counter + 1) * 0xD1B54A32D192ED03ull);
+  QDWHP_TRY(lanczos(st, false, nl, nl, Mn, nl, kSlqSteps, slq_seed, w.lws, w.lst));
+  QDWHP_TRY(quadrature_median(st, w.lst, w.scal + 4));
   diag_sum_kernel<<<1, 1024, 0, st>>>((int)nl, Mn, nl, w.scal);
   QDWHP_LAUNCH_CHECK();
-  double tr = 0.0;
-  QDWHP_TRY(read_scalar(st, w.scal, &tr));
-  double sigma = tr / (double)nl;
-  sigma = std::min(std::max(sigma, lo), hi);
-  const double alpha = std::max(sigma - lo, hi - sigma) + 1e-12 * c.scale;
-
-  // polar factor of (M - sigma I) / alpha
-  QDWHP_TRY(axpby(st, nl, nl, 1.0 / alpha, Mn, nl, 0.0, w.X, nl, -sigma / alpha));
-  QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
-  int n_qr = 0, n_chol = 0, n_f32 = 0;
-  QDWHP_TRY(run_schedule(st, nl, nl, w.X, nl, c.sched, false, w.q, &n_qr, &n_chol, &n_f32));
-  c.stats->qdwh_steps += n_qr + n_chol;
-  // P = (I + U_p) / 2, symmetrised
-  QDWHP_TRY(symmetrize_avg(st, nl, w.X, nl));
-  QDWHP_TRY(axpby(st, nl, nl, 0.5, w.X, nl, 0.0, w.X, nl, 0.5));
-  diag_sum_kernel<<<1, 1024, 0, st>>>((int)nl, w.X, nl, w.scal + 1);
-  QDWHP_LAUNCH_CHECK();
-  int fail = 0;
-  QDWHP_CUDA_TRY(cudaMemcpyAsync(&fail, w.q.fail, sizeof(int), cudaMemcpyDeviceToHost, st));
-  double trP = 0.0;
-  QDWHP_TRY(read_scalar(st, w.scal + 1, &trP));
-  if (fail) return QDWHP_ERR_BREAKDOWN;
-  if (!std::isfinite(trP)) return QDWHP_ERR_NONFINITE;
-  const int64_t r = std::min<int64_t>(nl, std::max<int64_t>(0, std::llround(trP)));
-  // Every eigenvalue on one side means all lie within the polar resolution of the mean:
-  // a cluster, which Jacobi settles at once.
+  double sc[6];
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(sc, w.scal, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+  double cand[3];
+  int ncand = 0;
+  const bool have_median = sc[5] > 0.0 && std::isfinite(sc[4]);
+  if (have_median) cand[ncand++] = sc[4];
+  cand[ncand++] = sc[0] / (double)nl;
+  cand[ncand++] = 0.5 * (lo + hi);
+  double sigma = 0.0, alpha = 0.0;
+  int64_t r = 0;
+  for (int ci = 0; ci < ncand; ++ci) {
+    sigma = std::min(std::max(cand[ci], lo), hi);
+    alpha = std::max(sigma - lo, hi - sigma) + 1e-12 * c.scale;
+    // polar factor of (M - sigma I) / alpha
+    QDWHP_TRY(axpby(st, nl, nl, 1.0 / alpha, Mn, nl, 0.0, w.X, nl, -sigma / alpha));
+    QDWHP_CUDA_TRY(cudaMemsetAsync(w.q.fail, 0, sizeof(int), st));
+    int n_qr = 0, n_chol = 0, n_f32 = 0;
+    QDWHP_TRY(run_schedule(st, nl, nl, w.X, nl, c.sched, false, w.q, &n_qr, &n_chol, &n_f32));
+    c.stats->qdwh_steps += n_qr + n_chol;
+    // P = (I + U_p) / 2, symmetrised
+    QDWHP_TRY(symmetrize_avg(st, nl, w.X, nl));
+    QDWHP_TRY(axpby(st, nl, nl, 0.5, w.X, nl, 0.0, w.X, nl, 0.5));
+    diag_sum_kernel<<<1, 1024, 0, st>>>((int)nl, w.X, nl, w.scal + 1);
+    QDWHP_LAUNCH_CHECK();
+    int fail = 0;
+    QDWHP_CUDA_TRY(cudaMemcpyAsync(&fail, w.q.fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    double trP = 0.0;
+    QDWHP_TRY(read_scalar(st, w.scal + 1, &trP));
+    if (fail) return QDWHP_ERR_BREAKDOWN;
+    if (!std::isfinite(trP)) return QDWHP_ERR_NONFINITE;
+    r = std::min<int64_t>(nl, std::max<int64_t>(0, std::llround(trP)));
+    if (r > 0 && r < nl) {
+      sumsq_parts_kernel<<<kDiffParts, 256, 0, st>>>((int)nl, (int)nl, w.X, nl, w.parts);
+      QDWHP_LAUNCH_CHECK();
+      QDWHP_TRY(reduce_parts(st, w.parts, kDiffParts, w.scal + 3));
+      double p2 = 0.0;
+      QDWHP_TRY(read_scalar(st, w.scal + 3, &p2));
+      if (!std::isfinite(p2)) return QDWHP_ERR_NONFINITE;
+      if (trP - p2 <= kUnresolved) {
+        if (ci == 0 && have_median) c.stats->median_splits += 1;
+        break;
+      }
+      c.stats->unresolved_splits += 1;
+    }
+    r = 0;
+  }
+  // No candidate split two-sidedly and resolved: the eigenvalues lie within the polar
+  // resolution of every candidate, a cluster, which Jacobi settles at once.
   if (r == 0 || r == nl) return leaf(c, c0, nl, moff, lo, hi);
   c.stats->nodes += 1;
   c.stats->depth = std::max(c.stats->depth, depth + 1);
@@ -211,6 +247,8 @@ void carve_dc_own(Arena& ar, int64_t cap, DcWs& w) {
   w.scal = ar.take<double>(8);
   w.parts = ar.take<double>(kDiffParts);
   w.jst = ar.take<JacobiState>(1);
+  w.lst = ar.take<LanczosState>(1);
+  w.lws = ar.take<double>(lanczos_ws_elems(cap, cap, kSlqSteps));
 }
 
 void carve_dc(Arena& ar, int64_t cap, DcWs& w) {
@@ -329,6 +367,7 @@ qdwhp_status syev_impl(const double* A, int64_t n, int64_t lda, double* lambda, 
     info->jacobi_sweeps = stats.jacobi_sweeps;
     info->max_offblock = stats.max_offblock;
     info->ms_total = ms;
+    info->median_splits = stats.median_splits;
   }
   return QDWHP_OK;
 }

@@ -32,6 +32,8 @@ struct DcWs {
   double* scal = nullptr;    // device scalars
   double* parts = nullptr;   // kDiffParts partial sums
   JacobiState* jst = nullptr;
+  LanczosState* lst = nullptr;   // split-point estimate: Lanczos on the node matrix
+  double* lws = nullptr;
 };
 
 // Carves every buffer of w for problems up to order cap.
@@ -48,6 +50,8 @@ struct DcStats {
   int refinements = 0;     // extra subspace-iteration passes (off-diagonal block above tolerance)
   int jacobi_sweeps = 0;   // largest leaf sweep count
   double max_offblock = 0; // largest ||Q2^T M Q1||_F / ||M - sigma I||_2 accepted
+  int median_splits = 0;   // splits made at the quadrature estimate of the median
+  int unresolved_splits = 0; // candidate split points rejected: eigenvalues within the polar resolution
 };
 
 // Eigendecomposition of the symmetric n x n matrix held in w.M (ld n; destroyed), whose

@@ -138,6 +138,7 @@ qdwhp_status gesvd_impl(const double* A, int64_t m, int64_t n, int64_t lda, doub
   inf->depth = stats.depth;
   inf->jacobi_sweeps = stats.jacobi_sweeps;
   inf->max_offblock = stats.max_offblock;
+  inf->median_splits = stats.median_splits;
 
   // sigma = |lambda| descending; V unsigned, U = U_p (V sign(lambda))
   abs_sign_kernel<<<ceil_div(n, 256), 256, 0, st>>>((int)n, w.lam, w.absval, w.sgn);

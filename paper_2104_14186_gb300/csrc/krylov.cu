@@ -223,6 +223,105 @@ inline int grid1d(size_t total, int threads) {
   return (int)std::max<size_t>(1, std::min<size_t>((total + threads - 1) / threads, 16 * (size_t)kNumSMs));
 }
 
+// Split point of a spectrum from the Gauss quadrature of the Lanczos tridiagonal T
+// (Golub-Welsch: the nodes are the eigenvalues of T, the weights the squared first
+// components of its eigenvectors), which approximates the spectral distribution of the
+// operator seen from the start vector.  One thread: implicit symmetric tridiagonal QR with
+// the Wilkinson shift (Golub and Van Loan, Section 8.3), accumulating only the first row of
+// the eigenvector matrix.  With the nodes ascending and c_j the cumulative weights, j* is the
+// first node with c_j >= 1/2.  Ritz values converge onto clusters, so a node may coincide
+// with an eigenvalue; the candidates are therefore the midpoints next to theta_j*: of
+// theta_{j*-1} and theta_j* (predicted fraction at or below: c_{j*-1}) and of theta_j* and
+// theta_{j*+1} (predicted c_j*).
+// out[0] = the candidate whose prediction is nearer 1/2 among those strictly inside (0, 1),
+// out[1] = its prediction, or -1 when there is none (or T is not finite).
+__global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  out[0] = 0.0;
+  out[1] = -1.0;
+  if (stt->nonfinite) return;
+  const int m = max(1, min(stt->m, kMaxT));
+  double d[kMaxT], e[kMaxT], z[kMaxT];
+  for (int i = 0; i < m; ++i) {
+    d[i] = stt->alpha[i];
+    e[i] = i + 1 < m ? stt->beta[i] : 0.0;
+    z[i] = i == 0 ? 1.0 : 0.0;
+  }
+  const double eps = 0x1.0p-52;
+  int hi = m - 1;
+  for (int it = 0; hi > 0 && it < 30 * kMaxT; ++it) {
+    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+    // Wilkinson shift: the eigenvalue of the trailing 2 x 2 block nearer d[hi]
+    const double dd = 0.5 * (d[hi - 1] - d[hi]), b2 = e[hi - 1] * e[hi - 1];
+    const double mu = d[hi] - b2 / (dd + copysign(sqrt(dd * dd + b2), dd >= 0.0 ? 1.0 : -1.0));
+    double x = d[lo] - mu, y = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = hypot(x, y);
+      const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? y / r : 0.0;
+      if (k > lo) e[k - 1] = r;
+      const double a = d[k], b = e[k], cc = d[k + 1];
+      d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
+      d[k + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+      e[k] = c * s * (cc - a) + (c * c - s * s) * b;
+      if (k + 1 < hi) {
+        x = e[k];
+        y = s * e[k + 1];   // the bulge at (k, k + 2)
+        e[k + 1] *= c;
+      }
+      const double zk = z[k];
+      z[k] = c * zk + s * z[k + 1];
+      z[k + 1] = -s * zk + c * z[k + 1];
+    }
+  }
+  if (hi > 0) return;   // not converged: no estimate
+  // nodes ascending with their weights
+  double wsum = 0.0;
+  for (int i = 0; i < m; ++i) {
+    z[i] *= z[i];
+    wsum += z[i];
+  }
+  for (int i = 1; i < m; ++i) {
+    const double di = d[i], zi = z[i];
+    int j = i - 1;
+    for (; j >= 0 && d[j] > di; --j) {
+      d[j + 1] = d[j];
+      z[j + 1] = z[j];
+    }
+    d[j + 1] = di;
+    z[j + 1] = zi;
+  }
+  if (!(wsum > 0.0) || !isfinite(wsum)) return;
+  double cum = 0.0, prev = 0.0;
+  int js = m - 1;
+  for (int i = 0; i < m; ++i) {
+    prev = cum;
+    cum += z[i] / wsum;
+    if (cum >= 0.5) {
+      js = i;
+      break;
+    }
+  }
+  const double lo_cut = 1e-12, hi_cut = 1.0 - 1e-12;
+  double best = 0.0, best_pred = -1.0;
+  if (js > 0 && prev > lo_cut && prev < hi_cut) {
+    best = 0.5 * (d[js - 1] + d[js]);
+    best_pred = prev;
+  }
+  if (js + 1 < m && cum > lo_cut && cum < hi_cut && (best_pred < 0.0 || fabs(cum - 0.5) < fabs(best_pred - 0.5))) {
+    best = 0.5 * (d[js] + d[js + 1]);
+    best_pred = cum;
+  }
+  if (best_pred < 0.0 || !isfinite(best)) return;
+  out[0] = best;
+  out[1] = best_pred;
+}
+
 }  // namespace
 
 qdwhp_status gemv_t(cudaStream_t st, int64_t m, int64_t n, const double* A, int64_t lda, const double* x, double* y) {
@@ -295,6 +394,12 @@ qdwhp_status lanczos(cudaStream_t st, bool normal, int64_t m, int64_t n, const d
     QDWHP_LAUNCH_CHECK();
   }
   tridiag_extremes_kernel<<<1, 32, 0, st>>>(stt);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status quadrature_median(cudaStream_t st, const LanczosState* stt, double* out_dev) {
+  quadrature_median_kernel<<<1, 32, 0, st>>>(stt, out_dev);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

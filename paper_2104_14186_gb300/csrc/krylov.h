@@ -22,6 +22,10 @@ size_t lanczos_ws_elems(int64_t m, int64_t n, int steps);
 // normal == false: symmetric n x n A; normal == true: the operator A^T A of the m x n A.
 qdwhp_status lanczos(cudaStream_t st, bool normal, int64_t m, int64_t n, const double* A, int64_t lda, int steps,
                      uint64_t seed, double* ws, LanczosState* stt);
+// Split point near the median of the spectrum from the Gauss quadrature of the tridiagonal
+// a lanczos() run left in *stt (device): out_dev[0] = the point, out_dev[1] = the predicted
+// fraction of eigenvalues at or below it, -1 if no estimate.
+qdwhp_status quadrature_median(cudaStream_t st, const LanczosState* stt, double* out_dev);
 
 // ---- jacobi.cu ----
 struct JacobiState {

@@ -62,7 +62,7 @@ class SyevInfo(C.Structure):
     _fields_ = [
         ("nodes", C.c_int32), ("leaves", C.c_int32), ("depth", C.c_int32), ("qdwh_steps", C.c_int32),
         ("refinements", C.c_int32), ("jacobi_sweeps", C.c_int32), ("max_offblock", C.c_double),
-        ("ms_total", C.c_float),
+        ("ms_total", C.c_float), ("median_splits", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -73,11 +73,11 @@ class GesvdInfo(C.Structure):
     _fields_ = [
         ("it_qr", C.c_int32), ("it_chol", C.c_int32), ("nodes", C.c_int32), ("leaves", C.c_int32),
         ("depth", C.c_int32), ("jacobi_sweeps", C.c_int32), ("orthonormalized", C.c_int32),
-        ("reserved", C.c_int32), ("alpha", C.c_double), ("max_offblock", C.c_double), ("ms_total", C.c_float),
+        ("median_splits", C.c_int32), ("alpha", C.c_double), ("max_offblock", C.c_double), ("ms_total", C.c_float),
     ]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class QdwhpError(RuntimeError):

@@ -117,3 +117,25 @@ def test_syev_one_point_spectrum(Q, c):
     lam, V = lam.cpu().numpy(), V.cpu().numpy()
     assert np.max(np.abs(lam - c)) <= 1e-14 * max(1.0, abs(c))
     assert np.linalg.norm(V.T @ V - np.eye(n)) <= ORTH_TOL * n
+
+
+def test_syev_graded_splits_at_quadrature_median(Q):
+    """Eigenvalues log-spaced over 12 decades (n = 1500): the splits are made at the Lanczos
+    quadrature estimate of the median, depth 3 (at the mean eigenvalue each split peels off
+    ~12 % and the depth is 7); every eigenpair meets the tolerances."""
+    rng = np.random.default_rng(17)
+    lam = 10.0 ** (-12.0 * np.arange(1500) / 1499)
+    A = I.symmetric_with_spectrum(lam, rng)
+    l, V, info = Q.syev(dev(A))
+    check_full(A, lam, l, V)
+    assert info["median_splits"] >= 2 and info["depth"] <= 4, info
+
+
+def test_syev_two_point_spectrum(Q):
+    """Two eigenvalues, 100-fold and 900-fold: one split separates them exactly."""
+    rng = np.random.default_rng(19)
+    lam = np.concatenate([np.full(100, -0.5), np.full(900, 2.0)])
+    A = I.symmetric_with_spectrum(lam, rng)
+    l, V, info = Q.syev(dev(A))
+    check_full(A, lam, l, V)
+    assert info["nodes"] == 1, info

@@ -115,3 +115,51 @@ def test_qdwh_svd_rank_deficient_and_zero():
     s, U, V, info = O.full.qdwh_svd(np.zeros((30, 20)))
     assert np.all(s == 0.0) and info["zero"]
     assert np.array_equal(U, np.eye(30, 20)) and np.array_equal(V, np.eye(20))
+
+
+def test_quadrature_exact_to_degree_2m_minus_1():
+    """Gauss quadrature from m Lanczos steps integrates polynomials of degree <= 2m - 1
+    exactly against the spectral measure of the start vector: sum_j w_j theta_j^p =
+    q0^T A^p q0 (Golub-Welsch; a wrong weight vector or node set fails this)."""
+    from oracle.partial import STREAM_LANCZOS, lanczos_tridiagonal
+    from oracle.rng import uniform_pm1
+    rng = np.random.default_rng(2)
+    n, m, seed = 60, 6, 99
+    A = I.symmetric_with_spectrum(rng.uniform(-1.0, 2.0, n), rng)
+    al, be = lanczos_tridiagonal(lambda x: A @ x, n, m, seed)
+    theta, w = O.full.quadrature_nodes_weights(al, be)
+    q0 = uniform_pm1(seed ^ STREAM_LANCZOS, n)
+    q0 = q0 / np.linalg.norm(q0)
+    v = q0.copy()
+    for p in range(2 * m):
+        mom = q0 @ v
+        assert abs(np.sum(w * theta ** p) - mom) <= 1e-12 * max(1.0, np.sum(np.abs(w * theta ** p))), p
+        v = A @ v
+
+
+def test_quadrature_median_balances_graded_spectra():
+    """Sigma log-spaced over 12 decades: the mean splits 88/12, the quadrature estimate
+    far nearer the middle; a two-point spectrum gets a point strictly between its values."""
+    rng = np.random.default_rng(3)
+    lam = 10.0 ** (-12.0 * np.arange(1024) / 1023)
+    A = I.symmetric_with_spectrum(lam, rng)
+    s = O.full.quadrature_median(A)
+    assert np.mean(lam <= np.mean(lam)) > 0.85
+    assert 0.2 <= np.mean(lam <= s) <= 0.8
+    lam2 = np.concatenate([np.zeros(20), np.ones(180)])
+    s2 = O.full.quadrature_median(I.symmetric_with_spectrum(lam2, rng))
+    assert 0.0 < s2 < 1.0
+
+
+def test_unresolved_split_is_detected():
+    """A split point on a 30-fold eigenvalue: those directions sit within rounding (~1e-16)
+    of sigma, below the polar resolution ell_0 = 1e-15, so C has eigenvalues strictly inside
+    (0, 1) there and trace(C) - ||C||_F^2 = sum p (1 - p) is far above the 0.05 acceptance
+    bound (at most 30/4); a split point in a gap gives ~0."""
+    rng = np.random.default_rng(5)
+    lam = np.concatenate([rng.uniform(-1.0, -0.1, 50), np.full(30, 0.25), rng.uniform(0.5, 1.0, 40)])
+    A = I.symmetric_with_spectrum(lam, rng)
+    _, _, _, C = O.full.split(A, 0.25, 1.3)
+    assert 1.0 <= np.trace(C) - np.sum(C * C) <= 7.5 + 1e-9
+    _, _, _, C = O.full.split(A, 0.4, 1.45)
+    assert abs(np.trace(C) - np.sum(C * C)) <= 1e-10
