@@ -490,12 +490,21 @@ def run_gesvd(args):
     fl = info["it_qr"] * (2 * (2 * (m + n) * n * n - 2 * n ** 3 / 3) + 2 * m * n * n) \
         + info["it_chol"] * (3 * m * n * n + n ** 3 / 3) + 4 * m * n * n + 9 * n ** 3
     t = statistics.median(ms) / 1e3
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's definition of the result (the LAPACK SVD through numpy), timed once on the host
+        import oracle as O
+        t0 = time.perf_counter()
+        O.full.gesvd(p.A)
+        cpu = {"value": 1.0 / (time.perf_counter() - t0), "unit": "solves/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"1 full SVD of the {m}x{n} matrix (numpy/LAPACK FP64)"}
     print(json.dumps({"workload": f"QDWH-SVD, all {n} triplets of the {m}x{n} matrix (sigma log-spaced 1..1e-12)",
                       "precision": args.precision, "ms_median": 1e3 * t, "solves_per_s": 1 / t,
                       "paper_flop_tflops": fl / t / 1e12,
                       "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9 if prof["gemm_ms"] else None,
                       "gemm_share": prof["gemm_ms"] / sum(ms), "accuracy": acc,
-                      "info": {k: info[k] for k in ("it_qr", "it_chol", "nodes", "leaves", "depth",
+                      "cpu_baseline": cpu,
+                      "info": {k: info[k] for k in ("it_qr", "it_chol", "nodes", "leaves", "depth", "median_splits",
                                                     "jacobi_sweeps", "orthonormalized", "max_offblock")}}),
           flush=True)
 
