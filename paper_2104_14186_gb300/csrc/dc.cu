@@ -326,10 +326,10 @@ qdwhp_status syev_impl(const double* A, int64_t n, int64_t lda, double* lambda, 
   SyevWs w;
   carve_syev(ar, n, w);
   if (!ar.ok()) return QDWHP_ERR_NOMEM;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  QDWHP_CUDA_TRY(cudaEventCreate(&e0));
-  QDWHP_CUDA_TRY(cudaEventCreate(&e1));
-  QDWHP_CUDA_TRY(cudaEventRecord(e0, st));
+  EventPair ev;
+  QDWHP_CUDA_TRY(cudaEventCreate(&ev.e0));
+  QDWHP_CUDA_TRY(cudaEventCreate(&ev.e1));
+  QDWHP_CUDA_TRY(cudaEventRecord(ev.e0, st));
   QDWHP_CUDA_TRY(cudaMemsetAsync(w.nonfinite, 0, sizeof(unsigned), st));
   QDWHP_TRY(count_nonfinite(st, n, n, A, lda, w.nonfinite));
   unsigned nonfinite = 0;
@@ -352,12 +352,10 @@ qdwhp_status syev_impl(const double* A, int64_t n, int64_t lda, double* lambda, 
   QDWHP_TRY(select_sort(st, n, w.lam, 1.0, INFINITY, w.order, w.count));
   QDWHP_TRY(gather_values(st, n, w.lam, w.order, lambda));
   QDWHP_TRY(gather_columns(st, n, n, w.V, n, w.order, nullptr, V, ldv));
-  QDWHP_CUDA_TRY(cudaEventRecord(e1, st));
-  QDWHP_CUDA_TRY(cudaEventSynchronize(e1));
+  QDWHP_CUDA_TRY(cudaEventRecord(ev.e1, st));
+  QDWHP_CUDA_TRY(cudaEventSynchronize(ev.e1));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   if (info) {
     info->nodes = stats.nodes;
     info->leaves = stats.leaves;

@@ -197,10 +197,10 @@ QDWHP_API qdwhp_status qdwhp_gesvd_f64(const double* A, int64_t m, int64_t n, in
   EmulationScope emu_scope(w.emu, w.emu_bytes);
   qdwhp_gesvd_info inf;
   memset(&inf, 0, sizeof(inf));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  QDWHP_CUDA_TRY(cudaEventCreate(&e0));
-  QDWHP_CUDA_TRY(cudaEventCreate(&e1));
-  QDWHP_CUDA_TRY(cudaEventRecord(e0, st));
+  EventPair ev;
+  QDWHP_CUDA_TRY(cudaEventCreate(&ev.e0));
+  QDWHP_CUDA_TRY(cudaEventCreate(&ev.e1));
+  QDWHP_CUDA_TRY(cudaEventRecord(ev.e0, st));
   qdwhp_status rc;
   if (m >= n) {
     rc = gesvd_impl(A, m, n, lda, sigma, U, ldu, V, ldv, w, &inf, st);
@@ -211,12 +211,10 @@ QDWHP_API qdwhp_status qdwhp_gesvd_f64(const double* A, int64_t m, int64_t n, in
   }
   if (rc == QDWHP_OK) {
     float ms = 0.f;
-    if (cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
-      cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaEventRecord(ev.e1, st) == cudaSuccess && cudaEventSynchronize(ev.e1) == cudaSuccess)
+      cudaEventElapsedTime(&ms, ev.e0, ev.e1);
     inf.ms_total = ms;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (info) *info = inf;
   return rc;
 }

@@ -7,6 +7,18 @@ namespace qdwhp {
 
 enum Uplo { FULL = 0, LOWER = 1 };
 
+// The two timing events of an entry point, destroyed on every return path.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 // ---- gemm.cu ----
 // C = alpha op(A) op(B) + beta C (+ diag_add on the diagonal), FP64 DMMA tiles.
 // uplo == LOWER computes and writes only the lower triangle of C (SYRK use).
