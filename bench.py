@@ -519,6 +519,17 @@ def run_batched(args):
     from paper_2104_14186_gb300 import inputs as I
     from paper_2104_14186_gb300 import qdwhp as Q
 
+    tuning = None
+    if args.tune:
+        # launch-shape table: reuse a saved one, else tune on this device and save it
+        from paper_2104_14186_gb300 import autotune
+        if os.path.exists(args.tune):
+            res = autotune.load(args.tune)
+        else:
+            res = autotune.tune()
+            autotune.save(res, args.tune)
+        autotune.apply(res)
+        tuning = {"table": res["table"], "path": args.tune}
     sizes = I.batch_sizes(args.count, 4000)
     As = [I.eig_uniform_device(int(n), 4000 + i, 0.10)[0] for i, n in enumerate(sizes)]
     prec = precision_code(Q, args.precision)
@@ -544,7 +555,7 @@ def run_batched(args):
     print(json.dumps({"workload": f"batched QDWHpartial-EIG: {args.count} matrices, n in [64, 1024], top 10 %",
                       "precision": args.precision, "zolo_r": args.zolo, "concurrency": args.concurrency,
                       "solves_per_s": args.count / t, "ms_per_batch": 1e3 * t, "alg_tflops_lower_bound": fl / t / 1e12,
-                      "max_lam_err": worst_lam, "max_resid": worst_res}), flush=True)
+                      "max_lam_err": worst_lam, "max_resid": worst_res, "tuning": tuning}), flush=True)
 
 
 def run_serve(args):
@@ -634,6 +645,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "mixed", "emulated", "mixed-emulated"], default="fp64")
     ap.add_argument("--refine", type=int, default=0, help="FP64 refinement steps on Q2 (SVD)")
+    ap.add_argument("--tune", default=None,
+                    help="batched: launch-shape table (JSON) to load, or to tune on this device and write")
     ap.add_argument("--zolo", type=int, default=0, help="Zolo-PD of order r in place of the QDWH steps (0: QDWH)")
     ap.add_argument("--kernel", choices=["gemm"], default=None,
                     help="time one building block in isolation instead of the full solve")

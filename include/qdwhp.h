@@ -213,6 +213,22 @@ QDWHP_API qdwhp_status qdwhp_gesvd_f64(const double* A, int64_t m, int64_t n, in
                                        double* sigma, double* U, int64_t ldu, double* V, int64_t ldv,
                                        void* workspace, size_t ws_bytes, qdwhp_gesvd_info* info, void* stream);
 
+/*
+ * Launch tuning (not part of the method): per size class (0: <= 128, 1: <= 256, 2: <= 512,
+ * 3: <= 1024, 4: larger) the library picks launch shapes from a table that the autotuner
+ * (paper_2104_14186_gb300/autotune.py) fills by timing solves.  Every value gives the same
+ * result; only the speed changes.  Knobs and their valid ranges:
+ *   0  rows per CTA of the cooperative Householder panel, by the panel's row count [16, 512] (64)
+ *   1  least warps per CTA of a Jacobi sweep, by the column count                  [1, 16]   (2)
+ *   2  CTAs per SM that split-K aims for, by max(m, n) of the product              [1, 8]    (2)
+ * qdwhp_tune_set returns QDWHP_ERR_ARG for an unknown knob or class or a value outside the
+ * range; qdwhp_tune_get returns -1 for an unknown knob or class.  The table is process-wide;
+ * set it before solves start (a solve reads it as it launches).
+ */
+QDWHP_API qdwhp_status qdwhp_tune_set(int32_t knob, int32_t size_class, int32_t value);
+QDWHP_API int32_t qdwhp_tune_get(int32_t knob, int32_t size_class);
+QDWHP_API void qdwhp_tune_reset(void);
+
 /* ---- Request queue (serving) and batched solves; not part of the paper's method ---- */
 
 /*

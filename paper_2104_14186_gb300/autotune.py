@@ -1,0 +1,94 @@
+"""Autotuner for the library's launch shapes (qdwhp_tune_set), per size class.
+
+The library reads three launch parameters from a per-size-class table (see include/qdwhp.h):
+the rows per CTA of the cooperative Householder panel, the least warps per CTA of a Jacobi
+sweep, and the CTAs per SM that split-K aims for.  Every value computes the same result, so
+tuning is a matter of timing.  For each class, smallest first, `tune` times a QDWHpartial-EIG
+solve (top 10 %, eigenvalues uniform in [-1, 1]) of a representative order on the device
+(CUDA events, median of `reps` solves after one warm-up) for every candidate of every knob
+in turn, keeping the fastest (coordinate descent), and returns the table.  Larger solves
+reach into smaller classes (their trailing panels and reduced problems), which is why the
+small classes are settled first.  `save`/`load` keep the table as JSON; `apply` installs it.
+"""
+
+from __future__ import annotations
+
+import json
+import statistics
+
+KNOBS = {
+    "panel_rows_per_cta": (0, (32, 64, 128, 256)),
+    "jacobi_min_warps": (1, (1, 2, 4, 8)),
+    "splitk_ctas_per_sm": (2, (1, 2, 4)),
+}
+# representative order of each size class (<= 128, <= 256, <= 512, <= 1024, larger)
+CLASS_ORDERS = (96, 192, 384, 768, 1536)
+
+
+def _time_solve(Q, A, k, reps: int) -> float:
+    import torch
+    Q.eig(A, k=k)
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Q.eig(A, k=k)
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def tune(classes=(0, 1, 2, 3, 4), reps: int = 5, seed: int = 5150) -> dict:
+    """Times the candidates on the current CUDA device; returns the table (and the timings)."""
+    from . import build
+    build.build()
+    from . import inputs as I
+    from . import qdwhp as Q
+
+    lib = Q.lib()
+    table = {name: [lib.qdwhp_tune_get(knob, c) for c in range(5)] for name, (knob, _) in KNOBS.items()}
+    log = []
+    for c in classes:
+        n = CLASS_ORDERS[c]
+        A, _, k = I.eig_uniform_device(n, seed + c, 0.10)
+        for name, (knob, cands) in KNOBS.items():
+            best_v, best_t = None, float("inf")
+            for v in cands:
+                if lib.qdwhp_tune_set(knob, c, v) != 0:
+                    continue
+                t = _time_solve(Q, A, k, reps)
+                log.append({"class": c, "n": n, "knob": name, "value": v, "ms": t})
+                if t < best_t:
+                    best_v, best_t = v, t
+            lib.qdwhp_tune_set(knob, c, best_v)
+            table[name][c] = best_v
+    return {"version": 1, "classes": ["<=128", "<=256", "<=512", "<=1024", ">1024"], "table": table, "log": log}
+
+
+def apply(result: dict) -> None:
+    """Installs a table produced by `tune` (or read by `load`)."""
+    from . import qdwhp as Q
+    lib = Q.lib()
+    for name, values in result["table"].items():
+        knob = KNOBS[name][0]
+        for c, v in enumerate(values):
+            if lib.qdwhp_tune_set(knob, c, int(v)) != 0:
+                raise ValueError(f"{name}[{c}] = {v} is outside the knob's range")
+
+
+def save(result: dict, path: str) -> None:
+    with open(path, "w") as f:
+        json.dump(result, f, indent=1)
+
+
+def load(path: str) -> dict:
+    with open(path) as f:
+        result = json.load(f)
+    if result.get("version") != 1 or set(result.get("table", {})) != set(KNOBS):
+        raise ValueError(f"{path} is not a version-1 tuning table")
+    for name, values in result["table"].items():
+        if len(values) != 5:
+            raise ValueError(f"{path}: {name} needs one value per size class")
+    return result

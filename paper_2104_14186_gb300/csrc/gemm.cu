@@ -233,7 +233,8 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
   int split = 1;
   const size_t mn = (size_t)M * N;
   if (splitk_ws != nullptr && tiles < kNumSMs && K >= 512 && mn <= kSplitMaxElems) {
-    split = (int)std::min<int64_t>((2 * kNumSMs + tiles - 1) / std::max<int64_t>(tiles, 1), K / 256);
+    const int64_t target = (int64_t)tune_value(kTuneSplitkPerSM, std::max(M, N)) * kNumSMs;
+    split = (int)std::min<int64_t>((target + tiles - 1) / std::max<int64_t>(tiles, 1), K / 256);
     split = std::min(split, kMaxSplit);
     while (split > 1 && (size_t)split * mn > splitk_ws_elems) --split;
     if (split < 1) split = 1;

@@ -7,6 +7,15 @@ namespace qdwhp {
 
 enum Uplo { FULL = 0, LOWER = 1 };
 
+// ---- tune.cu ----
+// Run-time launch parameters per size class (<= 128, <= 256, <= 512, <= 1024, larger),
+// set through qdwhp_tune_set by the autotuner.
+enum TuneKnob { kTunePanelRows = 0, kTuneJacobiWarps = 1, kTuneSplitkPerSM = 2 };
+constexpr int kTuneKnobs = 3;
+constexpr int kTuneClasses = 5;
+int tune_class(int64_t size);
+int tune_value(TuneKnob knob, int64_t size);
+
 // The two timing events of an entry point, destroyed on every return path.
 struct EventPair {
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -248,14 +248,14 @@ __global__ void __launch_bounds__(kSweepRegMaxThreads) jacobi_sweep_reg_kernel(i
 
 // Launch shape of a sweep: at most one CTA per SM (the budget of the cooperative-launch gate).
 // A pair is one warp's work, and an SM's FP64 pipe is the bottleneck once it holds a few
-// warps, so the pairs are first spread over the SMs at two warps each; only when there are
-// more pairs than that (long rounds) does a CTA take more warps, up to 16, to hide the
-// latency of the column loads.
+// warps, so the pairs are first spread over the SMs at min_warps each (2 unless tuned); only
+// when there are more pairs than that (long rounds) does a CTA take more warps, up to 16, to
+// hide the latency of the column loads.
 struct SweepShape {
   int grid;
   int threads;
 };
-SweepShape sweep_shape(int pairs, int max_threads) {
+SweepShape sweep_shape(int pairs, int max_threads, int min_warps) {
   static std::once_flag once;
   static int max_blocks = 0;
   std::call_once(once, [] {
@@ -264,7 +264,8 @@ SweepShape sweep_shape(int pairs, int max_threads) {
     max_blocks = sms;
   });
   const int max_warps = max_threads / 32;
-  const int warps = std::max(2, std::min(max_warps, (pairs + max_blocks - 1) / max_blocks));
+  const int least = std::max(1, std::min(max_warps, min_warps));
+  const int warps = std::max(least, std::min(max_warps, (pairs + max_blocks - 1) / max_blocks));
   const int grid = std::max(1, std::min(max_blocks, (pairs + warps - 1) / warps));
   return {grid, warps * 32};
 }
@@ -351,7 +352,7 @@ qdwhp_status jacobi_onesided(cudaStream_t st, int64_t mg, int64_t nc, double* G,
     fn = (const void*)jacobi_sweep_reg_kernel<16>;
   }
   if (len <= 512) max_threads = kSweepRegMaxThreads;
-  const SweepShape shape = sweep_shape(N / 2, max_threads);
+  const SweepShape shape = sweep_shape(N / 2, max_threads, tune_value(kTuneJacobiWarps, nc));
   // Converged when the largest normalised inner product of a sweep is <= tol, or, once it
   // is below sqrt(mg) u (the level of a plain dot product's rounding), when a sweep no
   // longer reduces it by 4x: rotations of that size only stir rounding noise.

@@ -35,7 +35,6 @@ constexpr int NBO = kQROuter;      // outer block width (256 = 8 panels)
 constexpr size_t kQRSplitCap = size_t(4) << 20;   // split-K scratch of the trailing products (doubles)
 constexpr int kPanelThreads = 256;
 constexpr int kPanelCTAs = 96;
-constexpr int kMinRowsPerCTA = 64;
 constexpr int kPartStride = NB + 1;
 
 struct PanelArgs {
@@ -231,8 +230,10 @@ __global__ void __launch_bounds__(kPanelThreads) panel_qr_kernel(PanelArgs a) {
   }
 }
 
+// CTAs of a panel of R rows: one per kTunePanelRows rows (64 unless tuned), at most kPanelCTAs.
 int panel_ctas(int R) {
-  int g = (R + kMinRowsPerCTA - 1) / kMinRowsPerCTA;
+  const int rows = tune_value(kTunePanelRows, R);
+  int g = (R + rows - 1) / rows;
   return std::max(1, std::min(g, kPanelCTAs));
 }
 

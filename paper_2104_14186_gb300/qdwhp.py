@@ -133,6 +133,9 @@ SIGNATURES = {
     "qdwhp_eig_batched": (C.c_int, [I64, C.POINTER(P), C.POINTER(I64), C.POINTER(I64), C.POINTER(Opts),
                                     C.POINTER(P), C.POINTER(P), C.POINTER(I64), C.c_int32, C.POINTER(C.c_int),
                                     C.POINTER(Info), P]),
+    "qdwhp_tune_set": (C.c_int, [C.c_int32, C.c_int32, C.c_int32]),
+    "qdwhp_tune_get": (C.c_int32, [C.c_int32, C.c_int32]),
+    "qdwhp_tune_reset": (None, []),
     "qdwhp_launch_count": (C.c_ulonglong, []),
     "qdwhp_profile_begin": (C.c_int, []),
     "qdwhp_profile_end": (C.c_int, [C.POINTER(D), C.POINTER(D), C.POINTER(I64)]),

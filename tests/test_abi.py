@@ -143,3 +143,31 @@ def test_struct_offsets_match_c_compiler(tmp_path):
         assert int(got[cname]) == C.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_tuning_table_checks_and_roundtrip(lib, tmp_path):
+    """Launch-shape knobs: range checks, get/set/reset, and the autotuner's JSON table."""
+    from paper_2104_14186_gb300 import autotune
+    try:
+        assert [lib.qdwhp_tune_get(k, 2) for k in range(3)] == [64, 2, 2]
+        assert lib.qdwhp_tune_set(0, 2, 128) == 0 and lib.qdwhp_tune_get(0, 2) == 128
+        assert lib.qdwhp_tune_set(0, 2, 8) == -1          # below the panel's 16 rows per CTA
+        assert lib.qdwhp_tune_set(0, 2, 1024) == -1       # panel shared memory would pass 128 KB
+        assert lib.qdwhp_tune_set(1, 0, 17) == -1
+        assert lib.qdwhp_tune_set(2, 5, 2) == -1 and lib.qdwhp_tune_get(3, 0) == -1
+        res = {"version": 1, "classes": [], "table": {"panel_rows_per_cta": [32, 64, 64, 128, 256],
+                                                       "jacobi_min_warps": [4, 2, 2, 1, 1],
+                                                       "splitk_ctas_per_sm": [2, 2, 4, 1, 2]}}
+        path = str(tmp_path / "tune.json")
+        autotune.save(res, path)
+        got = autotune.load(path)
+        assert got["table"] == res["table"]
+        autotune.apply(got)
+        assert lib.qdwhp_tune_get(0, 4) == 256 and lib.qdwhp_tune_get(1, 0) == 4 and lib.qdwhp_tune_get(2, 2) == 4
+        bad = dict(res, table=dict(res["table"], jacobi_min_warps=[4, 2]))
+        autotune.save(bad, path)
+        with pytest.raises(ValueError):
+            autotune.load(path)
+    finally:
+        lib.qdwhp_tune_reset()
+    assert [lib.qdwhp_tune_get(k, 4) for k in range(3)] == [64, 2, 2]
