@@ -526,7 +526,9 @@ def run_batched(args):
         if os.path.exists(args.tune):
             res = autotune.load(args.tune)
         else:
-            res = autotune.tune()
+            # the batched workload's sizes (64..1024) and concurrency: tune its throughput
+            res = autotune.tune(classes=(0, 1, 2, 3), reps=2, objective="throughput", batch=32,
+                                concurrency=args.concurrency)
             autotune.save(res, args.tune)
         autotune.apply(res)
         tuning = {"table": res["table"], "path": args.tune}

@@ -3,10 +3,14 @@
 The library reads three launch parameters from a per-size-class table (see include/qdwhp.h):
 the rows per CTA of the cooperative Householder panel, the least warps per CTA of a Jacobi
 sweep, and the CTAs per SM that split-K aims for.  Every value computes the same result, so
-tuning is a matter of timing.  For each class, smallest first, `tune` times a QDWHpartial-EIG
-solve (top 10 %, eigenvalues uniform in [-1, 1]) of a representative order on the device
-(CUDA events, median of `reps` solves after one warm-up) for every candidate of every knob
-in turn, keeping the fastest (coordinate descent), and returns the table.  Larger solves
+tuning is a matter of timing.  For each class, smallest first, `tune` times QDWHpartial-EIG
+(top 10 %, eigenvalues uniform in [-1, 1]) at a representative order on the device for every
+candidate of every knob in turn, keeping the fastest (coordinate descent), and returns the
+table.  The objective is the use the table serves: "latency" times one solve at a time (CUDA
+events, median of `reps` after a warm-up); "throughput" times a batch of `batch` solves
+through qdwhp_eig_batched at `concurrency` worker streams (median wall time).  They disagree:
+alone, a solve is fastest with more, smaller panel CTAs, while 16 concurrent solves run
+faster with fewer, because their cooperative launches share the SMs.  Larger solves
 reach into smaller classes (their trailing panels and reduced problems), which is why the
 small classes are settled first.  `save`/`load` keep the table as JSON; `apply` installs it.
 """
@@ -40,8 +44,29 @@ def _time_solve(Q, A, k, reps: int) -> float:
     return statistics.median(out)
 
 
-def tune(classes=(0, 1, 2, 3, 4), reps: int = 5, seed: int = 5150) -> dict:
+def _time_batch(Q, A, batch: int, concurrency: int, reps: int) -> float:
+    import time
+
+    import torch
+    As = [A] * batch
+    Q.eig_batched(As[: max(1, concurrency)], 0.10, concurrency=concurrency)
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, sts = Q.eig_batched(As, 0.10, concurrency=concurrency)
+        torch.cuda.synchronize()
+        out.append(1e3 * (time.perf_counter() - t0))
+        if any(sts):
+            raise RuntimeError(f"a tuning solve failed: {sts}")
+    return statistics.median(out)
+
+
+def tune(classes=(0, 1, 2, 3, 4), reps: int = 5, seed: int = 5150, objective: str = "latency",
+         batch: int = 32, concurrency: int = 16) -> dict:
     """Times the candidates on the current CUDA device; returns the table (and the timings)."""
+    if objective not in ("latency", "throughput"):
+        raise ValueError("objective is 'latency' or 'throughput'")
     from . import build
     build.build()
     from . import inputs as I
@@ -58,13 +83,15 @@ def tune(classes=(0, 1, 2, 3, 4), reps: int = 5, seed: int = 5150) -> dict:
             for v in cands:
                 if lib.qdwhp_tune_set(knob, c, v) != 0:
                     continue
-                t = _time_solve(Q, A, k, reps)
+                t = _time_solve(Q, A, k, reps) if objective == "latency" else \
+                    _time_batch(Q, A, batch, concurrency, reps)
                 log.append({"class": c, "n": n, "knob": name, "value": v, "ms": t})
                 if t < best_t:
                     best_v, best_t = v, t
             lib.qdwhp_tune_set(knob, c, best_v)
             table[name][c] = best_v
-    return {"version": 1, "classes": ["<=128", "<=256", "<=512", "<=1024", ">1024"], "table": table, "log": log}
+    return {"version": 1, "objective": objective, "classes": ["<=128", "<=256", "<=512", "<=1024", ">1024"],
+            "table": table, "log": log}
 
 
 def apply(result: dict) -> None:
