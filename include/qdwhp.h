@@ -118,8 +118,13 @@ QDWHP_API int64_t qdwhp_k_from_fraction(int64_t n, double fraction);
  *   lambda: k doubles, ordered largest-first (LARGEST) or smallest-first (SMALLEST).
  *   V:      n x k, leading dimension ldv >= n, orthonormal eigenvectors (signs unspecified).
  *   workspace/ws_bytes: device scratch of at least qdwhp_eig_workspace_bytes(n, opts).
- * k comes from opts->count or opts->fraction.  Returns QDWHP_ERR_COUNT if fewer than
- * k pairs are captured after opts->max_retries widenings of the threshold.
+ * k comes from opts->count or opts->fraction.  A spectrum that is one point to rounding
+ * (n = 1, c I, the zero matrix) returns the first k unit vectors and their Rayleigh quotients.
+ * Errors: QDWHP_ERR_COUNT if fewer than k pairs are captured after opts->max_retries
+ * widenings of the threshold; QDWHP_ERR_NONFINITE (A holds NaN/Inf); QDWHP_ERR_BREAKDOWN
+ * (a Cholesky-based step failed); QDWHP_ERR_NOT_CONVERGED (the reduced-problem Jacobi hit
+ * opts->jacobi_max_sweeps); QDWHP_ERR_ARG for invalid options (nothing launched).
+ * Synchronises `stream` (bounds, threshold, ell, counts).
  */
 QDWHP_API size_t qdwhp_eig_workspace_bytes(int64_t n, const qdwhp_opts* opts);
 QDWHP_API qdwhp_status qdwhp_eig(const double* A, int64_t n, int64_t lda, const qdwhp_opts* opts,
@@ -132,6 +137,9 @@ QDWHP_API qdwhp_status qdwhp_eig(const double* A, int64_t n, int64_t lda, const 
  *   k: wanted count (0 = take it from opts->count / opts->fraction of min(m, n)).
  *   sigma: k doubles, descending.  U: m x k (ldu >= m).  V: n x k (ldv >= n).
  *   workspace/ws_bytes: at least qdwhp_svd_workspace_bytes(m, n, opts).
+ * The zero matrix returns sigma = 0 with the first k unit vectors as U and V.
+ * Errors: as for qdwhp_eig; QDWHP_ERR_COUNT also when k exceeds the number of nonzero
+ * singular values (only sigma >= s alpha > 0 are kept, Algorithm 2 step 7).
  */
 QDWHP_API size_t qdwhp_svd_workspace_bytes(int64_t m, int64_t n, const qdwhp_opts* opts);
 QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t lda, int64_t k,
@@ -142,11 +150,12 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
 /*
  * Full symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG,
  * Section 3.2, eq. pdeig): A - sigma I = U_p H, the projector (I + U_p) / 2 splits the
- * spectrum at sigma (the mean eigenvalue), and the two Rayleigh-Ritz blocks are split
- * again until they are small enough for one-sided Jacobi.  The split point is an estimate of
- * the median eigenvalue from the Gauss quadrature of 30 Lanczos steps on the block, or the
- * mean eigenvalue when that estimate has no interior point or splits one-sidedly.  The same solver handles the
- * Rayleigh-Ritz problems of qdwhp_eig when they are large.
+ * spectrum at sigma, and the two Rayleigh-Ritz blocks are split again until they are small
+ * enough (order <= 512) for one-sided Jacobi.  sigma is an estimate of the block's median
+ * eigenvalue (a midpoint between Gauss-quadrature nodes of 30 Lanczos steps on the block),
+ * kept when the split is two-sided and resolved (trace(P) - ||P||_F^2 <= 0.05); otherwise the
+ * mean eigenvalue, then the middle of the block's spectral interval.  The same solver handles
+ * the Rayleigh-Ritz problems of qdwhp_eig when they are large.
  *   A: n x n symmetric (both triangles stored; the average of A and A^T is used), lda >= n,
  *      never modified.
  *   lambda: n doubles, ascending.  V: n x n (ldv >= n), orthonormal eigenvectors in the
@@ -166,7 +175,7 @@ typedef struct {
   int32_t jacobi_sweeps;  /* largest sweep count of a leaf */
   double max_offblock;    /* largest ||Q2^T M Q1||_F / ||M - sigma I||_2 of a split */
   float ms_total;         /* device time (CUDA events) */
-  int32_t median_splits;  /* splits made at the Lanczos-quadrature median (the others at the mean) */
+  int32_t median_splits;  /* splits made at the quadrature median (the others at a fallback point) */
 } qdwhp_syev_info;
 QDWHP_API size_t qdwhp_syev_workspace_bytes(int64_t n);
 QDWHP_API qdwhp_status qdwhp_syev_f64(const double* A, int64_t n, int64_t lda, double* lambda, double* V,
