@@ -33,6 +33,10 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   zolo.*                 pinned: r = 1 equals the QDWH weights, Chebyshev alternation
                          (2r + 2 points), composition law, spectral-map identity of both
                          term forms, polar factor from the SVD, iteration counts
+  full.quadrature_median pinned: Gauss quadrature exact to degree 2m - 1, balance on a
+                         12-decade spectrum, interior point of a two-point spectrum; the
+                         unresolved-split measure trace(C) - ||C||_F^2 on a split at a
+                         30-fold eigenvalue
   full.qdwh_svd          pinned: constructed singular values (to 1e-12 relative decades),
                          m < n, rank-deficient and zero matrices, residual invariants
 """
