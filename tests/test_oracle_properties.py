@@ -1,0 +1,55 @@
+"""Property tests (hypothesis) of the rational maps at random ell and order r: the scaled
+Zolotarev function maps [ell, 1] into [Z(ell), 1] and takes the value 1 at x = 1; it is odd
+and increasing on [0, ell]; at r = 1 it is the QDWH map of Section 3.1; and the next bound
+Z(ell) exceeds ell (each iteration makes progress)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import zolo as Z
+
+hyp = pytest.importorskip("hypothesis")
+st = pytest.importorskip("hypothesis.strategies")
+
+ELL = st.floats(min_value=1e-5, max_value=0.98)
+ORDER = st.integers(min_value=1, max_value=8)
+
+
+@hyp.settings(max_examples=60, deadline=None)
+@hyp.given(ell=ELL, r=ORDER)
+def test_zolotarev_maps_interval_into_itself(ell, r):
+    c, a, M = Z.zolo_coeffs(ell, r)
+    x = np.geomspace(ell, 1.0, 2001)
+    f = Z.zolo_map(x, c, M)
+    z_ell = float(Z.zolo_map(ell, c, M))
+    assert abs(float(Z.zolo_map(1.0, c, M)) - 1.0) <= 1e-13
+    assert np.all(f <= 1.0 + 1e-12) and np.all(f >= z_ell - 1e-12)
+    assert z_ell > ell
+    # odd, increasing below ell
+    y = np.linspace(0.0, ell, 200)
+    g = Z.zolo_map(y, c, M)
+    assert np.all(np.diff(g) >= -1e-15) and np.allclose(Z.zolo_map(-y, c, M), -g, atol=1e-15)
+    # partial fractions equal the product form
+    pf = M * x * (1.0 + sum(a[j] / (x * x + c[2 * j]) for j in range(r)))
+    assert np.max(np.abs(pf - f)) <= 1e-10
+
+
+@hyp.settings(max_examples=60, deadline=None)
+@hyp.given(ell=ELL)
+def test_order_one_is_qdwh(ell):
+    c, _, M = Z.zolo_coeffs(ell, 1)
+    a, b, cq, nxt = O.dwh_weights(ell)
+    x = np.geomspace(ell, 1.0, 101)
+    assert np.max(np.abs(Z.zolo_map(x, c, M) - O.rational_map(x, a, b, cq))) <= 1e-10
+    assert abs(float(Z.zolo_map(ell, c, M)) - nxt) <= 1e-10
+
+
+@hyp.settings(max_examples=40, deadline=None)
+@hyp.given(ell=ELL, r=st.integers(min_value=2, max_value=8))
+def test_higher_order_never_slower(ell, r):
+    """The best type (2r+1, 2r) approximation is at least as good as type (3, 2) composed
+    with nothing: Z_r(ell) >= Z_1(ell), so the bound after one iteration grows with r."""
+    c1, _, M1 = Z.zolo_coeffs(ell, 1)
+    cr, _, Mr = Z.zolo_coeffs(ell, r)
+    assert float(Z.zolo_map(ell, cr, Mr)) >= float(Z.zolo_map(ell, c1, M1)) - 1e-12
