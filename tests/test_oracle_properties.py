@@ -1,7 +1,12 @@
 """Property tests (hypothesis) of the rational maps at random ell and order r: the scaled
 Zolotarev function maps [ell, 1] into [Z(ell), 1] and takes the value 1 at x = 1; it is odd
 and increasing on [0, ell]; at r = 1 it is the QDWH map of Section 3.1; and the next bound
-Z(ell) exceeds ell (each iteration makes progress)."""
+Z(ell) exceeds ell (each iteration makes progress).
+
+The oracle's coefficients come from scipy's elliptic functions, whose error grows as the
+parameter 1 - ell^2 approaches 1: in the map it is about 1e-13 / ell (2.4e-9 at ell = 1e-5),
+which bounds the interval checks.  Where the map is flat to rounding (ell near 1, high r),
+its increments below ell are rounding noise of order 1e-15."""
 
 import numpy as np
 import pytest
@@ -20,16 +25,17 @@ ORDER = st.integers(min_value=1, max_value=8)
 @hyp.given(ell=ELL, r=ORDER)
 def test_zolotarev_maps_interval_into_itself(ell, r):
     c, a, M = Z.zolo_coeffs(ell, r)
+    tol = 1e-12 + 1e-13 / ell
     x = np.geomspace(ell, 1.0, 2001)
     f = Z.zolo_map(x, c, M)
     z_ell = float(Z.zolo_map(ell, c, M))
     assert abs(float(Z.zolo_map(1.0, c, M)) - 1.0) <= 1e-13
-    assert np.all(f <= 1.0 + 1e-12) and np.all(f >= z_ell - 1e-12)
+    assert np.all(f <= 1.0 + tol) and np.all(f >= z_ell - tol)
     assert z_ell > ell
     # odd, increasing below ell
     y = np.linspace(0.0, ell, 200)
     g = Z.zolo_map(y, c, M)
-    assert np.all(np.diff(g) >= -1e-15) and np.allclose(Z.zolo_map(-y, c, M), -g, atol=1e-15)
+    assert np.all(np.diff(g) >= -1e-14) and np.allclose(Z.zolo_map(-y, c, M), -g, atol=1e-15)
     # partial fractions equal the product form
     pf = M * x * (1.0 + sum(a[j] / (x * x + c[2 * j]) for j in range(r)))
     assert np.max(np.abs(pf - f)) <= 1e-10
