@@ -59,3 +59,38 @@ def test_higher_order_never_slower(ell, r):
     c1, _, M1 = Z.zolo_coeffs(ell, 1)
     cr, _, Mr = Z.zolo_coeffs(ell, r)
     assert float(Z.zolo_map(ell, cr, Mr)) >= float(Z.zolo_map(ell, c1, M1)) - 1e-12
+
+
+@hyp.settings(max_examples=25, deadline=None)
+@hyp.given(n=st.integers(min_value=24, max_value=90), frac=st.floats(min_value=0.04, max_value=0.5),
+           side=st.sampled_from(["largest", "smallest"]), zolo=st.sampled_from([0, 2]),
+           seed=st.integers(min_value=0, max_value=2 ** 31))
+def test_partial_eig_matches_lapack(n, frac, side, zolo, seed):
+    """QDWHpartial-EIG (QDWH or Zolo-PD steps) on random spectra against LAPACK eigh."""
+    from paper_2104_14186_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(-1.0, 1.0, n)
+    A = I.symmetric_with_spectrum(lam, rng)
+    k = I.k_from_fraction(n, frac)
+    r = O.qdwhp_eig(A, O.EigOptions(k=k, side=side, zolo_r=zolo))
+    ref = np.linalg.eigvalsh(A)
+    want = ref[::-1][:k] if side == "largest" else ref[:k]
+    m = O.eig_metrics(A, r.lam, r.V, want)
+    assert m["lam_err"] <= 1e-12 and m["orth"] <= 5e-15 * n and m["resid"] <= 1e-13, m
+
+
+@hyp.settings(max_examples=20, deadline=None)
+@hyp.given(m=st.integers(min_value=20, max_value=80), n=st.integers(min_value=20, max_value=80),
+           frac=st.floats(min_value=0.05, max_value=0.4), seed=st.integers(min_value=0, max_value=2 ** 31))
+def test_partial_svd_matches_lapack(m, n, frac, seed):
+    """QDWHpartial-SVD on random shapes (tall and wide) against the LAPACK SVD."""
+    from paper_2104_14186_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n))
+    k = I.k_from_fraction(min(m, n), frac)
+    r = O.qdwhp_svd(A, O.SvdOptions(k=k))
+    s = np.linalg.svd(A, compute_uv=False)
+    mt = O.svd_metrics(A, r.sigma, r.U, r.V, s[:k])
+    assert mt["sigma_err"] <= 1e-12, mt
+    assert mt["orthU"] <= 5e-15 * k + 1e-14 and mt["orthV"] <= 5e-15 * k + 1e-14, mt
+    assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-12, mt
