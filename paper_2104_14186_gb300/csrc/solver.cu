@@ -307,7 +307,8 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     QDWHP_TRY(zolo_schedule(st, o.s_eig, o.zolo_r, o.c_qr, w.c.zsched));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.zsched, w.c.zsched, sizeof(ZoloSchedule), cudaMemcpyDeviceToHost, st));
   } else {
-    QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, o.c_qr, w.c.sched));
+    // Cholesky-based in every iteration (Section 4.1; c_qr is the SVD's switch)
+    QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, INFINITY, w.c.sched));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.sched, w.c.sched, sizeof(Schedule), cudaMemcpyDeviceToHost, st));
   }
   double theta_k = 0.0;
