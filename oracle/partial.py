@@ -61,6 +61,8 @@ class EigOptions:
     max_retries: int = 2
     seed: int = 1234
     zolo_r: int = 0             # 0: QDWH steps; r >= 1: Zolo-PD of type (2r+1, 2r) until ell = 1
+    c_qr: float = 100.0         # Zolo-PD: a term is QR-formed when 1 / c_{2j-1} > c_qr (QDWH EIG steps
+                                # are Cholesky-based whatever c, Section 4.1)
 
 
 @dataclass
@@ -238,7 +240,7 @@ def polar_iterations(X: np.ndarray, ell0: float, zolo_r: int, fixed_iters: int |
 
 
 def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float, iters: int, tol: float,
-              zolo_r: int = 0):
+              zolo_r: int = 0, c_qr: float = 100.0):
     """Algorithm 1 steps 1-6 for B = A' - t I with A' = eps_side * A, whose
     wanted eigenvalues lie on [mu, 0], mu = lam_lo - t <= lambda_min(B)."""
     n = A.shape[0]
@@ -249,7 +251,7 @@ def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float,
     X[np.diag_indices(n)] -= (1.0 - s) * t / absmu + s
     # Step 2: QDWH iterations from ell_0 = s, Cholesky-based in all iterations (Section 4.1);
     # or Zolo-PD iterations.
-    X, sched, _ = polar_iterations(X, s, zolo_r, iters, math.inf if zolo_r == 0 else 100.0)
+    X, sched, _ = polar_iterations(X, s, zolo_r, iters, math.inf if zolo_r == 0 else c_qr)
     # Step 3: QR of (r(A~) + I) / 2.
     Bq = 0.5 * (X + np.eye(n))
     Qf, R = np.linalg.qr(Bq, mode="complete")
@@ -309,7 +311,8 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
 
     retries = 0
     while True:
-        theta, W, Q2, mu, info = _eig_core(A, eps_side, t, lam_lo, opts.s, opts.iters, opts.tol, opts.zolo_r)
+        theta, W, Q2, mu, info = _eig_core(A, eps_side, t, lam_lo, opts.s, opts.iters, opts.tol, opts.zolo_r,
+                                           opts.c_qr)
         lamp = eps_side * theta               # Ritz values of A'
         sel = np.nonzero(lamp <= t)[0]
         if sel.size >= k or retries >= opts.max_retries:

@@ -22,8 +22,10 @@ Freund, SIAM Review 58 (2016)):
 * ell_{k+1} = Z(ell_k); iterate until |ell - 1| < 5 eps, as for QDWH.
 
 The elliptic functions are scipy's (parameter m = ell'^2); K' uses ellipkm1(ell^2) so that
-it stays accurate for small ell.  ellipj loses accuracy as m -> 1, so this oracle is meant
-for ell >= 1e-6 (the partial solvers' thresholds on the test problems).
+it stays accurate for small ell.  ellipj loses accuracy as m -> 1: from ell = 1e-3 up the
+map is exact to rounding for r <= 8 (the coefficients to ~3e-11 relative at 1e-3), while at
+some smaller ell (1e-5, 1e-4) it is off by up to 1e-8.  The oracle is meant for ell >= 1e-3,
+the range of the partial solvers' thresholds on the test problems that compare against it.
 """
 
 from __future__ import annotations

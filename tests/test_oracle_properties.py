@@ -3,10 +3,11 @@ Zolotarev function maps [ell, 1] into [Z(ell), 1] and takes the value 1 at x = 1
 and increasing on [0, ell]; at r = 1 it is the QDWH map of Section 3.1; and the next bound
 Z(ell) exceeds ell (each iteration makes progress).
 
-The oracle's coefficients come from scipy's elliptic functions, whose error grows as the
-parameter 1 - ell^2 approaches 1: in the map it is about 1e-13 / ell (2.4e-9 at ell = 1e-5),
-which bounds the interval checks.  Where the map is flat to rounding (ell near 1, high r),
-its increments below ell are rounding noise of order 1e-15."""
+The oracle's coefficients come from scipy's elliptic functions.  For the parameter
+1 - ell^2 within ~1e-8 of 1 those switch to an expansion whose error reaches 1e-8 in the map
+at some ell (1e-5, 1e-4) and not at others, so the properties are drawn for ell >= 1e-3,
+where the map is exact to rounding for every r <= 8.  Where the map is flat to rounding
+(ell near 1, high r), its increments below ell are rounding noise of order 1e-15."""
 
 import numpy as np
 import pytest
@@ -17,7 +18,7 @@ from oracle import zolo as Z
 hyp = pytest.importorskip("hypothesis")
 st = pytest.importorskip("hypothesis.strategies")
 
-ELL = st.floats(min_value=1e-5, max_value=0.98)
+ELL = st.floats(min_value=1e-3, max_value=0.98)
 ORDER = st.integers(min_value=1, max_value=8)
 
 
@@ -25,7 +26,7 @@ ORDER = st.integers(min_value=1, max_value=8)
 @hyp.given(ell=ELL, r=ORDER)
 def test_zolotarev_maps_interval_into_itself(ell, r):
     c, a, M = Z.zolo_coeffs(ell, r)
-    tol = 1e-12 + 1e-13 / ell
+    tol = 1e-12
     x = np.geomspace(ell, 1.0, 2001)
     f = Z.zolo_map(x, c, M)
     z_ell = float(Z.zolo_map(ell, c, M))
@@ -66,13 +67,17 @@ def test_higher_order_never_slower(ell, r):
            side=st.sampled_from(["largest", "smallest"]), zolo=st.sampled_from([0, 2]),
            seed=st.integers(min_value=0, max_value=2 ** 31))
 def test_partial_eig_matches_lapack(n, frac, side, zolo, seed):
-    """QDWHpartial-EIG (QDWH or Zolo-PD steps) on random spectra against LAPACK eigh."""
+    """QDWHpartial-EIG (QDWH or Zolo-PD steps) on random spectra against LAPACK eigh.  Zolo-PD
+    runs with c_qr = 20: at r = 2 from ell_0 = 0.2 its first Cholesky-formed term has
+    condition up to (1 + c_1) / c_1 = 62 (QDWH's first step: 18.5), which left residuals up to
+    1.13e-13 on 300 random problems of this kind; with that term QR-formed the worst was
+    1.3e-14 (QDWH's 8.6e-14)."""
     from paper_2104_14186_gb300 import inputs as I
     rng = np.random.default_rng(seed)
     lam = rng.uniform(-1.0, 1.0, n)
     A = I.symmetric_with_spectrum(lam, rng)
     k = I.k_from_fraction(n, frac)
-    r = O.qdwhp_eig(A, O.EigOptions(k=k, side=side, zolo_r=zolo))
+    r = O.qdwhp_eig(A, O.EigOptions(k=k, side=side, zolo_r=zolo, c_qr=20.0))
     ref = np.linalg.eigvalsh(A)
     want = ref[::-1][:k] if side == "largest" else ref[:k]
     m = O.eig_metrics(A, r.lam, r.V, want)
