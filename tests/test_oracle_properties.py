@@ -86,14 +86,16 @@ def test_partial_eig_matches_lapack(n, frac, side, zolo, seed):
 
 @hyp.settings(max_examples=20, deadline=None)
 @hyp.given(m=st.integers(min_value=20, max_value=80), n=st.integers(min_value=20, max_value=80),
-           frac=st.floats(min_value=0.05, max_value=0.4), seed=st.integers(min_value=0, max_value=2 ** 31))
-def test_partial_svd_matches_lapack(m, n, frac, seed):
-    """QDWHpartial-SVD on random shapes (tall and wide) against the LAPACK SVD."""
+           frac=st.floats(min_value=0.05, max_value=0.4), zolo=st.sampled_from([0, 2]),
+           seed=st.integers(min_value=0, max_value=2 ** 31))
+def test_partial_svd_matches_lapack(m, n, frac, zolo, seed):
+    """QDWHpartial-SVD (QDWH or Zolo-PD steps) on random shapes, tall and wide, against the
+    LAPACK SVD."""
     from paper_2104_14186_gb300 import inputs as I
     rng = np.random.default_rng(seed)
     A = rng.standard_normal((m, n))
     k = I.k_from_fraction(min(m, n), frac)
-    r = O.qdwhp_svd(A, O.SvdOptions(k=k))
+    r = O.qdwhp_svd(A, O.SvdOptions(k=k, zolo_r=zolo))
     s = np.linalg.svd(A, compute_uv=False)
     mt = O.svd_metrics(A, r.sigma, r.U, r.V, s[:k])
     assert mt["sigma_err"] <= 1e-12, mt
