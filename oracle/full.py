@@ -10,10 +10,11 @@ C = (I + U_p) / 2 = V_+ V_+^T projects onto the eigenvectors with eigenvalues ab
 sigma; take orthonormal bases of range(C) and of its complement, project A on each
 (Rayleigh-Ritz) and recurse.  Readings (the paper does not fix them): the split point is
 an estimate of the median eigenvalue from the Gauss quadrature of 30 Lanczos steps on A
-(`quadrature_median`, a midpoint between two nodes), then the mean eigenvalue trace(A) / n
-and the middle of [lo, hi], the first whose split is two-sided and resolved
-(trace(C) - ||C||_F^2 <= 0.05, C being a projector to rounding); the polar decomposition
-starts from ell_0 = 1e-15
+(`quadrature_median`, a midpoint between two distinct nodes), then the mean eigenvalue
+trace(A) / n and the middle of [lo, hi], the first whose split is two-sided, resolved
+(trace(C) - ||C||_F^2 <= 0.05, C being a projector to rounding) and exact to rounding
+(||V2^T A V1||_F <= 64 eps sqrt(n) alpha); the polar decomposition starts from
+ell_0 = 1e-15
 (QR-based steps while c_k > 100), rank(C) = round(trace(C)), the bases come from
 Householder QR with column pivoting of C, and problems of order <= `leaf` go to the
 dense eigensolver.
@@ -46,6 +47,7 @@ ELL0_SPLIT = 1e-15
 ELL0_SVD = 1e-15
 ORTH_FIX_SVD = 1e-14
 UNRESOLVED = 0.05
+OFFBLOCK = 64 * 2.0 ** -52
 SLQ_STEPS = 30
 SLQ_SEED = 4242
 
@@ -91,13 +93,22 @@ def quadrature_median(A: np.ndarray, seed: int = SLQ_SEED):
     n = A.shape[0]
     alpha, beta = lanczos_tridiagonal(lambda x: A @ x, n, SLQ_STEPS, seed)
     theta, w = quadrature_nodes_weights(alpha, beta)
+    m = theta.shape[0]
     c = np.cumsum(w / np.sum(w))
-    j = int(min(np.searchsorted(c, 0.5), theta.shape[0] - 1))
+    j = int(min(np.searchsorted(c, 0.5), m - 1))
+    # two nodes may sit on one cluster: a midpoint is taken only between distinct nodes
+    sep = 1e-8 * max(theta[-1] - theta[0], np.max(np.abs(theta)), 1e-300)
     cands = []
-    if j > 0:
-        cands.append((0.5 * (theta[j - 1] + theta[j]), c[j - 1]))
-    if j + 1 < theta.shape[0]:
-        cands.append((0.5 * (theta[j] + theta[j + 1]), c[j]))
+    a = j - 1
+    while a >= 0 and theta[j] - theta[a] <= sep:
+        a -= 1
+    if a >= 0:
+        cands.append((0.5 * (theta[a] + theta[j]), c[a]))
+    b = j + 1
+    while b < m and theta[b] - theta[j] <= sep:
+        b += 1
+    if b < m:
+        cands.append((0.5 * (theta[j] + theta[b]), c[b - 1]))
     cands = [x for x in cands if 1e-12 < x[1] < 1.0 - 1e-12]
     if not cands:
         return None
@@ -117,7 +128,10 @@ def qdwh_eig(A: np.ndarray, lo: float, hi: float, leaf: int = 64):
         sigma = min(max(cand, lo), hi)
         alpha = max(sigma - lo, hi - sigma)
         r, V1, V2, C = split(A, sigma, alpha)
-        if 0 < r < n and np.trace(C) - np.sum(C * C) <= UNRESOLVED:
+        if not (0 < r < n and np.trace(C) - np.sum(C * C) <= UNRESOLVED):
+            continue
+        # the split's backward error, at the level of the rounding of the products
+        if np.linalg.norm(V2.T @ A @ V1) <= OFFBLOCK * np.sqrt(n) * alpha:
             break
     else:
         return np.linalg.eigh(A)

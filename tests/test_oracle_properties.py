@@ -101,3 +101,25 @@ def test_partial_svd_matches_lapack(m, n, frac, zolo, seed):
     assert mt["sigma_err"] <= 1e-12, mt
     assert mt["orthU"] <= 5e-15 * k + 1e-14 and mt["orthV"] <= 5e-15 * k + 1e-14, mt
     assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-12, mt
+
+
+@hyp.settings(max_examples=25, deadline=None)
+@hyp.given(n=st.integers(min_value=40, max_value=120), nrep=st.integers(min_value=0, max_value=30),
+           graded=st.booleans(), seed=st.integers(min_value=0, max_value=2 ** 31))
+def test_full_spectrum_recursion_matches_lapack(n, nrep, graded, seed):
+    """QDWH-EIG divide and conquer (leaf 16, so several levels) on random spectra, with an
+    nrep-fold eigenvalue and optionally graded over 8 decades, against LAPACK eigh: every
+    split point (quadrature median, mean or interval middle) must leave the recursion exact."""
+    from paper_2104_14186_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    lam = 10.0 ** rng.uniform(-8, 0, n) if graded else rng.uniform(-1.0, 1.0, n)
+    if nrep > 1:
+        lam[:min(nrep, n)] = lam[0]
+    A = I.symmetric_with_spectrum(lam, rng)
+    lo, hi = float(lam.min()) - 0.05, float(lam.max()) + 0.05
+    l, V = O.full.qdwh_eig(A, lo, hi, leaf=16)
+    o = np.argsort(l)
+    l, V = l[o], V[:, o]
+    assert np.max(np.abs(l - np.sort(lam))) <= 1e-12 * np.max(np.abs(lam))
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 5e-15 * n
+    assert np.linalg.norm(A @ V - V * l) <= 1e-13 * np.linalg.norm(A)
