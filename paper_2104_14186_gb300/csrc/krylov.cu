@@ -230,9 +230,9 @@ inline int grid1d(size_t total, int threads) {
 // the Wilkinson shift (Golub and Van Loan, Section 8.3), accumulating only the first row of
 // the eigenvector matrix.  With the nodes ascending and c_j the cumulative weights, j* is the
 // first node with c_j >= 1/2.  Ritz values converge onto clusters, so a node may coincide
-// with an eigenvalue; the candidates are therefore the midpoints next to theta_j*: of
-// theta_{j*-1} and theta_j* (predicted fraction at or below: c_{j*-1}) and of theta_j* and
-// theta_{j*+1} (predicted c_j*).
+// with an eigenvalue; the candidates are therefore midpoints beside theta_j*, between it and
+// the nearest nodes below and above that differ from it by more than 1e-8 of the nodes'
+// scale (a, predicted fraction at or below: c_a; b, predicted c_{b-1}).
 // out[0] = the candidate whose prediction is nearer 1/2 among those strictly inside (0, 1),
 // out[1] = its prediction, or -1 when there is none (or T is not finite).
 __global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
@@ -297,25 +297,35 @@ __global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
     z[j + 1] = zi;
   }
   if (!(wsum > 0.0) || !isfinite(wsum)) return;
-  double cum = 0.0, prev = 0.0;
-  int js = m - 1;
+  // cumulative weights; js = the first node at which they reach 1/2
+  double cw[kMaxT];
+  double acc = 0.0;
+  int js = -1;
   for (int i = 0; i < m; ++i) {
-    prev = cum;
-    cum += z[i] / wsum;
-    if (cum >= 0.5) {
-      js = i;
-      break;
-    }
+    acc += z[i] / wsum;
+    cw[i] = acc;
+    if (js < 0 && acc >= 0.5) js = i;
   }
+  if (js < 0) js = m - 1;
+  // Two nodes may sit on one cluster, and their midpoint is then the clustered eigenvalue:
+  // the neighbours taken are the nearest nodes that differ from theta_js by more than sep.
+  const double sep = 1e-8 * fmax(fmax(d[m - 1] - d[0], fmax(fabs(d[0]), fabs(d[m - 1]))), 1e-300);
+  int lo_i = js - 1;
+  while (lo_i >= 0 && d[js] - d[lo_i] <= sep) --lo_i;
+  int hi_i = js + 1;
+  while (hi_i < m && d[hi_i] - d[js] <= sep) ++hi_i;
   const double lo_cut = 1e-12, hi_cut = 1.0 - 1e-12;
   double best = 0.0, best_pred = -1.0;
-  if (js > 0 && prev > lo_cut && prev < hi_cut) {
-    best = 0.5 * (d[js - 1] + d[js]);
-    best_pred = prev;
+  if (lo_i >= 0 && cw[lo_i] > lo_cut && cw[lo_i] < hi_cut) {
+    best = 0.5 * (d[lo_i] + d[js]);
+    best_pred = cw[lo_i];
   }
-  if (js + 1 < m && cum > lo_cut && cum < hi_cut && (best_pred < 0.0 || fabs(cum - 0.5) < fabs(best_pred - 0.5))) {
-    best = 0.5 * (d[js] + d[js + 1]);
-    best_pred = cum;
+  if (hi_i < m) {
+    const double pu = cw[hi_i - 1];   // every node up to hi_i - 1 lies at or below the midpoint
+    if (pu > lo_cut && pu < hi_cut && (best_pred < 0.0 || fabs(pu - 0.5) < fabs(best_pred - 0.5))) {
+      best = 0.5 * (d[js] + d[hi_i]);
+      best_pred = pu;
+    }
   }
   if (best_pred < 0.0 || !isfinite(best)) return;
   out[0] = best;
