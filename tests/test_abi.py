@@ -171,3 +171,49 @@ def test_tuning_table_checks_and_roundtrip(lib, tmp_path):
     finally:
         lib.qdwhp_tune_reset()
     assert [lib.qdwhp_tune_get(k, 4) for k in range(3)] == [64, 2, 2]
+
+
+def test_autotuner_coordinate_descent_on_a_known_cost(monkeypatch):
+    """The tuner's search logic on the host, with the library and the timing replaced by a
+    known cost: per class and knob it must keep the candidate of least cost, knob by knob."""
+    from paper_2104_14186_gb300 import autotune
+
+    table = {(k, c): v for k in range(3) for c in range(5) for v in [(64, 2, 2)[k]]}
+
+    class FakeLib:
+        def qdwhp_tune_get(self, k, c):
+            return table[(k, c)]
+
+        def qdwhp_tune_set(self, k, c, v):
+            lo, hi = [(16, 512), (1, 16), (1, 8)][k]
+            if not lo <= v <= hi:
+                return -1
+            table[(k, c)] = v
+            return 0
+
+    class FakeQ:
+        @staticmethod
+        def lib():
+            return FakeLib()
+
+    best = {0: {0: 128, 1: 32, 2: 256, 3: 64}, 1: {0: 4, 1: 1, 2: 8, 3: 2}, 2: {0: 1, 1: 4, 2: 2, 3: 4}}
+
+    def cost(c):
+        # separable cost, minimal at `best`; the tuner must find it one knob at a time
+        return sum(abs(np.log2(table[(k, c)]) - np.log2(best[k][c])) for k in range(3)) + 1.0
+
+    import numpy as np
+    import sys
+    from paper_2104_14186_gb300 import inputs
+    monkeypatch.setattr(inputs, "eig_uniform_device", lambda n, seed, frac: (n, None, 1))
+    monkeypatch.setattr(autotune, "_time_solve", lambda Q, A, k, reps: cost(autotune.CLASS_ORDERS.index(A)))
+    import paper_2104_14186_gb300 as pkg
+    fake_build = type("FakeBuild", (), {"build": staticmethod(lambda: None)})
+    for name, mod in (("build", fake_build), ("qdwhp", FakeQ)):
+        monkeypatch.setattr(pkg, name, mod, raising=False)
+        monkeypatch.setitem(sys.modules, f"paper_2104_14186_gb300.{name}", mod)
+    res = autotune.tune(classes=(0, 1, 2, 3), reps=1)
+    for name, (k, _) in autotune.KNOBS.items():
+        for c in range(4):
+            assert res["table"][name][c] == best[k][c], (name, c, res["table"][name])
+        assert res["table"][name][4] == (64, 2, 2)[k]     # class 4 untouched
