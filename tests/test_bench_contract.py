@@ -43,3 +43,41 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert len(lines) == 1, out.stdout[-2000:]
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_clock_summary_flags_throttle_reasons():
+    """The clocks object of the bench line from nvidia-smi rows: median SM clock, max clock,
+    the throttle reasons seen Active, unparsable rows skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    s = bench.ClockSampler(0)
+    row = lambda sm, cap: [str(sm), "2070", "900.5", "0x0", "Not Active", "Not Active", "Not Active", cap]
+    s.rows = [row(2070, "Not Active"), row(1980, "Active"), row(2070, "Not Active"),
+              ["[N/A]", "[N/A]", "", "", "", "", "", ""]]
+    out = s.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s2 = bench.ClockSampler(0)
+    s2.rows = [[str(1500), "2070", "1", "0x1", "Active", "Not Active", "Active", "Not Active"]]
+    assert s2.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_emulated_roofline_counts_algorithmic_flops():
+    """The emulated-product roofline: 60 digit products of 2mnk (n(n+1)k for a lower SYRK)
+    per recorded product, over the summed launch time, against the BF16 peak."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FakeQ:
+        @staticmethod
+        def profile_records():
+            # m, n, k, lower, split (-1: emulated), ms
+            return [(4096.0, 4096.0, 4096.0, 0.0, -1.0, 10.0), (256.0, 256.0, 512.0, 1.0, -1.0, 0.5),
+                    (512.0, 512.0, 512.0, 0.0, 1.0, 3.0)]    # a native DMMA record: ignored
+
+    r = bench.emulated_roofline(FakeQ, 100.0, 2000.0)
+    fp64 = 2.0 * 4096 ** 3 + 256 * 257 * 512
+    assert r["launches"] == 2 and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 60 * fp64 / 10.5e-3 / 1e12) <= 1e-9 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 2000.0) <= 1e-12
+    assert abs(r["fp64_equivalent_tflops"] - fp64 / 10.5e-3 / 1e12) <= 1e-9 * r["fp64_equivalent_tflops"]
+    assert abs(r["share_of_step"] - 10.5 / 100.0) <= 1e-12
