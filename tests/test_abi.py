@@ -217,3 +217,20 @@ def test_autotuner_coordinate_descent_on_a_known_cost(monkeypatch):
         for c in range(4):
             assert res["table"][name][c] == best[k][c], (name, c, res["table"][name])
         assert res["table"][name][4] == (64, 2, 2)[k]     # class 4 untouched
+
+
+def test_info_dict_slices_schedule_by_iterations(lib):
+    """ell_k / conv hold one entry per polar iteration: QDWH steps (it_qr + it_chol) or, with
+    Zolo-PD, its iterations (it_qr and it_chol then count terms)."""
+    from paper_2104_14186_gb300 import qdwhp as Q
+    info = Q.Info()
+    info.it_qr, info.it_chol = 1, 5
+    for i in range(12):
+        info.ell_k[i] = 0.5 + i
+    assert len(info.as_dict()["ell_k"]) == 6
+    info.zolo_steps = 2
+    d = info.as_dict()
+    assert d["ell_k"] == [0.5, 1.5] and len(d["conv"]) == 2 and d["zolo_steps"] == 2
+    g = Q.GesvdInfo()
+    g.median_splits = 3
+    assert g.as_dict()["median_splits"] == 3 and "reserved" not in g.as_dict()
