@@ -22,6 +22,12 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   threshold_from_count   pinned: Cauchy interlacing (k eigenvalues beyond t)
   qdwhp_eig / qdwhp_svd  pinned: constructed spectra, brute-force Jacobi (n<=64),
                          LAPACK eigh/svd, Theorem 1 containment bound
+  extraction_qr          pinned: Theorem 1 containment bound with and without Omega; on a
+                         Kahan matrix (unpivoted diag(R) far above sigma_min) only the
+                         Omega form captures the null vector and its diag(R) tracks
+                         sigma_min(R11)
+  gaussian               pinned: Kolmogorov-Smirnov against the normal distribution,
+                         moments, independence of the Box-Muller pair
   subspace size ell      parity unpinned (several ell are correct; only final
                          outputs are compared)
   syev                   the definition (all eigenpairs); pinned: constructed
@@ -41,12 +47,13 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                          m < n, rank-deficient and zero matrices, residual invariants
 """
 
-from .rng import splitmix64, uniform_pm1  # noqa: F401
+from .rng import splitmix64, uniform_pm1, gaussian  # noqa: F401
 from .qdwh import dwh_weights, dwh_schedule, qdwh_chol_step, qdwh_qr_step, qdwh_polar, rational_map  # noqa: F401
 from .partial import (  # noqa: F401
     EigOptions, SvdOptions, EigResult, SvdResult,
     lanczos_extremes, lanczos_extremes_normal, threshold_from_count_eig, threshold_from_count_svd,
-    qdwhp_eig, qdwhp_svd, qdwhp_eig_negative, qdwhp_svd_threshold, index_from_diag,
+    qdwhp_eig, qdwhp_svd, qdwhp_eig_negative, qdwhp_svd_threshold, index_from_diag, extraction_qr,
+    gaussian_omega,
 )
 from .jacobi import jacobi_eig  # noqa: F401
 from .full import syev  # noqa: F401

@@ -40,11 +40,12 @@ import scipy.linalg as sla
 
 from .qdwh import dwh_schedule, qdwh_chol_step, qdwh_qr_step
 from .zolo import zolo_schedule, zolo_step
-from .rng import uniform_pm1
+from .rng import gaussian, uniform_pm1
 
-# Stream ids of the two random draws of the method (XORed into the user seed).
+# Stream ids of the random draws of the method (XORed into the user seed).
 STREAM_LANCZOS = 0x4C414E43   # "LANC"
 STREAM_BLOCK = 0x424C4F43     # "BLOC"
+STREAM_OMEGA = 0x4F4D4547     # "OMEG"
 
 
 @dataclass
@@ -61,8 +62,9 @@ class EigOptions:
     max_retries: int = 2
     seed: int = 1234
     zolo_r: int = 0             # 0: QDWH steps; r >= 1: Zolo-PD of type (2r+1, 2r) until ell = 1
-    c_qr: float = 100.0         # Zolo-PD: a term is QR-formed when 1 / c_{2j-1} > c_qr (QDWH EIG steps
-                                # are Cholesky-based whatever c, Section 4.1)
+    zolo_c_qr: float = 20.0     # Zolo-PD: a term is QR-formed when 1 / c_{2j-1} > zolo_c_qr (QDWH EIG
+                                # steps are Cholesky-based whatever c, Section 4.1)
+    use_omega: bool = False     # QR of (r(A~) + I) Omega / 2 with a Gaussian Omega (Section 4.1)
 
 
 @dataclass
@@ -77,6 +79,8 @@ class SvdOptions:
     max_retries: int = 2
     seed: int = 1234
     zolo_r: int = 0             # 0: QDWH steps; r >= 1: Zolo-PD of type (2r+1, 2r)
+    zolo_c_qr: float = 20.0     # Zolo-PD: a term is QR-formed when 1 / c_{2j-1} > zolo_c_qr
+    use_omega: bool = False     # QR of (I - r^T r) Omega with a Gaussian Omega (Section 4.1)
 
 
 @dataclass
@@ -218,15 +222,36 @@ def index_from_diag(R: np.ndarray, tol: float) -> int:
     return int(hits[0]) if hits.size else d.shape[0]
 
 
-def polar_iterations(X: np.ndarray, ell0: float, zolo_r: int, fixed_iters: int | None, c_qr: float):
+def gaussian_omega(n: int, seed: int) -> np.ndarray:
+    """The n x n Gaussian matrix Omega of Section 4.1 (the QR of B Omega is rank revealing with
+    high probability), entries N(0, 1/n) so that B Omega keeps B's unit scale and the index
+    tolerance means the same with and without it.  Column-major draw from the Box-Muller
+    transform of the SplitMix64 stream seed ^ STREAM_OMEGA."""
+    return gaussian(seed ^ STREAM_OMEGA, n * n).reshape((n, n), order="F") / math.sqrt(n)
+
+
+def extraction_qr(B: np.ndarray, tol: float, omega_seed: int | None = None):
+    """Steps 3-5 of Algorithms 1 and 2: the full Householder QR of B, or of B Omega with the
+    Gaussian Omega of Section 4.1 when omega_seed is given (rank revealing with high
+    probability), then the index rule on diag(R).  Returns (F, Q, R, ind): F is the matrix
+    factored, and Q2 = Q[:, ind:] (ell = n - ind columns) contains B's numerical null space
+    up to ||V0^T F||_2 / sigma_min(R11) (Theorem 1)."""
+    F = B if omega_seed is None else B @ gaussian_omega(B.shape[1], omega_seed)
+    Qf, R = np.linalg.qr(F, mode="complete")
+    return F, Qf, R, index_from_diag(R, tol)
+
+
+def polar_iterations(X: np.ndarray, ell0: float, zolo_r: int, fixed_iters: int | None, c_qr: float,
+                     zolo_c_qr: float = 20.0):
     """Step 2 of Algorithms 1 and 2: QDWH from ell0 (fixed_iters steps, or until |ell - 1| < 5 eps),
     QR-based while c_k > c_qr; or, with zolo_r >= 1, Zolo-PD iterations of type (2 zolo_r + 1,
-    2 zolo_r) until |ell - 1| < 5 eps.  Returns (X, schedule, number of QR-formed steps or terms)."""
+    2 zolo_r) until |ell - 1| < 5 eps, a term QR-formed when 1 / c_{2j-1} > zolo_c_qr.
+    Returns (X, schedule, number of QR-formed steps or terms)."""
     n_qr = 0
     if zolo_r > 0:
         sched = zolo_schedule(ell0, zolo_r)
         for c, a, M, _, _ in sched:
-            X, q = zolo_step(X, c, a, M, c_qr)
+            X, q = zolo_step(X, c, a, M, zolo_c_qr)
             n_qr += q
         return X, sched, n_qr
     sched = dwh_schedule(ell0, fixed_iters=fixed_iters)
@@ -240,7 +265,7 @@ def polar_iterations(X: np.ndarray, ell0: float, zolo_r: int, fixed_iters: int |
 
 
 def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float, iters: int, tol: float,
-              zolo_r: int = 0, c_qr: float = 100.0):
+              zolo_r: int = 0, zolo_c_qr: float = 20.0, omega_seed: int | None = None):
     """Algorithm 1 steps 1-6 for B = A' - t I with A' = eps_side * A, whose
     wanted eigenvalues lie on [mu, 0], mu = lam_lo - t <= lambda_min(B)."""
     n = A.shape[0]
@@ -251,24 +276,25 @@ def _eig_core(A: np.ndarray, eps_side: float, t: float, lam_lo: float, s: float,
     X[np.diag_indices(n)] -= (1.0 - s) * t / absmu + s
     # Step 2: QDWH iterations from ell_0 = s, Cholesky-based in all iterations (Section 4.1);
     # or Zolo-PD iterations.
-    X, sched, _ = polar_iterations(X, s, zolo_r, iters, math.inf if zolo_r == 0 else c_qr)
-    # Step 3: QR of (r(A~) + I) / 2.
+    X, sched, _ = polar_iterations(X, s, zolo_r, iters, math.inf, zolo_c_qr)
+    # Step 3: QR of (r(A~) + I) / 2, or of (r(A~) + I) Omega / 2 (Section 4.1); steps 4-5: index
+    # rule and trailing columns of Q.
     Bq = 0.5 * (X + np.eye(n))
-    Qf, R = np.linalg.qr(Bq, mode="complete")
-    # Steps 4-5: index rule and trailing columns of Q.
-    ind = index_from_diag(R, tol)
+    F, Qf, R, ind = extraction_qr(Bq, tol, omega_seed)
     Q2 = Qf[:, ind:]
     # Step 6: Rayleigh-Ritz on the original A, so the Ritz values need no rescaling (step 7).
     M = Q2.T @ (A @ Q2)
     M = 0.5 * (M + M.T)
     theta, W = np.linalg.eigh(M)
-    return theta, W, Q2, mu, {"sched": sched, "ind": ind, "B": Bq, "Q": Qf, "R": R}
+    return theta, W, Q2, mu, {"sched": sched, "ind": ind, "B": Bq, "F": F, "Q": Qf, "R": R}
 
 
-def qdwhp_eig_negative(A: np.ndarray, mu: float, s: float = 0.2, iters: int = 3, tol: float = 0.01):
+def qdwhp_eig_negative(A: np.ndarray, mu: float, s: float = 0.2, iters: int = 3, tol: float = 0.01,
+                       omega_seed: int | None = None):
     """Algorithm 1 as printed: the negative eigenpairs of A, given a lower bound
-    mu <= lambda_min(A) < 0.  Returns (lam ascending, V, info)."""
-    theta, W, Q2, _, info = _eig_core(A, 1.0, 0.0, mu, s, iters, tol)
+    mu <= lambda_min(A) < 0 (step 3 with the Gaussian Omega when omega_seed is given).
+    Returns (lam ascending, V, info)."""
+    theta, W, Q2, _, info = _eig_core(A, 1.0, 0.0, mu, s, iters, tol, omega_seed=omega_seed)
     sel = np.nonzero(theta < 0.0)[0]
     return theta[sel], Q2 @ W[:, sel], info
 
@@ -312,7 +338,7 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
     retries = 0
     while True:
         theta, W, Q2, mu, info = _eig_core(A, eps_side, t, lam_lo, opts.s, opts.iters, opts.tol, opts.zolo_r,
-                                           opts.c_qr)
+                                           opts.zolo_c_qr, opts.seed if opts.use_omega else None)
         lamp = eps_side * theta               # Ritz values of A'
         sel = np.nonzero(lamp <= t)[0]
         if sel.size >= k or retries >= opts.max_retries:
@@ -330,25 +356,23 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
 
 
 def qdwhp_svd_threshold(A: np.ndarray, s: float, alpha: float, tol: float = 0.01, c_qr: float = 100.0,
-                        zolo_r: int = 0):
+                        zolo_r: int = 0, omega_seed: int | None = None, zolo_c_qr: float = 20.0):
     """Algorithm 2 as printed, for m >= n: the singular triplets with sigma >= s alpha,
     alpha ~ ||A||_2.  Returns (sigma descending, U, V, info)."""
     n = A.shape[1]
     # Step 2: QDWH on A/alpha from ell_0 = s until |ell - 1| < 5 eps; QR-based steps
     # while c_k > c_qr (Section 4.2: the QR form for the first step when s is small).
-    X, sched, n_qr = polar_iterations(A / alpha, s, zolo_r, None, c_qr)
-    # Step 3: QR of I - r(A~)^T r(A~).
+    X, sched, n_qr = polar_iterations(A / alpha, s, zolo_r, None, c_qr, zolo_c_qr)
+    # Step 3: QR of I - r(A~)^T r(A~), or of (I - r^T r) Omega (Section 4.1); steps 4-5.
     Bq = np.eye(n) - X.T @ X
-    Qf, R = np.linalg.qr(Bq, mode="complete")
-    # Steps 4-5.
-    ind = index_from_diag(R, tol)
+    F, Qf, R, ind = extraction_qr(Bq, tol, omega_seed)
     Q2 = Qf[:, ind:]
     # Step 6: A Q2 with the unscaled A, and its SVD.
     C = A @ Q2
     Ut, St, Vtt = np.linalg.svd(C, full_matrices=False)
     # Step 7: the triplets above s ||A||_2; step 8: V1 = Q2 V~1.
     sel = np.nonzero(St >= s * alpha)[0]
-    info = {"sched": sched, "n_qr": n_qr, "ind": ind, "B": Bq, "Q": Qf, "R": R}
+    info = {"sched": sched, "n_qr": n_qr, "ind": ind, "B": Bq, "F": F, "Q": Qf, "R": R}
     return St[sel], Ut[:, sel], Q2 @ Vtt[sel, :].T, info
 
 
@@ -373,7 +397,8 @@ def qdwhp_svd(A: np.ndarray, opts: SvdOptions) -> SvdResult:
     s = max(sig_hat / alpha * (1.0 - 1e-10), opts.s_min)
     retries = 0
     while True:
-        sigma, U, V, info = qdwhp_svd_threshold(A, s, alpha, opts.tol, opts.c_qr, opts.zolo_r)
+        sigma, U, V, info = qdwhp_svd_threshold(A, s, alpha, opts.tol, opts.c_qr, opts.zolo_r,
+                                                opts.seed if opts.use_omega else None, opts.zolo_c_qr)
         if sigma.shape[0] >= k or retries >= opts.max_retries:
             break
         retries += 1

@@ -37,3 +37,23 @@ def uniform_pm1(seed: int, count: int, offset: int = 0) -> np.ndarray:
     z = splitmix64(seed, count, offset)
     u = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
     return 2.0 * u - 1.0
+
+
+def gaussian(seed: int, count: int) -> np.ndarray:
+    """Standard normal doubles by the Box-Muller transform (Box and Muller, Ann. Math. Stat.
+    1958) of consecutive SplitMix64 pairs: output 2j uses cos and output 2j + 1 sin of the
+    same pair (u1, u2), with u1 = ((z_{2j} >> 11) + 1) 2^-53 in (0, 1] (so log(u1) is finite)
+    and u2 = (z_{2j+1} >> 11) 2^-53 in [0, 1):
+        g_{2j}   = sqrt(-2 log u1) cos(2 pi u2)
+        g_{2j+1} = sqrt(-2 log u1) sin(2 pi u2)
+    The device implements the same definition; the transcendental functions round differently
+    there, so the two agree to a few ulps, not bit for bit."""
+    pairs = (count + 1) // 2
+    z = splitmix64(seed, 2 * pairs)
+    u1 = ((z[0::2] >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+    u2 = (z[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    r = np.sqrt(-2.0 * np.log(u1))
+    out = np.empty(2 * pairs)
+    out[0::2] = r * np.cos(2.0 * np.pi * u2)
+    out[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return out[:count]

@@ -67,17 +67,17 @@ def test_higher_order_never_slower(ell, r):
            side=st.sampled_from(["largest", "smallest"]), zolo=st.sampled_from([0, 2]),
            seed=st.integers(min_value=0, max_value=2 ** 31))
 def test_partial_eig_matches_lapack(n, frac, side, zolo, seed):
-    """QDWHpartial-EIG (QDWH or Zolo-PD steps) on random spectra against LAPACK eigh.  Zolo-PD
-    runs with c_qr = 20: at r = 2 from ell_0 = 0.2 its first Cholesky-formed term has
-    condition up to (1 + c_1) / c_1 = 62 (QDWH's first step: 18.5), which left residuals up to
-    1.13e-13 on 300 random problems of this kind; with that term QR-formed the worst was
-    1.3e-14 (QDWH's 8.6e-14)."""
+    """QDWHpartial-EIG (QDWH or Zolo-PD steps, default options) on random spectra against LAPACK
+    eigh.  Zolo-PD's default QR-forms a term once 1 / c_{2j-1} > 20: at r = 2 from ell_0 = 0.2 the
+    first term's Gram shift has (1 + c_1) / c_1 up to 62 (QDWH's first step factors a matrix of
+    condition <= 18.5), and Cholesky-forming it left residuals up to 1.13e-13 on 300 random
+    problems of this kind; QR-formed, the worst was 1.3e-14 (QDWH's 8.6e-14)."""
     from paper_2104_14186_gb300 import inputs as I
     rng = np.random.default_rng(seed)
     lam = rng.uniform(-1.0, 1.0, n)
     A = I.symmetric_with_spectrum(lam, rng)
     k = I.k_from_fraction(n, frac)
-    r = O.qdwhp_eig(A, O.EigOptions(k=k, side=side, zolo_r=zolo, c_qr=20.0))
+    r = O.qdwhp_eig(A, O.EigOptions(k=k, side=side, zolo_r=zolo))
     ref = np.linalg.eigvalsh(A)
     want = ref[::-1][:k] if side == "largest" else ref[:k]
     m = O.eig_metrics(A, r.lam, r.V, want)
