@@ -66,7 +66,8 @@ typedef struct {
   double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
   int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */
   int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
-  double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.1; the paper prints 0.01) */
+  double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.1; the paper prints 0.01,
+                             which holds the FP64 tolerances with use_omega = 1) */
   double c_qr;            /* SVD: QR-based step while c_k > c_qr (default 100) */
   int32_t block_extra;    /* p: the count-to-threshold subspace starts from k + p vectors (16) */
   int32_t power_steps;    /* q: products with the operator; 0 = automatic.  EIG: block Krylov space of
@@ -80,8 +81,14 @@ typedef struct {
   int32_t zolo_r;         /* 0 (default): QDWH steps.  1..8: Zolo-PD iterations (the type (2r+1, 2r)
                              Zolotarev variant of Section 3.1) from ell_0 = s_eig (EIG) or s (SVD)
                              until ell_k = 1, each with one Gram matrix and r independent terms
-                             X (X^T X + c I)^{-1} (Cholesky-formed, or QR-formed when 1 / c > c_qr);
+                             X (X^T X + c I)^{-1} (Cholesky-formed, or QR-formed when 1 / c > zolo_c_qr);
                              iters_eig is then unused.  QDWHP_FP64 or QDWHP_FP64_EMULATED only. */
+  int32_t use_omega;      /* 0 (default) or 1: the extraction QR of Algorithms 1-2 step 3 factors B Omega
+                             instead of B (B = (r(A~) + I) / 2, or I - r^T r for the SVD), Omega an n x n
+                             Gaussian matrix with N(0, 1/n) entries (SplitMix64 + Box-Muller from `seed`):
+                             rank revealing with high probability (Section 4.1), at the cost of one more
+                             n x n x n product */
+  double zolo_c_qr;       /* Zolo-PD: a term is QR-formed when 1 / c_{2j-1} > zolo_c_qr (default 20) */
 } qdwhp_opts;
 
 /* Per-solve report (host struct, filled when the pointer is non-NULL). */
@@ -146,6 +153,26 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
                                  const qdwhp_opts* opts, double* sigma, double* U, int64_t ldu,
                                  double* V, int64_t ldv, void* workspace, size_t ws_bytes,
                                  qdwhp_info* info, void* stream);
+
+/*
+ * Host-buffer forms of qdwhp_eig and qdwhp_svd (the same solvers): A_host and the outputs are
+ * HOST arrays (column-major, leading dimensions as above; page-locked memory lets the copies
+ * run asynchronously), the rest as for the device forms.  The library copies A to the device,
+ * solves, and copies lambda / sigma, U and V back, all on `stream`, then synchronises it; the
+ * outputs are complete on return.  workspace/ws_bytes (device): at least
+ * qdwhp_eig_host_workspace_bytes(n, opts) or qdwhp_svd_host_workspace_bytes(m, n, k, opts),
+ * which add the device copies of A and of the outputs to the solver's own workspace
+ * (0 = invalid sizes).  Errors: as for the device forms; QDWHP_ERR_CUDA if a copy fails.
+ */
+QDWHP_API size_t qdwhp_eig_host_workspace_bytes(int64_t n, const qdwhp_opts* opts);
+QDWHP_API qdwhp_status qdwhp_eig_host(const double* A_host, int64_t n, int64_t lda, const qdwhp_opts* opts,
+                                      double* lambda_host, double* V_host, int64_t ldv, void* workspace,
+                                      size_t ws_bytes, qdwhp_info* info, void* stream);
+QDWHP_API size_t qdwhp_svd_host_workspace_bytes(int64_t m, int64_t n, int64_t k, const qdwhp_opts* opts);
+QDWHP_API qdwhp_status qdwhp_svd_host(const double* A_host, int64_t m, int64_t n, int64_t lda, int64_t k,
+                                      const qdwhp_opts* opts, double* sigma_host, double* U_host, int64_t ldu,
+                                      double* V_host, int64_t ldv, void* workspace, size_t ws_bytes,
+                                      qdwhp_info* info, void* stream);
 
 /*
  * Full symmetric eigendecomposition by QDWH spectral divide and conquer (QDWH-EIG,

@@ -117,13 +117,11 @@ qdwhp_status trsm_rec(cudaStream_t st, bool trans, int64_t m, int64_t n, T* X, i
 template <typename T>
 qdwhp_status potrf_rec(cudaStream_t st, int64_t n, T* Z, int64_t ldz, T* Linv, T* scratch, int* fail, int64_t off) {
   if (n <= NB) {
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-      attr_err = cudaFuncSetAttribute(potrf_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)leaf_smem<T>());
-    });
-    QDWHP_CUDA_TRY(attr_err);
+    static PerDeviceOnce attr;
+    QDWHP_CUDA_TRY(attr.run([] {
+      return cudaFuncSetAttribute(potrf_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)leaf_smem<T>());
+    }));
     potrf_leaf_kernel<T><<<1, 256, leaf_smem<T>(), st>>>((int)n, Z, ldz, Linv, fail, (int)off);
     QDWHP_LAUNCH_CHECK();
     return QDWHP_OK;

@@ -105,6 +105,7 @@ __host__ __device__ __forceinline__ double uniform_pm1_at(uint64_t seed, uint64_
 
 constexpr uint64_t kStreamLanczos = 0x4C414E43ull;   // "LANC"
 constexpr uint64_t kStreamBlock = 0x424C4F43ull;     // "BLOC"
+constexpr uint64_t kStreamOmega = 0x4F4D4547ull;     // "OMEG"
 
 // Bump allocator over a caller-owned device workspace.  Every carve is 256-byte aligned.
 struct Arena {

@@ -1,9 +1,35 @@
 // Internal host-side interfaces shared by the library's translation units.
 #pragma once
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace qdwhp {
+
+// Runs a setter once per device, the first time that device is current, and again on a later
+// call if it failed.  Function attributes (cudaFuncSetAttribute) and __constant__ tables act on
+// the current device only, so a process-wide once would leave a second device unconfigured.
+class PerDeviceOnce {
+ public:
+  template <class F>
+  cudaError_t run(F&& set) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return set();
+    std::lock_guard<std::mutex> lk(mu_);
+    if (done_[dev]) return cudaSuccess;
+    e = set();
+    if (e == cudaSuccess) done_[dev] = true;
+    return e;
+  }
+
+ private:
+  static constexpr int kMaxDevices = 64;
+  std::mutex mu_;
+  bool done_[kMaxDevices] = {};
+};
 
 enum Uplo { FULL = 0, LOWER = 1 };
 

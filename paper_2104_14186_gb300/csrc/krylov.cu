@@ -51,6 +51,26 @@ __global__ void fill_uniform_kernel(size_t count, uint64_t seed, double* out, in
   }
 }
 
+// Standard normal samples by the Box-Muller transform (Box and Muller 1958) of consecutive
+// SplitMix64 outputs: output 2j is sqrt(-2 log u1) cos(2 pi u2) and output 2j + 1 the same
+// radius times sin(2 pi u2), with u1 = ((z_2j >> 11) + 1) 2^-53 in (0, 1] and
+// u2 = (z_2j+1 >> 11) 2^-53 in [0, 1); element e of the column-major rows x cols block takes
+// output e, times `scale`.
+__global__ void fill_gaussian_kernel(size_t count, uint64_t seed, double scale, double* out, int64_t rows,
+                                     int64_t ld) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t pair = e >> 1;
+    const uint64_t z1 = splitmix64_at(seed, 2 * pair), z2 = splitmix64_at(seed, 2 * pair + 1);
+    const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    const int64_t i = (int64_t)(e % rows), j = (int64_t)(e / rows);
+    out[i + j * ld] = scale * r * ((e & 1) ? sn : cs);
+  }
+}
+
 // h[c] = Q(:, c)^T w for c < ncols (one CTA per column).
 __global__ void dots_t_kernel(int n, const double* Q, int64_t ldq, const double* w, double* h) {
   __shared__ double red[32];
@@ -352,6 +372,15 @@ qdwhp_status gemv_n(cudaStream_t st, int64_t m, int64_t n, const double* A, int6
   gemv_n_part_kernel<<<grid, 256, 0, st>>>((int)m, (int)n, A, lda, x, part);
   QDWHP_LAUNCH_CHECK();
   sum_chunks_kernel<<<ceil_div(m, 256), 256, 0, st>>>((int)m, nchunks, part, y);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status fill_gaussian(cudaStream_t st, int64_t rows, int64_t cols, uint64_t seed, double scale, double* out,
+                           int64_t ld) {
+  const size_t count = (size_t)rows * cols;
+  if (count == 0) return QDWHP_OK;
+  fill_gaussian_kernel<<<grid1d(count, 256), 256, 0, st>>>(count, seed, scale, out, rows, ld);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

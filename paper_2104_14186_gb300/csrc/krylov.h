@@ -18,6 +18,9 @@ size_t gemv_n_part_elems(int64_t m, int64_t n);
 qdwhp_status gemv_n(cudaStream_t st, int64_t m, int64_t n, const double* A, int64_t lda, const double* x, double* y,
                     double* part);
 qdwhp_status fill_uniform(cudaStream_t st, int64_t rows, int64_t cols, uint64_t seed, double* out, int64_t ld);
+// rows x cols block of N(0, scale^2) samples (SplitMix64 + Box-Muller, column-major order).
+qdwhp_status fill_gaussian(cudaStream_t st, int64_t rows, int64_t cols, uint64_t seed, double scale, double* out,
+                           int64_t ld);
 size_t lanczos_ws_elems(int64_t m, int64_t n, int steps);
 // normal == false: symmetric n x n A; normal == true: the operator A^T A of the m x n A.
 qdwhp_status lanczos(cudaStream_t st, bool normal, int64_t m, int64_t n, const double* A, int64_t lda, int steps,

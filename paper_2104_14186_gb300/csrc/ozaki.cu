@@ -456,12 +456,10 @@ qdwhp_status slice_map(CUtensorMap* map, const unsigned short* base, int rows_pa
 qdwhp_status launch_umma_ws(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
                             const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta,
                             double* C, int64_t ldc, Uplo uplo, double diag_add, int* err) {
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(oz_umma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
-  });
-  QDWHP_CUDA_TRY(attr_err);
+  static PerDeviceOnce attr;
+  QDWHP_CUDA_TRY(attr.run([] {
+    return cudaFuncSetAttribute(oz_umma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
+  }));
   CUtensorMap mapA, mapB;
   QDWHP_TRY(slice_map(&mapA, Asl, mp, kp));
   QDWHP_TRY(slice_map(&mapB, Bsl, np, kp));
@@ -474,11 +472,10 @@ qdwhp_status launch_umma_ws(cudaStream_t st, int64_t m, int64_t n, int kp, int m
 
 int ceil_to(int64_t a, int b) { return (int)(((a + b - 1) / b) * b); }
 
-std::once_flag g_pairs_once;
-qdwhp_status g_pairs_status = QDWHP_OK;
+PerDeviceOnce g_pairs_once;
 
 qdwhp_status upload_pairs() {
-  std::call_once(g_pairs_once, [] {
+  const cudaError_t e = g_pairs_once.run([] {
     PairTable t;
     memset(&t, 0, sizeof(t));
     int p = 0;
@@ -494,9 +491,13 @@ qdwhp_status upload_pairs() {
         ++p;
       }
     t.npairs = p;
-    if (cudaMemcpyToSymbol(c_pairs, &t, sizeof(t)) != cudaSuccess) g_pairs_status = QDWHP_ERR_CUDA;
+    return cudaMemcpyToSymbol(c_pairs, &t, sizeof(t));
   });
-  return g_pairs_status;
+  if (e != cudaSuccess) {
+    set_last_error(e, "upload of the digit-pair table", __FILE__, __LINE__);
+    return QDWHP_ERR_CUDA;
+  }
+  return QDWHP_OK;
 }
 
 }  // namespace

@@ -245,12 +245,9 @@ size_t panel_smem_bytes(int R, int G) {
 qdwhp_status launch_panel(cudaStream_t st, PanelArgs& pa) {
   const int G = panel_ctas(pa.R);
   const size_t smem = panel_smem_bytes(pa.R, G);
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  });
-  QDWHP_CUDA_TRY(attr_err);
+  static PerDeviceOnce attr;
+  QDWHP_CUDA_TRY(attr.run(
+      [] { return cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); }));
   if (smem > 160 * 1024) return QDWHP_ERR_ARG;
   void* args[] = {&pa};
   return launch_cooperative((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, st);

@@ -304,7 +304,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   // Zolo-PD of order zolo_r until ell_k = 1.
   const bool zolo = o.zolo_r > 0;
   if (zolo) {
-    QDWHP_TRY(zolo_schedule(st, o.s_eig, o.zolo_r, o.c_qr, w.c.zsched));
+    QDWHP_TRY(zolo_schedule(st, o.s_eig, o.zolo_r, o.zolo_c_qr, w.c.zsched));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.zsched, w.c.zsched, sizeof(ZoloSchedule), cudaMemcpyDeviceToHost, st));
   } else {
     // Cholesky-based in every iteration (Section 4.1; c_qr is the SVD's switch)
@@ -336,9 +336,16 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     inf.it_f32 = n_f32;
     inf.it_qr = n_qr;
     inf.it_chol = n_chol;
-    // Step 3: QR of (r(A~) + I) / 2.
+    // Step 3: QR of (r(A~) + I) / 2, or of (r(A~) + I) Omega / 2 with the Gaussian Omega of
+    // Section 4.1 (S1 and S2 are free until Rayleigh-Ritz).
     QDWHP_TRY(axpby(st, n, n, 0.5, w.X, n, 0.0, w.X, n, 0.5));
-    QDWHP_TRY(geqrf(st, n, n, w.X, n, w.f, w.qr_scratch));
+    double* F = w.X;
+    if (o.use_omega) {
+      QDWHP_TRY(fill_gaussian(st, n, n, o.seed ^ kStreamOmega, 1.0 / std::sqrt((double)n), w.S2, n));
+      QDWHP_TRY(gemm(st, false, false, n, n, n, 1.0, w.X, n, w.S2, n, 0.0, w.S1, n));
+      F = w.S1;
+    }
+    QDWHP_TRY(geqrf(st, n, n, F, n, w.f, w.qr_scratch));
     // Step 4: index rule.
     index_scan_kernel<<<1, 1024, 0, st>>>((int)n, w.f.diagR, o.tol, w.c.ints);
     QDWHP_LAUNCH_CHECK();
@@ -500,7 +507,7 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   for (;;) {
     const bool zolo = o.zolo_r > 0;
     if (zolo) {
-      QDWHP_TRY(zolo_schedule(st, s, o.zolo_r, o.c_qr, w.c.zsched));
+      QDWHP_TRY(zolo_schedule(st, s, o.zolo_r, o.zolo_c_qr, w.c.zsched));
       QDWHP_TRY(sync_read(st, &hs.zsched, w.c.zsched, sizeof(ZoloSchedule)));
     } else {
       QDWHP_TRY(dwh_schedule(st, nullptr, s, 0, o.c_qr, w.c.sched));
@@ -521,7 +528,14 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
     double* B = w.q.Z;
     QDWHP_TRY(gemm(st, true, false, n, n, m, -1.0, w.X, m, w.X, m, 0.0, B, n, LOWER, 1.0));
     QDWHP_TRY(symmetrize_from_lower(st, n, B, n));
-    QDWHP_TRY(geqrf(st, n, n, B, n, w.f, w.qr_scratch));
+    // or the QR of (I - X^T X) Omega (Section 4.1; W and Vj are free until the projection)
+    double* F = B;
+    if (o.use_omega) {
+      QDWHP_TRY(fill_gaussian(st, n, n, o.seed ^ kStreamOmega, 1.0 / std::sqrt((double)n), w.W, n));
+      QDWHP_TRY(gemm(st, false, false, n, n, n, 1.0, B, n, w.W, n, 0.0, w.Vj, n));
+      F = w.Vj;
+    }
+    QDWHP_TRY(geqrf(st, n, n, F, n, w.f, w.qr_scratch));
     index_scan_kernel<<<1, 1024, 0, st>>>((int)n, w.f.diagR, o.tol, w.c.ints);
     QDWHP_LAUNCH_CHECK();
     int fail = 0;
@@ -595,6 +609,7 @@ bool opts_valid(const qdwhp_opts& o) {
          o.c_qr > 0.0 && o.block_extra >= 0 && o.power_steps >= 0 && o.power_steps <= 16 && o.lanczos_steps >= 1 &&
          o.guard >= 0.0 && o.guard < 1.0 && o.max_retries >= 0 && o.jacobi_max_sweeps >= 1 &&
          o.refine_steps >= 0 && o.refine_steps <= 64 && o.zolo_r >= 0 && o.zolo_r <= kZoloMaxR &&
+         (o.use_omega == 0 || o.use_omega == 1) && o.zolo_c_qr > 0.0 &&
          (o.zolo_r == 0 || o.precision == QDWHP_FP64 || o.precision == QDWHP_FP64_EMULATED) &&
          (o.side == QDWHP_LARGEST || o.side == QDWHP_SMALLEST) &&
          (o.precision == QDWHP_FP64 || o.precision == QDWHP_MIXED || o.precision == QDWHP_FP64_EMULATED ||
@@ -628,6 +643,8 @@ QDWHP_API void qdwhp_default_opts(qdwhp_opts* o) {
   o->seed = 1234;
   o->refine_steps = 0;
   o->zolo_r = 0;
+  o->use_omega = 0;
+  o->zolo_c_qr = 20.0;
 }
 
 QDWHP_API const char* qdwhp_status_string(qdwhp_status s) {
@@ -708,6 +725,110 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
   // m < n: solve on A^T (n x m) and swap the roles of U and V (Section 4.2).
   QDWHP_TRY(transpose(st, m, n, A, lda, w.At, n));
   return svd_impl(w.At, n, m, n, kk, *opts, sigma, V, ldv, U, ldu, w, info, st);
+}
+
+// ---- host-buffer forms: the copies run on the caller's stream inside the library ----
+
+namespace {
+struct HostIo {
+  double* A = nullptr;
+  double* vals = nullptr;
+  double* U = nullptr;
+  double* V = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+// Device copies of the input and outputs in front of the solver's own workspace.
+void carve_host_io(Arena& ar, int64_t m, int64_t n, int64_t k, bool svd, HostIo& h) {
+  h.A = ar.take<double>((size_t)m * n);
+  h.vals = ar.take<double>((size_t)k);
+  if (svd) h.U = ar.take<double>((size_t)m * k);
+  h.V = ar.take<double>((size_t)n * k);
+  const size_t front = ar.used;
+  h.ws = ar.take<char>(0);
+  h.ws_bytes = ar.cap > front ? ar.cap - front : 0;
+}
+
+qdwhp_status copy_in(cudaStream_t st, double* dst, const double* src_host, int64_t rows, int64_t cols, int64_t ld) {
+  QDWHP_CUDA_TRY(cudaMemcpy2DAsync(dst, rows * sizeof(double), src_host, ld * sizeof(double), rows * sizeof(double),
+                                   cols, cudaMemcpyHostToDevice, st));
+  return QDWHP_OK;
+}
+
+qdwhp_status copy_out(cudaStream_t st, double* dst_host, int64_t ld, const double* src, int64_t rows, int64_t cols) {
+  QDWHP_CUDA_TRY(cudaMemcpy2DAsync(dst_host, ld * sizeof(double), src, rows * sizeof(double), rows * sizeof(double),
+                                   cols, cudaMemcpyDeviceToHost, st));
+  return QDWHP_OK;
+}
+}  // namespace
+
+QDWHP_API size_t qdwhp_eig_host_workspace_bytes(int64_t n, const qdwhp_opts* opts) {
+  qdwhp_opts o;
+  if (opts) o = *opts; else qdwhp_default_opts(&o);
+  const int64_t k = resolve_k(n, o, 0);
+  if (n < 1 || k < 1 || k > n) return 0;
+  Arena ar;
+  ar.dry = true;
+  HostIo h;
+  carve_host_io(ar, n, n, k, false, h);
+  return ar.used + qdwhp_eig_workspace_bytes(n, &o) + 256;
+}
+
+QDWHP_API qdwhp_status qdwhp_eig_host(const double* A_host, int64_t n, int64_t lda, const qdwhp_opts* opts,
+                                      double* lambda_host, double* V_host, int64_t ldv, void* workspace,
+                                      size_t ws_bytes, qdwhp_info* info, void* stream) {
+  if (!opts || !A_host || !lambda_host || !V_host || n < 1 || lda < n || ldv < n) return QDWHP_ERR_ARG;
+  if (!opts_valid(*opts) || n > (1 << 20)) return QDWHP_ERR_ARG;
+  const int64_t k = resolve_k(n, *opts, 0);
+  if (k < 1 || k > n) return QDWHP_ERR_ARG;
+  if (!workspace || ws_bytes < qdwhp_eig_host_workspace_bytes(n, opts)) return QDWHP_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar{(char*)workspace, ws_bytes};
+  HostIo h;
+  carve_host_io(ar, n, n, k, false, h);
+  QDWHP_TRY(copy_in(st, h.A, A_host, n, n, lda));
+  QDWHP_TRY(qdwhp_eig(h.A, n, n, opts, h.vals, h.V, n, h.ws, h.ws_bytes, info, stream));
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(lambda_host, h.vals, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  QDWHP_TRY(copy_out(st, V_host, ldv, h.V, n, k));
+  QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+  return QDWHP_OK;
+}
+
+QDWHP_API size_t qdwhp_svd_host_workspace_bytes(int64_t m, int64_t n, int64_t k, const qdwhp_opts* opts) {
+  qdwhp_opts o;
+  if (opts) o = *opts; else qdwhp_default_opts(&o);
+  if (m < 1 || n < 1) return 0;
+  const int64_t kk = resolve_k(std::min(m, n), o, k);
+  if (kk < 1 || kk > std::min(m, n)) return 0;
+  Arena ar;
+  ar.dry = true;
+  HostIo h;
+  carve_host_io(ar, m, n, kk, true, h);
+  return ar.used + qdwhp_svd_workspace_bytes(m, n, &o) + 256;
+}
+
+QDWHP_API qdwhp_status qdwhp_svd_host(const double* A_host, int64_t m, int64_t n, int64_t lda, int64_t k,
+                                      const qdwhp_opts* opts, double* sigma_host, double* U_host, int64_t ldu,
+                                      double* V_host, int64_t ldv, void* workspace, size_t ws_bytes,
+                                      qdwhp_info* info, void* stream) {
+  if (!opts || !A_host || !sigma_host || !U_host || !V_host || m < 1 || n < 1 || lda < m || ldu < m || ldv < n)
+    return QDWHP_ERR_ARG;
+  if (!opts_valid(*opts) || k < 0 || std::max(m, n) > (1 << 20)) return QDWHP_ERR_ARG;
+  const int64_t kk = resolve_k(std::min(m, n), *opts, k);
+  if (kk < 1 || kk > std::min(m, n)) return QDWHP_ERR_ARG;
+  if (!workspace || ws_bytes < qdwhp_svd_host_workspace_bytes(m, n, k, opts)) return QDWHP_ERR_NOMEM;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena ar{(char*)workspace, ws_bytes};
+  HostIo h;
+  carve_host_io(ar, m, n, kk, true, h);
+  QDWHP_TRY(copy_in(st, h.A, A_host, m, n, lda));
+  QDWHP_TRY(qdwhp_svd(h.A, m, n, m, kk, opts, h.vals, h.U, m, h.V, n, h.ws, h.ws_bytes, info, stream));
+  QDWHP_CUDA_TRY(cudaMemcpyAsync(sigma_host, h.vals, sizeof(double) * kk, cudaMemcpyDeviceToHost, st));
+  QDWHP_TRY(copy_out(st, U_host, ldu, h.U, m, kk));
+  QDWHP_TRY(copy_out(st, V_host, ldv, h.V, n, kk));
+  QDWHP_CUDA_TRY(cudaStreamSynchronize(st));
+  return QDWHP_OK;
 }
 
 }  // extern "C"

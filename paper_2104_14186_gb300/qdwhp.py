@@ -38,7 +38,7 @@ class Opts(C.Structure):
         ("s_eig", C.c_double), ("iters_eig", C.c_int32), ("lanczos_steps", C.c_int32), ("tol", C.c_double),
         ("c_qr", C.c_double), ("block_extra", C.c_int32), ("power_steps", C.c_int32), ("guard", C.c_double),
         ("max_retries", C.c_int32), ("jacobi_max_sweeps", C.c_int32), ("seed", C.c_uint64),
-        ("refine_steps", C.c_int32), ("zolo_r", C.c_int32),
+        ("refine_steps", C.c_int32), ("zolo_r", C.c_int32), ("use_omega", C.c_int32), ("zolo_c_qr", C.c_double),
     ]
 
 
@@ -104,6 +104,11 @@ SIGNATURES = {
     "qdwhp_svd_workspace_bytes": (C.c_size_t, [I64, I64, C.POINTER(Opts)]),
     "qdwhp_svd": (C.c_int, [P, I64, I64, I64, I64, C.POINTER(Opts), P, P, I64, P, I64, P, C.c_size_t,
                             C.POINTER(Info), P]),
+    "qdwhp_eig_host_workspace_bytes": (C.c_size_t, [I64, C.POINTER(Opts)]),
+    "qdwhp_eig_host": (C.c_int, [P, I64, I64, C.POINTER(Opts), P, P, I64, P, C.c_size_t, C.POINTER(Info), P]),
+    "qdwhp_svd_host_workspace_bytes": (C.c_size_t, [I64, I64, I64, C.POINTER(Opts)]),
+    "qdwhp_svd_host": (C.c_int, [P, I64, I64, I64, I64, C.POINTER(Opts), P, P, I64, P, I64, P, C.c_size_t,
+                                 C.POINTER(Info), P]),
     "qdwhp_syev_workspace_bytes": (C.c_size_t, [I64]),
     "qdwhp_syev_f64": (C.c_int, [P, I64, I64, P, P, I64, P, C.c_size_t, C.POINTER(SyevInfo), P]),
     "qdwhp_gesvd_workspace_bytes": (C.c_size_t, [I64, I64, C.c_int32]),
@@ -216,9 +221,27 @@ class SvdResult:
     info: dict
 
 
+def _host_colmajor(A: torch.Tensor) -> torch.Tensor:
+    """Column-major storage of a host float64 matrix: A's own storage when it is already
+    column-major (A.t() contiguous), else a copy."""
+    if A.dtype != torch.float64 or A.is_cuda or A.dim() != 2:
+        raise ValueError("expected a 2-D float64 host tensor")
+    At = A.t()
+    return At if At.is_contiguous() else At.contiguous()
+
+
+def _host_out(shape, pin: bool) -> torch.Tensor:
+    return torch.empty(shape, dtype=torch.float64, pin_memory=pin)
+
+
 def eig(A: torch.Tensor, k: int | None = None, fraction: float | None = None, side: str = "largest",
-        ws: torch.Tensor | None = None, stream=None, **opts) -> EigResult:
-    """qdwhp_eig: k largest (or smallest) eigenpairs of the symmetric CUDA float64 matrix A."""
+        ws: torch.Tensor | None = None, stream=None, device=None, out=None, **opts) -> EigResult:
+    """qdwhp_eig: k largest (or smallest) eigenpairs of the symmetric float64 matrix A.
+
+    A CUDA tensor is solved on its device.  A host tensor goes through qdwhp_eig_host (the
+    library copies A in and lambda, V out on the stream of `device`, default cuda:0); `out`
+    may hold preallocated host tensors (lambda (k,), V^T (k, n)), pinned for asynchronous
+    copies."""
     n = A.shape[0]
     if A.shape != (n, n):
         raise ValueError("A must be square")
@@ -229,6 +252,22 @@ def eig(A: torch.Tensor, k: int | None = None, fraction: float | None = None, si
         o.count = 0
         o.fraction = float(fraction)
     kk = int(o.count) if o.count > 0 else k_from_fraction(n, o.fraction)
+    if not A.is_cuda:
+        dev = torch.device(device or "cuda")
+        Ac = _host_colmajor(A)
+        lam, Vt = out if out is not None else (_host_out(max(kk, 1), Ac.is_pinned()),
+                                               _host_out((max(kk, 1), n), Ac.is_pinned()))
+        need = lib().qdwhp_eig_host_workspace_bytes(n, C.byref(o))
+        if need == 0:
+            raise QdwhpError(-1, "qdwhp_eig_host_workspace_bytes")
+        if ws is None or ws.numel() < need:
+            ws = workspace(need, dev)
+        info = Info()
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        rc = lib().qdwhp_eig_host(_ptr(Ac), n, n, C.byref(o), _ptr(lam), _ptr(Vt), n, _ptr(ws), ws.numel(),
+                                  C.byref(info), st.cuda_stream)
+        _check(rc, "qdwhp_eig_host")
+        return EigResult(lam[:kk], Vt[:kk].t(), info.as_dict())
     Ac = _colmajor(A)
     lam = torch.empty(max(kk, 1), dtype=torch.float64, device=A.device)
     Vt = torch.empty(max(kk, 1), n, dtype=torch.float64, device=A.device)
@@ -284,25 +323,15 @@ def gesvd(A: torch.Tensor, precision: int = 0, ws: torch.Tensor | None = None, s
 
 
 def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws: torch.Tensor | None = None,
-        stream=None, device=None, **opts) -> SvdResult:
+        stream=None, device=None, out=None, **opts) -> SvdResult:
     """qdwhp_svd: k largest singular triplets of the float64 matrix A (m x n).
 
-    A CUDA tensor is solved in place on its device.  A host tensor (pinned for
-    asynchronous copies) is copied to `device` (default cuda:0) on the stream, solved,
-    and sigma, U and V are copied back into host tensors before returning.
+    A CUDA tensor is solved in place on its device.  A host tensor goes through
+    qdwhp_svd_host: the library copies A to `device` (default cuda:0), solves, and copies
+    sigma, U and V back into host tensors on the stream before returning; `out` may hold
+    preallocated host tensors (sigma (k,), U^T (k, m), V^T (k, n)), pinned for asynchronous
+    copies.
     """
-    host_in = not A.is_cuda
-    if host_in:
-        dev = torch.device(device or "cuda")
-        st = stream if stream is not None else torch.cuda.current_stream(dev)
-        with torch.cuda.stream(st):
-            Ad = A.to(dev, non_blocking=True)
-            r = svd(Ad, k=k, fraction=fraction, ws=ws, stream=st, **opts)
-            out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (r.sigma, r.U, r.V)]
-            for o_, t in zip(out, (r.sigma, r.U, r.V)):
-                o_.copy_(t, non_blocking=True)
-        st.synchronize()
-        return SvdResult(out[0], out[1], out[2], r.info)
     m, n = A.shape
     o = default_opts(**opts)
     kk = 0
@@ -311,6 +340,23 @@ def svd(A: torch.Tensor, k: int | None = None, fraction: float | None = None, ws
     elif fraction is not None:
         o.fraction = float(fraction)
     kres = kk if kk > 0 else (int(o.count) if o.count > 0 else k_from_fraction(min(m, n), o.fraction))
+    if not A.is_cuda:
+        dev = torch.device(device or "cuda")
+        Ac = _host_colmajor(A)
+        pin = Ac.is_pinned()
+        sig, Ut, Vt = out if out is not None else (_host_out(max(kres, 1), pin), _host_out((max(kres, 1), m), pin),
+                                                   _host_out((max(kres, 1), n), pin))
+        need = lib().qdwhp_svd_host_workspace_bytes(m, n, kk, C.byref(o))
+        if need == 0:
+            raise QdwhpError(-1, "qdwhp_svd_host_workspace_bytes")
+        if ws is None or ws.numel() < need:
+            ws = workspace(need, dev)
+        info = Info()
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        rc = lib().qdwhp_svd_host(_ptr(Ac), m, n, m, kk, C.byref(o), _ptr(sig), _ptr(Ut), m, _ptr(Vt), n, _ptr(ws),
+                                  ws.numel(), C.byref(info), st.cuda_stream)
+        _check(rc, "qdwhp_svd_host")
+        return SvdResult(sig[:kres], Ut[:kres].t(), Vt[:kres].t(), info.as_dict())
     with torch.cuda.stream(stream) if stream is not None else _nullctx():
         Ac = _colmajor(A)
         sigma = torch.empty(max(kres, 1), dtype=torch.float64, device=A.device)

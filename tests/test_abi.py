@@ -46,6 +46,7 @@ def test_struct_layouts_match_header(lib):
     assert o.s_eig == 0.2 and o.iters_eig == 3 and o.tol == 0.1 and o.c_qr == 100.0
     assert o.lanczos_steps == 30 and o.block_extra == 16 and o.power_steps == 0 and o.seed == 1234
     assert o.max_retries == 2 and o.jacobi_max_sweeps == 30 and o.side == Q.LARGEST
+    assert o.use_omega == 0 and o.zolo_c_qr == 20.0 and o.zolo_r == 0 and o.refine_steps == 0
 
 
 def test_k_from_fraction(lib):
@@ -234,3 +235,28 @@ def test_info_dict_slices_schedule_by_iterations(lib):
     g = Q.GesvdInfo()
     g.median_splits = 3
     assert g.as_dict()["median_splits"] == 3 and "reserved" not in g.as_dict()
+
+
+def test_host_entry_points_argument_checks(lib):
+    """The host-buffer forms size their workspace as the solver's plus the device copies of A
+    and the outputs, and reject bad arguments before any copy or launch."""
+    from paper_2104_14186_gb300 import qdwhp as Q
+    o = Q.default_opts()
+    o.count = 20
+    eig_ws = lib.qdwhp_eig_workspace_bytes(300, C.byref(o))
+    host_ws = lib.qdwhp_eig_host_workspace_bytes(300, C.byref(o))
+    assert host_ws >= eig_ws + (300 * 300 + 20 + 300 * 20) * 8
+    svd_ws = lib.qdwhp_svd_workspace_bytes(400, 300, C.byref(o))
+    assert lib.qdwhp_svd_host_workspace_bytes(400, 300, 25, C.byref(o)) >= svd_ws + (400 * 300 + 25 * 701) * 8
+    assert lib.qdwhp_svd_host_workspace_bytes(400, 300, 301, C.byref(o)) == 0     # k > min(m, n)
+    assert lib.qdwhp_eig_host_workspace_bytes(0, C.byref(o)) == 0
+    info = Q.Info()
+    buf = (C.c_double * 16)()
+    assert lib.qdwhp_eig_host(None, 300, 300, C.byref(o), buf, buf, 300, None, 0, C.byref(info), None) == -1
+    assert lib.qdwhp_eig_host(buf, 300, 299, C.byref(o), buf, buf, 300, None, 0, C.byref(info), None) == -1
+    assert lib.qdwhp_eig_host(buf, 300, 300, C.byref(o), buf, buf, 300, None, 0, C.byref(info), None) == -2
+    assert lib.qdwhp_svd_host(buf, 400, 300, 400, 25, C.byref(o), buf, buf, 399, buf, 300, None, 0,
+                              C.byref(info), None) == -1
+    o.use_omega = 3
+    assert lib.qdwhp_svd_host(buf, 400, 300, 400, 25, C.byref(o), buf, buf, 400, buf, 300, None, 0,
+                              C.byref(info), None) == -1

@@ -74,12 +74,22 @@ def test_queue_admission_and_timeout(Q):
         q.submit_eig(dev(p.A), p.k)
     assert e.value.status == -8
     p2 = I.eig_uniform(200, 8, 0.1)
-    rid = q.submit_eig(dev(p2.A), p2.k)
+    A2 = dev(p2.A)
+    # The request's input is produced on this stream behind a kernel that runs for about a
+    # second, so the solve cannot have finished when the zero-millisecond wait looks at it.
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(2_000_000_000)
+        rid = q.submit_eig(A2, p2.k, stream=side)
     info = Q.Info()
     st = Q.lib().qdwhp_wait(q.h, rid, 0, __import__("ctypes").byref(info))
-    assert st in (0, -6)                            # finished already, or a bounded wait that expired
+    assert st == -6                                 # the bounded wait expired
+    assert q.poll(rid) == 1                         # still pending
     r = q.wait(rid)
     assert r.lam.shape[0] == p2.k
+    m = O.eig_metrics(p2.A, r.lam.cpu().numpy(), r.V.cpu().numpy(), np.sort(p2.lam)[::-1][: p2.k])
+    assert m["lam_err"] <= 1e-12 and m["resid"] <= 1e-13
     q.close()
 
 

@@ -175,3 +175,65 @@ def test_eig_count_extremes(Q, n, k, side):
     true = np.sort(lam)[::-1][:k] if side == "largest" else np.sort(lam)[:k]
     m = O.eig_metrics(A, r.lam.cpu().numpy(), r.V.cpu().numpy(), true)
     assert m["lam_err"] <= LAM_TOL and m["orth"] <= ORTH_TOL * n and m["resid"] <= RES_TOL, m
+
+
+# ---- Section 4.1's Gaussian Omega with the printed tol = 0.01 ----
+
+@pytest.mark.parametrize("n,frac,side,seed", [
+    (512, 0.10, "largest", 1000),      # the EIG workload
+    (300, 0.05, "smallest", 5013),     # the unpivoted QR misses 1e-13 here at tol = 0.01 (oracle pin)
+    (700, 0.02, "largest", 5),
+])
+def test_eig_omega_tol001_vs_oracle(Q, n, frac, side, seed):
+    p = I.eig_uniform(n, seed, frac, side)
+    r = Q.eig(dev(p.A), k=p.k, side=side, tol=0.01, use_omega=1)
+    ref = O.qdwhp_eig(p.A, O.EigOptions(k=p.k, side=side, tol=0.01, use_omega=True))
+    check_eig(p, r, ref)
+    r0 = Q.eig(dev(p.A), k=p.k, side=side)
+    print(f"n={n} k={p.k}: ell {r.info['ell']} with (tol 0.01, Omega), {r0.info['ell']} with the defaults")
+    assert r.info["ell"] >= p.k
+
+
+@pytest.mark.parametrize("m,n,frac,seed", [(700, 500, 0.05, 2000), (401, 257, 0.2, 3)])
+def test_svd_omega_tol001_vs_oracle(Q, m, n, frac, seed):
+    q = I.svd_logspaced(m, n, seed, frac)
+    r = Q.svd(dev(q.A), k=q.k, tol=0.01, use_omega=1)
+    ref = O.qdwhp_svd(q.A, O.SvdOptions(k=q.k, tol=0.01, use_omega=True))
+    check_svd(q, r, ref)
+
+
+def test_svd_full_size_workload_omega(Q):
+    """The 4096 x 4096 benchmark workload with (tol = 0.01, Omega) at the FP64 tolerances."""
+    q = I.svd_logspaced(4096, 4096, 2000, 0.05)
+    r = Q.svd(dev(q.A), k=q.k, tol=0.01, use_omega=1)
+    check_svd(q, r)
+    print(f"4096^2 top 5 %: ell {r.info['ell']} with (tol 0.01, Omega)")
+
+
+def test_omega_rejects_other_values(Q):
+    p = I.eig_uniform(64, 3, 0.1)
+    with pytest.raises(Q.QdwhpError) as e:
+        Q.eig(dev(p.A), k=p.k, use_omega=2)
+    assert e.value.status == -1
+
+
+# ---- host-buffer entry points (qdwhp_eig_host / qdwhp_svd_host) ----
+
+def test_host_entry_points_equal_device_ones(Q):
+    """Same arithmetic, same stream order: the host-buffer forms return exactly what the
+    device forms return, for pinned and for pageable host memory, tall and wide."""
+    p = I.eig_uniform(300, 41, 0.1, "smallest")
+    rd = Q.eig(dev(p.A), k=p.k, side="smallest")
+    for pin in (True, False):
+        Ah = torch.from_numpy(np.ascontiguousarray(p.A.T)).t()
+        if pin:
+            Ah = Ah.t().pin_memory().t()
+        rh = Q.eig(Ah, k=p.k, side="smallest")
+        assert not rh.lam.is_cuda and torch.equal(rh.lam, rd.lam.cpu()) and torch.equal(rh.V, rd.V.cpu())
+    for shape in ((260, 200), (200, 260)):
+        q = I.svd_logspaced(max(shape), min(shape), 43, 0.1)
+        A = q.A if shape[0] >= shape[1] else np.asfortranarray(q.A.T)
+        sd = Q.svd(dev(A), k=q.k)
+        sh = Q.svd(torch.from_numpy(np.ascontiguousarray(A)), k=q.k)     # row-major: the binding reorders
+        assert torch.equal(sh.sigma, sd.sigma.cpu()) and torch.equal(sh.U, sd.U.cpu())
+        assert torch.equal(sh.V, sd.V.cpu())

@@ -66,6 +66,49 @@ def test_noalloc_breakdown_flag_starts_clean(Q):
     assert st == 0 and info == 0
 
 
+def test_noalloc_allocates_no_device_memory(Q):
+    """The property the entry point exists for: after a warm-up call, further calls change
+    neither the device's free memory (cudaMemGetInfo) nor torch's allocator statistics."""
+    n = 2048
+    Z = _spd(n, 21)
+    Zc = torch.from_numpy(np.asfortranarray(Z).T.copy()).to("cuda")
+    work = Zc.clone()
+    info = C.c_int(-1)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert Q.lib().qdwhp_potrf_f64_noalloc(n, work.data_ptr(), n, C.byref(info), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(3):
+        work.copy_(Zc)
+        assert Q.lib().qdwhp_potrf_f64_noalloc(n, work.data_ptr(), n, C.byref(info), stream) == 0
+        assert info.value == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == alloc0
+
+
+@pytest.mark.parametrize("n,bad", [(300, 128), (4096, 64 * 40), (4096, 4095)])
+def test_noalloc_breakdown_on_split_boundaries_and_at_the_limit(Q, n, bad):
+    """A failing pivot on a recursion split (a multiple of the 64-wide leaf), and at the largest
+    order the static scratch takes; a successful call right after a failing one gives the same
+    factor as qdwhp_potrf_f64."""
+    Z = _spd(n, 5)
+    Z[bad, :] = 0.0
+    Z[:, bad] = 0.0
+    Z[bad, bad] = -1.0
+    st, info, _ = _noalloc(Q, Z)
+    assert st == -4 and info == bad + 1
+    Z2 = _spd(n, 6)
+    st, info, L = _noalloc(Q, Z2)
+    assert st == 0 and info == 0
+    L_ref, info_ref = Q.potrf_f64(torch.from_numpy(Z2).to("cuda"))
+    assert info_ref == 0
+    L_ref = L_ref.cpu().numpy()
+    assert np.linalg.norm(L - L_ref) <= 1e-13 * np.linalg.norm(L_ref)
+
+
 def test_noalloc_rejects_oversize(Q):
     n = 4097
     fake = C.c_void_p(0x1000)
