@@ -65,7 +65,7 @@ typedef struct {
                              rest native FP64); QDWHP_MIXED_EMULATED (both) */
   double s_eig;           /* EIG shift / ell_0, Algorithm 1 step 2 (default 0.2) */
   int32_t iters_eig;      /* EIG QDWH iterations (default 3; two for s_eig = 0.875) */
-  int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 48 used) */
+  int32_t lanczos_steps;  /* Lanczos steps for the spectral bounds (default 30, at most 64 used) */
   double tol;             /* index-rule tolerance on |diag(R)|, Section 4.1 (default 0.1; the paper prints 0.01,
                              which holds the FP64 tolerances with use_omega = 1) */
   double c_qr;            /* SVD: QR-based step while c_k > c_qr (default 100) */

@@ -20,6 +20,11 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   qdwh_polar             pinned: polar factor from the SVD, H symmetric PSD
   lanczos_extremes       pinned: bounds against the known spectrum
   threshold_from_count   pinned: Cauchy interlacing (k eigenvalues beyond t)
+  gauss_rule / slq_*     pinned: the Gauss rule integrates polynomials of degree <= 2m - 1
+                         exactly; its lower bound never exceeds the exact spectral
+                         distribution (Chebyshev-Markov-Stieltjes) on known spectra; the
+                         stochastic threshold leaves >= k eigenvalues beyond it on
+                         constructed spectra
   qdwhp_eig / qdwhp_svd  pinned: constructed spectra, brute-force Jacobi (n<=64),
                          LAPACK eigh/svd, Theorem 1 containment bound
   extraction_qr          pinned: Theorem 1 containment bound with and without Omega; on a
@@ -53,7 +58,7 @@ from .partial import (  # noqa: F401
     EigOptions, SvdOptions, EigResult, SvdResult,
     lanczos_extremes, lanczos_extremes_normal, threshold_from_count_eig, threshold_from_count_svd,
     qdwhp_eig, qdwhp_svd, qdwhp_eig_negative, qdwhp_svd_threshold, index_from_diag, extraction_qr,
-    gaussian_omega,
+    gaussian_omega, threshold_from_count_eig_slq, gauss_rule, slq_lower_bound, lanczos_tridiagonal,
 )
 from .jacobi import jacobi_eig  # noqa: F401
 from .full import syev  # noqa: F401

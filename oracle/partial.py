@@ -46,6 +46,7 @@ from .rng import gaussian, uniform_pm1
 STREAM_LANCZOS = 0x4C414E43   # "LANC"
 STREAM_BLOCK = 0x424C4F43     # "BLOC"
 STREAM_OMEGA = 0x4F4D4547     # "OMEG"
+STREAM_SLQ = 0x534C5150       # "SLQP"
 
 
 @dataclass
@@ -196,6 +197,69 @@ def threshold_from_count_eig(A: np.ndarray, eps_side: float, k: int, lam_hi: flo
     return float(theta[k - 1])
 
 
+# Stochastic Lanczos quadrature threshold (EIG, wide blocks): probes, Lanczos steps per probe,
+# safety factor on the standard error, and the smallest order that uses it (below it the
+# Ritz-value bound of the block subspace captures fewer unwanted eigenvalues).
+SLQ_PROBES = 16
+SLQ_STEPS = 64
+SLQ_Z = 3.0
+SLQ_MIN_N = 1024
+
+
+def slq_probe_seed(seed: int, j: int) -> int:
+    """Seed of probe j (its Lanczos start vector is drawn from seed ^ STREAM_LANCZOS inside
+    lanczos_tridiagonal, as for the bounds)."""
+    return (seed ^ STREAM_SLQ ^ (((j + 1) * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF)) & 0xFFFFFFFFFFFFFFFF
+
+
+def gauss_rule(alpha: np.ndarray, beta: np.ndarray):
+    """Gauss quadrature of the Lanczos tridiagonal (Golub and Welsch 1969): nodes = eigenvalues of
+    T (ascending), weights = squared first components of its eigenvectors (summing to 1 for a
+    unit start vector)."""
+    m = alpha.shape[0]
+    T = np.diag(alpha) + np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
+    theta, S = np.linalg.eigh(T)
+    w = S[0, :] ** 2
+    return theta, w / w.sum()
+
+
+def threshold_from_count_eig_slq(A: np.ndarray, eps_side: float, k: int, seed: int, probes: int = SLQ_PROBES,
+                                 steps: int = SLQ_STEPS, z: float = SLQ_Z):
+    """Threshold t' on A' = eps_side * A below which A' has at least k eigenvalues with high
+    probability, by stochastic Lanczos quadrature (Ubaru, Chen and Saad 2017).
+
+    Each probe v (a SplitMix64 vector, normalised) gives the Gauss rule (theta_i, w_i) of its
+    spectral distribution F_v(x) = sum over eigenpairs (lambda_i, u_i) of A' with lambda_i <= x
+    of (v^T u_i)^2.  By the Chebyshev-Markov-Stieltjes inequalities F_v(theta_j - 0) >=
+    w_1 + ... + w_{j-1}, so at any x, F_v(x) >= L_v(x) = the sum of the weights of the nodes
+    below the last node <= x.  The count of eigenvalues <= x is n E_v[F_v(x)]; t' is the
+    smallest node x of all probes with n (mean L_v(x) - z stderr) >= k.  Returns None when no
+    node qualifies (the caller then uses the block subspace bound).  Unlike the Ritz-value
+    bound this is an estimate: the solver's count check and retries still guarantee the k
+    pairs."""
+    n = A.shape[0]
+    rules = []
+    for j in range(probes):
+        al, be = lanczos_tridiagonal(lambda x: eps_side * (A @ x), n, steps, slq_probe_seed(seed, j))
+        rules.append(gauss_rule(al, be))
+    best = None
+    for x in np.concatenate([r[0] for r in rules]):
+        L = np.array([slq_lower_bound(theta, w, x) for theta, w in rules])
+        est = n * L.mean()
+        se = n * L.std(ddof=1) / math.sqrt(probes) if probes > 1 else 0.0
+        if est - z * se >= k and (best is None or x < best):
+            best = float(x)
+    return best
+
+
+def slq_lower_bound(theta: np.ndarray, w: np.ndarray, x: float) -> float:
+    """Lower bound of a spectral distribution at x from its Gauss rule (nodes theta ascending,
+    weights w): with theta_j the last node <= x, F(x) >= F(theta_j - 0) >= w_1 + ... + w_{j-1}
+    (Chebyshev-Markov-Stieltjes); 0 when no node lies at or below x."""
+    j = int(np.count_nonzero(theta <= x))
+    return float(w[: max(j - 1, 0)].sum())
+
+
 def threshold_from_count_svd(A: np.ndarray, k: int, p: int, q: int, seed: int) -> float:
     """sigma_hat_k <= sigma_k: square root of the k-th largest Ritz value of A^T A on
     span((A^T A)^(q+1) Om) (subspace iteration, each block orthonormalised before the next
@@ -330,8 +394,16 @@ def qdwhp_eig(A: np.ndarray, opts: EigOptions) -> EigResult:
     lam_lo = lo_raw - 0.01 * spread
     lam_hi = hi_raw + 0.01 * spread
 
-    # Threshold for the requested count (Cauchy interlacing), with the width guard.
-    t = threshold_from_count_eig(A, eps_side, k, lam_hi, opts.block_extra, opts.power_steps, opts.seed)
+    # Threshold for the requested count: the k-th Ritz value of a block Krylov space (Cauchy
+    # interlacing), or, when that basis would be too wide for n >= SLQ_MIN_N, the stochastic
+    # Lanczos quadrature estimate; then the width guard.
+    b = min(n, k + opts.block_extra)
+    wide = (opts.power_steps + 1) * b > min(n // 8, KRYLOV_MAX_COLS)
+    t = None
+    if wide and n >= SLQ_MIN_N:
+        t = threshold_from_count_eig_slq(A, eps_side, k, opts.seed)
+    if t is None:
+        t = threshold_from_count_eig(A, eps_side, k, lam_hi, opts.block_extra, opts.power_steps, opts.seed)
     t += 1e-10 * spread
     t = max(t, lam_lo + opts.guard * (lam_hi - lam_lo))
 

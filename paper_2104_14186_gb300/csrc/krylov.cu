@@ -4,7 +4,7 @@
 //
 // Lanczos runs with full reorthogonalisation (classical Gram-Schmidt, twice) and
 // keeps every scalar on the device: the host only enqueues the steps.  Only the
-// extreme eigenpairs of the tridiagonal T (at most 48 x 48) are needed: the extreme
+// extreme eigenpairs of the tridiagonal T (at most 64 x 64) are needed: the extreme
 // Ritz values and their residual norms beta_m |s_{m,i}| are the output.
 #include "internal.h"
 #include "krylov.h"
@@ -138,7 +138,7 @@ __global__ void normalize_kernel(int n, double* q) {
 // by two steps of inverse iteration with T - x I factored as L D L^T, x just outside
 // the spectrum so the factorisation is definite.  Writes theta_min, its residual norm
 // beta_{m-1} |s_{m-1}|, theta_max and its residual norm.
-constexpr int kMaxT = 48;
+constexpr int kMaxT = 64;
 
 __device__ int sturm_count(const double* al, const double* be, int m, double x, double pivmin) {
   // number of eigenvalues of T below x: negative pivots of T - x I = L D L^T
@@ -255,13 +255,16 @@ inline int grid1d(size_t total, int threads) {
 // scale (a, predicted fraction at or below: c_a; b, predicted c_{b-1}).
 // out[0] = the candidate whose prediction is nearer 1/2 among those strictly inside (0, 1),
 // out[1] = its prediction, or -1 when there is none (or T is not finite).
-__global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  out[0] = 0.0;
-  out[1] = -1.0;
-  if (stt->nonfinite) return;
+// Gauss rule of the Lanczos tridiagonal in *stt (Golub and Welsch 1969): the nodes are the
+// eigenvalues of T, the weights the squared first components of its eigenvectors.  One thread:
+// implicit symmetric tridiagonal QR with the Wilkinson shift (Golub and Van Loan, Section 8.3),
+// accumulating only the first row of the eigenvector matrix.  On return d[0..m) holds the nodes
+// ascending and z their weights normalised to sum 1; false if T is not finite, the QR did not
+// converge or the weights are degenerate.
+__device__ bool gauss_rule_thread(const LanczosState* stt, double* d, double* z, int* m_out) {
+  if (stt->nonfinite) return false;
   const int m = max(1, min(stt->m, kMaxT));
-  double d[kMaxT], e[kMaxT], z[kMaxT];
+  double e[kMaxT];
   for (int i = 0; i < m; ++i) {
     d[i] = stt->alpha[i];
     e[i] = i + 1 < m ? stt->beta[i] : 0.0;
@@ -299,7 +302,7 @@ __global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
       z[k + 1] = -s * zk + c * z[k + 1];
     }
   }
-  if (hi > 0) return;   // not converged: no estimate
+  if (hi > 0) return false;   // not converged: no rule
   // nodes ascending with their weights
   double wsum = 0.0;
   for (int i = 0; i < m; ++i) {
@@ -316,13 +319,34 @@ __global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
     d[j + 1] = di;
     z[j + 1] = zi;
   }
-  if (!(wsum > 0.0) || !isfinite(wsum)) return;
+  if (!(wsum > 0.0) || !isfinite(wsum)) return false;
+  for (int i = 0; i < m; ++i) z[i] /= wsum;
+  *m_out = m;
+  return true;
+}
+
+// Split point of a spectrum from the Gauss quadrature of the Lanczos tridiagonal T, which
+// approximates the spectral distribution of the operator seen from the start vector.  With
+// the nodes ascending and c_j the cumulative weights, j* is the first node with c_j >= 1/2.
+// Ritz values converge onto clusters, so a node may coincide with an eigenvalue; the
+// candidates are therefore midpoints beside theta_j*, between it and the nearest nodes below
+// and above that differ from it by more than 1e-8 of the nodes' scale (a, predicted fraction
+// at or below: c_a; b, predicted c_{b-1}).
+// out[0] = the candidate whose prediction is nearer 1/2 among those strictly inside (0, 1),
+// out[1] = its prediction, or -1 when there is none (or T is not finite).
+__global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  out[0] = 0.0;
+  out[1] = -1.0;
+  double d[kMaxT], z[kMaxT];
+  int m = 0;
+  if (!gauss_rule_thread(stt, d, z, &m)) return;
   // cumulative weights; js = the first node at which they reach 1/2
   double cw[kMaxT];
   double acc = 0.0;
   int js = -1;
   for (int i = 0; i < m; ++i) {
-    acc += z[i] / wsum;
+    acc += z[i];
     cw[i] = acc;
     if (js < 0 && acc >= 0.5) js = i;
   }
@@ -350,6 +374,75 @@ __global__ void quadrature_median_kernel(const LanczosState* stt, double* out) {
   if (best_pred < 0.0 || !isfinite(best)) return;
   out[0] = best;
   out[1] = best_pred;
+}
+
+// Count-to-threshold by stochastic Lanczos quadrature (Ubaru, Chen and Saad 2017).  State v
+// holds the Lanczos tridiagonal of A from probe v; the nodes of A' = eps A are eps times its
+// nodes.  By the Chebyshev-Markov-Stieltjes inequalities, at any x the probe's spectral
+// distribution F_v(x) is at least L_v(x) = w_0 + ... + w_{j-2}, theta_{j-1} being the last
+// node <= x.  out[0] = the smallest node x of all probes with
+// n (mean_v L_v(x) - z stderr) >= k, out[1] = 1; out[1] = 0 when no node qualifies or a
+// rule failed.  Threads 0 .. probes-1 build the rules, then every thread scans candidates.
+constexpr int kSlqMaxProbes = 16;
+
+__global__ void __launch_bounds__(256) slq_threshold_kernel(const LanczosState* states, int probes, double eps,
+                                                            double n, double k, double z, double* out) {
+  __shared__ double nodes[kSlqMaxProbes][kMaxT];
+  __shared__ double cum[kSlqMaxProbes][kMaxT];   // cum[v][i] = w_0 + ... + w_i
+  __shared__ int msz[kSlqMaxProbes];
+  __shared__ int ok_all;
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  if (tid == 0) ok_all = 1;
+  __syncthreads();
+  if (tid < probes) {
+    double d[kMaxT], w[kMaxT];
+    int m = 0;
+    if (!gauss_rule_thread(states + tid, d, w, &m)) {
+      atomicAnd(&ok_all, 0);
+      m = 0;
+    }
+    double acc = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const int src = eps > 0.0 ? i : m - 1 - i;   // eps < 0 reverses the order
+      nodes[tid][i] = eps * d[src];
+      acc += w[src];
+      cum[tid][i] = acc;
+    }
+    msz[tid] = m;
+  }
+  __syncthreads();
+  double best = INFINITY;
+  if (ok_all) {
+    for (int c = tid; c < probes * kMaxT; c += blockDim.x) {
+      const int v = c / kMaxT, i = c % kMaxT;
+      if (i >= msz[v]) continue;
+      const double x = nodes[v][i];
+      double L[kSlqMaxProbes];
+      double mean = 0.0;
+      for (int u = 0; u < probes; ++u) {
+        int j = 0;
+        while (j < msz[u] && nodes[u][j] <= x) ++j;   // nodes of probe u at or below x
+        L[u] = j >= 2 ? cum[u][j - 2] : 0.0;
+        mean += L[u];
+      }
+      mean /= probes;
+      double ss = 0.0;
+      for (int u = 0; u < probes; ++u) ss += (L[u] - mean) * (L[u] - mean);
+      const double se = probes > 1 ? sqrt(ss / (probes - 1) / probes) : 0.0;
+      if (n * (mean - z * se) >= k) best = fmin(best, x);
+    }
+  }
+  red[tid] = best;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] = fmin(red[tid], red[tid + s]);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[0] = red[0];
+    out[1] = isfinite(red[0]) ? 1.0 : 0.0;
+  }
 }
 
 }  // namespace
@@ -433,6 +526,14 @@ qdwhp_status lanczos(cudaStream_t st, bool normal, int64_t m, int64_t n, const d
     QDWHP_LAUNCH_CHECK();
   }
   tridiag_extremes_kernel<<<1, 32, 0, st>>>(stt);
+  QDWHP_LAUNCH_CHECK();
+  return QDWHP_OK;
+}
+
+qdwhp_status slq_threshold(cudaStream_t st, const LanczosState* states, int probes, double eps, int64_t n, int64_t k,
+                           double z, double* out_dev) {
+  if (probes < 1 || probes > kSlqMaxProbes) return QDWHP_ERR_ARG;
+  slq_threshold_kernel<<<1, 256, 0, st>>>(states, probes, eps, (double)n, (double)k, z, out_dev);
   QDWHP_LAUNCH_CHECK();
   return QDWHP_OK;
 }

@@ -29,6 +29,11 @@ qdwhp_status lanczos(cudaStream_t st, bool normal, int64_t m, int64_t n, const d
 // a lanczos() run left in *stt (device): out_dev[0] = the point, out_dev[1] = the predicted
 // fraction of eigenvalues at or below it, -1 if no estimate.
 qdwhp_status quadrature_median(cudaStream_t st, const LanczosState* stt, double* out_dev);
+// Stochastic Lanczos quadrature threshold from `probes` (<= 16) Lanczos runs on A (states, device):
+// out_dev[0] = the smallest Gauss node x of A' = eps A at which n (mean lower bound of the probes'
+// spectral distributions - z stderr) >= k, out_dev[1] = 1; out_dev[1] = 0 if none qualifies.
+qdwhp_status slq_threshold(cudaStream_t st, const LanczosState* states, int probes, double eps, int64_t n, int64_t k,
+                           double z, double* out_dev);
 
 // ---- jacobi.cu ----
 struct JacobiState {

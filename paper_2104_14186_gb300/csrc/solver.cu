@@ -56,6 +56,16 @@ __global__ void index_scan_kernel(int n, const double* diagR, double tol, int* i
 // Block Krylov bases of the count-to-threshold step wider than min(n / 8, this) keep only the
 // last block: a wider basis would make its Rayleigh-Ritz problem cost as much as the solve.
 constexpr int64_t kKrylovMaxCols = 2048;
+// Such wide blocks take the stochastic Lanczos quadrature estimate instead from this order on
+// (below it the block's Ritz-value bound captures fewer unwanted eigenvalues): kSlqProbes start
+// vectors, kSlqSteps Lanczos steps each, kSlqZ standard errors of margin.
+constexpr int64_t kSlqMinN = 1024;
+constexpr int kSlqProbes = 16;
+constexpr int kSlqSteps = 64;
+constexpr double kSlqZ = 3.0;
+constexpr uint64_t kStreamSlq = 0x534C5150ull;   // "SLQP"
+constexpr int kLanczosMaxSteps = 64;
+uint64_t slq_probe_seed(uint64_t seed, int j) { return seed ^ kStreamSlq ^ ((uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull); }
 // Stopping tolerance of the reduced-problem Jacobi when its vectors are used: the
 // normalised off-diagonal inner products (computed in double-double) down to ~2u.
 constexpr double kJacobiTight = 4.5e-16;
@@ -70,6 +80,7 @@ bool emulated_products(const qdwhp_opts& o) {
 struct Common {
   // small-problem and control buffers shared by both drivers
   LanczosState* lst = nullptr;
+  LanczosState* slq = nullptr;   // EIG: the probes of the stochastic count-to-threshold estimate
   JacobiState* jst = nullptr;
   Schedule* sched = nullptr;
   ZoloSchedule* zsched = nullptr;
@@ -94,6 +105,7 @@ struct HostScalars {
 
 void carve_common(Arena& ar, int64_t m, int64_t n, int steps, Common& c) {
   c.lst = ar.take<LanczosState>(1);
+  c.slq = ar.take<LanczosState>(kSlqProbes);
   c.jst = ar.take<JacobiState>(1);
   c.sched = ar.take<Schedule>(1);
   c.zsched = ar.take<ZoloSchedule>(1);
@@ -101,7 +113,8 @@ void carve_common(Arena& ar, int64_t m, int64_t n, int steps, Common& c) {
   c.nonfinite = ar.take<unsigned>(4);
   c.vals = ar.take<double>(std::max<int64_t>(n, 1));
   c.order = ar.take<int>(std::max<int64_t>(n, 1));
-  c.lws = ar.take<double>(lanczos_ws_elems(m, n, std::max(1, std::min(steps, 48))));
+  (void)steps;
+  c.lws = ar.take<double>(lanczos_ws_elems(m, n, kLanczosMaxSteps));
   c.splitk_elems = std::min<size_t>(gemm_splitk_ws_elems(std::min<int64_t>(n, 2048), std::min<int64_t>(n, 2048)),
                                     size_t(8) << 20);
   c.splitk = ar.take<double>(c.splitk_elems);
@@ -269,37 +282,55 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
 
   // Threshold for the requested count: block Krylov space of P = lam_hi I - A' from k + p
   // SplitMix64 vectors (each block orthonormalised before the next product), Rayleigh-Ritz of A'
-  // on it; when (q+1) b > min(n/8, 2048) columns only the last block, P^(q+1) Om, is kept.
+  // on it, whose k-th Ritz value bounds the k-th eigenvalue (Cauchy interlacing).  When
+  // (q+1) b > min(n/8, 2048) columns: for n >= kSlqMinN the stochastic Lanczos quadrature
+  // estimate (an estimate only: the count check after Rayleigh-Ritz and the retries keep the
+  // k pairs guaranteed), else, or if it finds no node, only the last block, P^(q+1) Om, is kept.
   const int64_t b = std::min<int64_t>(n, k + o.block_extra);
   const int q = o.power_steps > 0 ? o.power_steps : 6;
   const bool krylov = (int64_t)(q + 1) * b <= std::min<int64_t>(n / 8, kKrylovMaxCols);
-  const int64_t width = krylov ? (q + 1) * b : b;
-  double* Y = w.X;           // n x b
-  double* Kb = w.S3;         // n x width
-  double* Qj = w.q.Z;        // n x b
-  double* AK = w.q.Y;        // n x width
-  QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Y, n));
-  for (int j = 0; j <= q; ++j) {
-    double* Qdst = krylov ? Kb + (int64_t)j * b * n : Qj;
-    QDWHP_TRY(orth(st, n, b, Y, Qdst, w.f, w.qr_scratch));
-    if (j < q || !krylov) {
-      QDWHP_TRY(axpby(st, n, b, lam_hi, Qdst, n, 0.0, Y, n));
-      QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Qdst, n, 1.0, Y, n));
+  double theta_k = 0.0;
+  bool have_theta = false;
+  int sweeps = 0;
+  if (!krylov && n >= kSlqMinN) {
+    for (int j = 0; j < kSlqProbes; ++j)
+      QDWHP_TRY(lanczos(st, false, n, n, A, lda, kSlqSteps, slq_probe_seed(o.seed, j), w.c.lws, w.c.slq + j));
+    QDWHP_TRY(slq_threshold(st, w.c.slq, kSlqProbes, eps_side, n, k, kSlqZ, w.S1));
+    double got[2];
+    QDWHP_TRY(sync_read(st, got, w.S1, sizeof(got)));
+    if (got[1] > 0.0 && std::isfinite(got[0])) {
+      theta_k = got[0];
+      have_theta = true;
     }
   }
-  if (krylov) {
-    QDWHP_TRY(copy_matrix(st, n, width, Kb, n, AK, n));
-    QDWHP_TRY(orth(st, n, width, AK, Kb, w.f, w.qr_scratch));
-  } else {
-    QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
+  if (!have_theta) {
+    const int64_t width = krylov ? (q + 1) * b : b;
+    double* Y = w.X;           // n x b
+    double* Kb = w.S3;         // n x width
+    double* Qj = w.q.Z;        // n x b
+    double* AK = w.q.Y;        // n x width
+    QDWHP_TRY(fill_uniform(st, n, b, o.seed ^ kStreamBlock, Y, n));
+    for (int j = 0; j <= q; ++j) {
+      double* Qdst = krylov ? Kb + (int64_t)j * b * n : Qj;
+      QDWHP_TRY(orth(st, n, b, Y, Qdst, w.f, w.qr_scratch));
+      if (j < q || !krylov) {
+        QDWHP_TRY(axpby(st, n, b, lam_hi, Qdst, n, 0.0, Y, n));
+        QDWHP_TRY(gemm(st, false, false, n, b, n, -eps_side, A, lda, Qdst, n, 1.0, Y, n));
+      }
+    }
+    if (krylov) {
+      QDWHP_TRY(copy_matrix(st, n, width, Kb, n, AK, n));
+      QDWHP_TRY(orth(st, n, width, AK, Kb, w.f, w.qr_scratch));
+    } else {
+      QDWHP_TRY(orth(st, n, b, Y, Kb, w.f, w.qr_scratch));
+    }
+    QDWHP_TRY(gemm(st, false, false, n, width, n, eps_side, A, lda, Kb, n, 0.0, AK, n));
+    QDWHP_TRY(gemm(st, true, false, width, width, n, 1.0, Kb, n, AK, n, 0.0, w.S1, width, FULL, 0.0, w.c.splitk,
+                   w.c.splitk_elems));
+    QDWHP_TRY(small_sym_eig(st, width, lam_lo, lam_hi, o.seed, w, o.jacobi_max_sweeps, hs, &sweeps, true));
+    QDWHP_TRY(select_sort(st, width, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
+    QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
   }
-  QDWHP_TRY(gemm(st, false, false, n, width, n, eps_side, A, lda, Kb, n, 0.0, AK, n));
-  QDWHP_TRY(gemm(st, true, false, width, width, n, 1.0, Kb, n, AK, n, 0.0, w.S1, width, FULL, 0.0, w.c.splitk,
-                 w.c.splitk_elems));
-  int sweeps = 0;
-  QDWHP_TRY(small_sym_eig(st, width, lam_lo, lam_hi, o.seed, w, o.jacobi_max_sweeps, hs, &sweeps, true));
-  QDWHP_TRY(select_sort(st, width, w.c.vals, 1.0, INFINITY, w.c.order, w.c.ints + 1));
-  QDWHP_TRY(gather_values(st, 1, w.c.vals, w.c.order + (k - 1), w.S1));
   // Step 2's polar iterations: QDWH (iters_eig Cholesky-based steps from ell_0 = s) or
   // Zolo-PD of order zolo_r until ell_k = 1.
   const bool zolo = o.zolo_r > 0;
@@ -311,8 +342,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
     QDWHP_TRY(dwh_schedule(st, nullptr, o.s_eig, o.iters_eig, INFINITY, w.c.sched));
     QDWHP_CUDA_TRY(cudaMemcpyAsync(&hs.sched, w.c.sched, sizeof(Schedule), cudaMemcpyDeviceToHost, st));
   }
-  double theta_k = 0.0;
-  QDWHP_TRY(sync_read(st, &theta_k, w.S1, sizeof(double)));
+  if (!have_theta) QDWHP_TRY(sync_read(st, &theta_k, w.S1, sizeof(double)));
   double t = theta_k + 1e-10 * spread;
   t = std::max(t, lam_lo + o.guard * (lam_hi - lam_lo));
   const double s = o.s_eig;

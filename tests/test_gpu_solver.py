@@ -237,3 +237,21 @@ def test_host_entry_points_equal_device_ones(Q):
         sh = Q.svd(torch.from_numpy(np.ascontiguousarray(A)), k=q.k)     # row-major: the binding reorders
         assert torch.equal(sh.sigma, sd.sigma.cpu()) and torch.equal(sh.U, sd.U.cpu())
         assert torch.equal(sh.V, sd.V.cpu())
+
+
+# ---- stochastic Lanczos quadrature threshold (wide blocks, n >= 1024) ----
+
+@pytest.mark.parametrize("n,frac,kind,seed", [(1024, 0.25, "uniform", 9), (2048, 0.20, "clustered", 3000),
+                                              (1500, 0.05, "uniform", 3)])
+def test_eig_slq_threshold_vs_oracle(Q, n, frac, kind, seed):
+    """Wide count-to-threshold blocks at n >= 1024 take the stochastic Lanczos quadrature
+    estimate (16 probes x 64 steps) on the device and in the oracle; the k pairs match the
+    oracle and the constructed spectrum at the FP64 tolerances, with no retry."""
+    p = I.eig_uniform(n, seed, frac) if kind == "uniform" else I.eig_clustered(n, seed, frac)
+    r = Q.eig(dev(p.A), k=p.k)
+    ref = O.qdwhp_eig(p.A, O.EigOptions(k=p.k))
+    check_eig(p, r, ref if kind == "uniform" else None)
+    if kind == "clustered":   # inside the 1 +- 1e-6 cluster the eigenvectors are not unique
+        assert np.max(np.abs(r.lam.cpu().numpy() - ref.lam)) <= LAM_TOL
+    assert r.info["retries"] == 0
+    print(f"n={n} k={p.k}: ell {r.info['ell']} (oracle {ref.ell}), t {r.info['t']:.6f} (oracle {ref.t:.6f})")
