@@ -291,7 +291,12 @@ def run_ours(args):
     peaks = load_peaks()
     bf16 = peaks.get("bf16_tflops")
     peak = bf16 * NOMINAL_FP64_OVER_BF16 if bf16 else 1.9e3 * NOMINAL_FP64_OVER_BF16
-    achieved = prof["gemm_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else None
+    # the DMMA kernel's own launches (records with split-K slices >= 1; -1 and -2 mark the
+    # tensor-core products of the emulated and mixed precisions)
+    dmma = [r for r in Q.profile_records() if r[4] >= 1]
+    dmma_ms = sum(r[5] for r in dmma)
+    dmma_flops = sum((r[1] * (r[1] + 1) * r[2]) if r[3] else 2.0 * r[0] * r[1] * r[2] for r in dmma)
+    achieved = dmma_flops / (dmma_ms / 1e3) / 1e12 if dmma_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -311,8 +316,8 @@ def run_ours(args):
             # DRAM bytes of one 4096^3 launch from the ncu capture in profiles/ (the kernel is unchanged)
             "traffic": DGEMM_4096_TRAFFIC_BYTES, "traffic_launch": "dgemm_kernel<32,32,0,0> 4096^3",
             "peak_source": "measured bf16 dense burst x nominal FP64/BF16 ratio (1.25/2250), of measured",
-            "gemm_share_of_step": prof["gemm_ms"] / prof_total_ms if prof_total_ms > 0 else None,
-            "gemm_launches_per_solve": prof["gemm_launches"] / prof_steps,
+            "gemm_share_of_step": dmma_ms / prof_total_ms if prof_total_ms > 0 else None,
+            "gemm_launches_per_solve": len(dmma) / prof_steps,
             "measured": f"CUDA events around every GEMM launch in {prof_steps} instrumented solves run after "
                         "the timed steps (same workload, workspace and stream)",
         },
@@ -324,6 +329,11 @@ def run_ours(args):
     if args.precision in ("emulated", "mixed-emulated"):
         line["all_products_fp64_equivalent"] = line["roofline"]
         line["roofline"] = emulated_roofline(Q, prof_total_ms, bf16 if bf16 else 1.9e3)
+    if args.precision in ("mixed", "mixed-emulated"):
+        key = "roofline" if args.precision == "mixed" else "roofline_fp32_products"
+        if args.precision == "mixed":
+            line["fp64_products"] = line["roofline"]
+        line[key] = bf16x6_roofline(Q, prof_total_ms, bf16 if bf16 else 1.9e3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
         oracle_solve(p.A, k)
@@ -368,6 +378,28 @@ def emulated_roofline(Q, total_ms, bf16_peak):
             "share_of_step": ms / total_ms, "launches": len(recs)}
 
 
+B6_PAIRS = 6          # BF16 slice products per FP32-accurate product
+
+
+def bf16x6_roofline(Q, total_ms, bf16_peak):
+    """Roofline of the FP32-accurate BF16x6 kernel from the per-GEMM records (split slot -2): its
+    arithmetic is BF16 tensor work, six slice products of each FP32 product (algorithmic count of
+    the unpadded shape)."""
+    recs = [r for r in Q.profile_records() if r[4] == -2]
+    if not recs:
+        return None
+    ms = sum(r[5] for r in recs)
+    fp32_flops = sum((r[1] * (r[1] + 1) * r[2]) if r[3] else 2.0 * r[0] * r[1] * r[2] for r in recs)
+    achieved = B6_PAIRS * fp32_flops / (ms / 1e3) / 1e12
+    return {"kernel": "b6_umma_kernel (FP32 products as 6 BF16 slice products, tcgen05.mma kind::f16, FP32 sums in "
+                      "TMEM)",
+            "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": achieved / bf16_peak, "traffic": None,
+            "peak_source": "measured bf16 dense burst (cuBLAS), of measured",
+            "fp32_equivalent_tflops": fp32_flops / (ms / 1e3) / 1e12,
+            "share_of_step": ms / total_ms, "launches": len(recs)}
+
+
 def run_kernel_gemm(args):
     """Isolated DMMA GEMM C = A B (4096^3, FP64) through qdwhp_gemm_f64, one launch per step."""
     import torch
@@ -385,10 +417,17 @@ def run_kernel_gemm(args):
     lib = Q.lib()
 
     emulated = args.precision == "emulated"
+    fp32 = args.precision == "mixed"
     ws = Q.workspace(lib.qdwhp_gemm_f64_emulated_workspace_bytes(n, n, n)) if emulated else None
+    if fp32:
+        A, B, Cm = A.float(), B.float(), Cm.float()
+        ws = Q.workspace(lib.qdwhp_gemm_f32_bf16x6_workspace_bytes(n, n, n))
 
     def step():
-        if emulated:
+        if fp32:
+            rc = lib.qdwhp_gemm_f32_bf16x6(0, 0, n, n, n, 1.0, A.data_ptr(), n, B.data_ptr(), n, 0.0,
+                                           Cm.data_ptr(), n, ws.data_ptr(), ws.numel(), st.cuda_stream)
+        elif emulated:
             rc = lib.qdwhp_gemm_f64_emulated(0, 0, n, n, n, 1.0, A.data_ptr(), n, B.data_ptr(), n, 0.0,
                                              Cm.data_ptr(), n, ws.data_ptr(), ws.numel(), st.cuda_stream)
         else:
@@ -412,6 +451,13 @@ def run_kernel_gemm(args):
     peaks = load_peaks()
     peak = peaks.get("bf16_tflops", 1.9e3) * NOMINAL_FP64_OVER_BF16
     tf = 2.0 * n ** 3 / (statistics.median(ms) / 1e3) / 1e12
+    if fp32:
+        bf16_peak = peaks.get("bf16_tflops", 1.9e3)
+        bf16_tf = B6_PAIRS * 2.0 * n ** 3 / (statistics.median(ms) / 1e3) / 1e12
+        print(json.dumps({"kernel": "b6 split + b6_umma_kernel via qdwhp_gemm_f32_bf16x6", "m": n, "n": n, "k": n,
+                          "ms_median": statistics.median(ms), "fp32_equivalent_tflops": tf, "bf16_tflops": bf16_tf,
+                          "bf16_peak": bf16_peak, "bf16_frac": bf16_tf / bf16_peak}), flush=True)
+        return
     if emulated:
         bf16_peak = peaks.get("bf16_tflops", 1.9e3)
         bf16_tf = OZ_PAIRS * 2.0 * n ** 3 / (statistics.median(ms) / 1e3) / 1e12
@@ -426,7 +472,9 @@ def run_kernel_gemm(args):
 
 
 def run_eig_large(args):
-    """The n = 16384 EIG workload (clustered spectrum), 1 % or 20 % largest, timed per solve."""
+    """The n = 16384 EIG workload (clustered spectrum), 1 % or 20 % largest, timed per solve, for
+    each precision of --precisions (default: --precision); with --cpu-baseline the FP64 oracle is
+    timed once on the host cores on the same matrix."""
     import numpy as np
     import torch
 
@@ -438,36 +486,76 @@ def run_eig_large(args):
     frac = args.fraction
     A, lam, k = I.eig_clustered_device(16384, 3000, frac)
     n = A.shape[0]
-    prec = precision_code(Q, args.precision)
-    o = Q.default_opts(precision=prec, zolo_r=args.zolo)
-    ws = Q.workspace(Q.lib().qdwhp_eig_workspace_bytes(n, __import__("ctypes").byref(o)))
-    for _ in range(args.warmup):
-        r = Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
-    torch.cuda.synchronize()
-    ms = []
-    Q.profile_begin()
-    for _ in range(args.steps):
+    peak = load_peaks().get("bf16_tflops", 1.9e3) * NOMINAL_FP64_OVER_BF16
+    true = np.sort(lam)[::-1][:k]
+    nA = torch.linalg.norm(A)
+    for name in (args.precisions.split(",") if args.precisions else [args.precision]):
+        prec = precision_code(Q, name)
+        o = Q.default_opts(precision=prec, zolo_r=args.zolo)
+        ws = Q.workspace(Q.lib().qdwhp_eig_workspace_bytes(n, __import__("ctypes").byref(o)))
+        for _ in range(args.warmup):
+            r = Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        # GEMM share from one instrumented solve after the timed ones
+        Q.profile_begin()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
+        Q.eig(A, k=k, ws=ws, precision=prec, zolo_r=args.zolo)
         e1.record()
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    prof = Q.profile_end()
-    true = np.sort(lam)[::-1][:k]
-    err = float(np.max(np.abs(r.lam.cpu().numpy() - true)))
-    V = r.V
-    res = (torch.linalg.norm(A @ V - V * r.lam[None, :]) / torch.linalg.norm(A)).item()
-    ell = r.info["ell"]
-    fl = 3 * (n ** 3 + n ** 3 / 3 + 2 * n ** 3) + 4 / 3 * n ** 3 + 4 * n * n * ell + 2 * n * ell ** 2 + 9 * ell ** 3 \
-        + 2 * n * ell * k
-    t = statistics.median(ms) / 1e3
-    print(json.dumps({"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})",
-                      "precision": args.precision, "zolo_r": args.zolo, "ell": ell,
-                      "ms_median": 1e3 * t, "solves_per_s": 1 / t, "alg_tflops": fl / t / 1e12,
-                      "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9,
-                      "gemm_share": prof["gemm_ms"] / sum(ms), "lam_err": err, "resid": res,
-                      "jacobi_sweeps": r.info["jacobi_sweeps"], "dc_nodes": r.info["dc_nodes"]}), flush=True)
+        prof = Q.profile_end()
+        prof_ms = e0.elapsed_time(e1)
+        err = float(np.max(np.abs(r.lam.cpu().numpy() - true)))
+        V = r.V
+        res = (torch.linalg.norm(A @ V - V * r.lam[None, :]) / nA).item()
+        orth = torch.linalg.norm(V.T @ V - torch.eye(k, dtype=torch.float64, device=V.device)).item()
+        ell = r.info["ell"]
+        fl = 3 * (n ** 3 + n ** 3 / 3 + 2 * n ** 3) + 4 / 3 * n ** 3 + 4 * n * n * ell + 2 * n * ell ** 2 \
+            + 9 * ell ** 3 + 2 * n * ell * k
+        t = statistics.median(ms) / 1e3
+        del ws
+        line = {"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})",
+                "precision": name, "zolo_r": args.zolo, "ell": ell, "ms_median": 1e3 * t, "steps": args.steps,
+                "solves_per_s": 1 / t, "alg_tflops": fl / t / 1e12, "alg_frac_of_fp64_peak": fl / t / 1e12 / peak,
+                "fp64_peak_tflops": peak,
+                "gemm_tflops": prof["gemm_flops"] / prof["gemm_ms"] * 1e-9 if prof["gemm_ms"] else None,
+                "gemm_share": prof["gemm_ms"] / prof_ms, "lam_err": err / float(np.max(np.abs(lam))),
+                "resid": res, "orth": orth, "jacobi_sweeps": r.info["jacobi_sweeps"], "dc_nodes": r.info["dc_nodes"],
+                "it_f32": r.info["it_f32"]}
+        print(json.dumps(line), flush=True)
+    if args.cpu_baseline:
+        # Bounded sample of the FP64 oracle on the host cores: its first Cholesky-based QDWH step
+        # (eq. practical-polar-chol, 10/3 n^3 flops) on this matrix, shifted and scaled as the
+        # solver does, scaled to one solve by the algorithmic flop count (a full solve at this
+        # size takes tens of minutes on the host).
+        import oracle as O
+        X = A.cpu().numpy()
+        del A
+        torch.cuda.empty_cache()
+        t_thr, mu = r.info["t"], r.info["mu"]      # A' = -A, B = A' + t I (units of A), mu = lambda_min(B)
+        s_eig = 0.2
+        X *= -(1.0 - s_eig) / abs(mu)
+        X[np.diag_indices(n)] += (1.0 - s_eig) * t_thr / abs(mu) - s_eig
+        a, b, c, _ = O.dwh_weights(s_eig)
+        t0 = time.perf_counter()
+        O.qdwh_chol_step(X, a, b, c)
+        dt = time.perf_counter() - t0
+        per_solve = dt * fl / (10.0 / 3.0 * n ** 3)
+        print(json.dumps({"workload": f"QDWHpartial-EIG n={n} clustered, {100 * frac:g}% largest (k={k})",
+                          "cpu_baseline": {"value": 1.0 / per_solve, "unit": "solves/s", "cores": os.cpu_count(),
+                                           "kind": "oracle", "sample_seconds": dt,
+                                           "sample": "one Cholesky-based QDWH step of the numpy/LAPACK FP64 oracle "
+                                                     f"on this n={n} matrix (10/3 n^3 flops), scaled to a solve by the "
+                                                     f"algorithmic flop count of the GPU run (ell={ell})"}}),
+              flush=True)
 
 
 def run_gesvd(args):
@@ -683,6 +771,10 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=16)
     ap.add_argument("--rate", type=float, default=0.0)
     ap.add_argument("--fraction", type=float, default=0.01)
+    ap.add_argument("--precisions", default=None,
+                    help="--eig16384: comma-separated precisions to time on the same matrix")
+    ap.add_argument("--cpu-baseline", action="store_true",
+                    help="--eig16384: also time the FP64 oracle once on the host cores")
     args = ap.parse_args()
     if args.eig16384:
         run_eig_large(args)

@@ -345,6 +345,21 @@ QDWHP_API qdwhp_status qdwhp_gemm_f64_emulated(int transa, int transb, int64_t m
                                                void* stream);
 
 /*
+ * C = alpha * op(A) * op(B) + beta * C in FP32 (A, B, C float, column-major), FP32-accurate, on
+ * the BF16 tensor cores: each entry is split into three bfloat16 slices (x = h + m + l, each the
+ * rounding of what the previous ones leave), the six slice products with s + t <= 2 run as
+ * tcgen05 MMAs into one FP32 accumulator, so the error is that of an FP32 product (about 2^-24
+ * relative per term plus FP32 rounding of the sums).  Not part of the paper: the products of the
+ * FP32 Cholesky-based QDWH steps (eq. practical-polar-chol) of QDWHP_MIXED run on it.
+ *   workspace/ws_bytes: at least qdwhp_gemm_f32_bf16x6_workspace_bytes(m, n, k), 16-byte aligned.
+ *   beta == 0 never reads C.  A NaN or Inf in op(A) or op(B) reaches the affected rows and columns.
+ */
+QDWHP_API size_t qdwhp_gemm_f32_bf16x6_workspace_bytes(int64_t m, int64_t n, int64_t k);
+QDWHP_API qdwhp_status qdwhp_gemm_f32_bf16x6(int transa, int transb, int64_t m, int64_t n, int64_t k, float alpha,
+                                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                                             float* C, int64_t ldc, void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * Z = L L^T, lower Cholesky factor of the symmetric positive definite n x n Z in
  * place (lower triangle read and written; the strict upper triangle is left as is).
  * The factorisation W = chol(Z) of eq. practical-polar-chol with W = L^T.

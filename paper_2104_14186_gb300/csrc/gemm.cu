@@ -350,12 +350,29 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, float a
 
 }  // namespace
 
+thread_local void* t_f32tc_ws = nullptr;
+thread_local size_t t_f32tc_bytes = 0;
+
+Fp32TensorScope::Fp32TensorScope(void* ws, size_t bytes) : prev_ws(t_f32tc_ws), prev_bytes(t_f32tc_bytes) {
+  t_f32tc_ws = ws;
+  t_f32tc_bytes = bytes;
+}
+Fp32TensorScope::~Fp32TensorScope() {
+  t_f32tc_ws = prev_ws;
+  t_f32tc_bytes = prev_bytes;
+}
+
 qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
                   int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, Uplo uplo,
                   float diag_add) {
   if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
   if (m == 0 || n == 0) return QDWHP_OK;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return QDWHP_ERR_ARG;
+  // Below 256 the slice splitting and the 128 x 128 tiles cost more than the CUDA-core kernel
+  // (products of the triangular-solve recursion ran at 26 TFLOP/s FP32-equivalent at 128).
+  if (t_f32tc_ws != nullptr && m >= 256 && n >= 256 && k >= 256 && gemm_bf16x6_ws_bytes(m, n, k) <= t_f32tc_bytes)
+    return gemm_bf16x6(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add, t_f32tc_ws,
+                       t_f32tc_bytes);
   const int M = (int)m, N = (int)n, K = (int)k;
   dim3 grid(ceil_div(M, 64) * ceil_div(N, 64));
   if (!ta && !tb)

@@ -81,10 +81,26 @@ struct EmulationScope {
   void* prev_ws;
   size_t prev_bytes;
 };
-// FP32 on the CUDA cores (reduced-precision QDWH steps).
+// FP32 (reduced-precision QDWH steps): on the CUDA cores, or, with an Fp32TensorScope installed,
+// products with m, n, k >= 256 as the BF16x6 split on the tensor cores (bf16x6.cu).
 qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
                   int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, Uplo uplo = FULL,
                   float diag_add = 0.0f);
+// ---- bf16x6.cu ----
+// FP32-accurate product from six BF16 slice products on tcgen05 (three slices per operand,
+// FP32 accumulation); needs gemm_bf16x6_ws_bytes(m, n, k) bytes of scratch (16-byte aligned).
+size_t gemm_bf16x6_ws_bytes(int64_t m, int64_t n, int64_t k);
+qdwhp_status gemm_bf16x6(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
+                         const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                         Uplo uplo, float diag_add, void* ws, size_t ws_bytes);
+// Per host thread: while a scratch is installed, the FP32 gemm() routes products with
+// m, n, k >= 256 whose scratch fits to gemm_bf16x6.
+struct Fp32TensorScope {
+  Fp32TensorScope(void* ws, size_t bytes);
+  ~Fp32TensorScope();
+  void* prev_ws;
+  size_t prev_bytes;
+};
 
 // ---- elementwise.cu ----
 // Y = alpha X + beta Y (+ diag_add on the diagonal); beta == 0 never reads Y.

@@ -34,6 +34,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "umma.cuh"
 
 namespace qdwhp {
 
@@ -159,34 +160,13 @@ __global__ void oz_split_kernel(int rows, int k, int rows_pad, int k_pad, const 
 // in tensor memory (two 128-column accumulators), and every mbarrier wait is bounded: on a
 // timeout the tile is written as NaN and err is set.
 constexpr int kUmN = 128;
-constexpr int kUmAtomK = 64;                                    // K of one 128-byte swizzle atom row
+constexpr int kUmAtomK = umma::kAtomK;                           // K of one 128-byte swizzle atom row
 constexpr int kUmBK = 128;                                      // K per stage: two atoms per operand
 constexpr int kUmStages = 3;
 constexpr uint32_t kUmAtomBytes = 128 * kUmAtomK * 2;           // 16 KB: 128 rows x 64 K
 constexpr uint32_t kUmTileBytes = 128 * kUmBK * 2;              // 32 KB per operand and stage
 constexpr uint32_t kUmStageBytes = 2 * kUmTileBytes;
 constexpr size_t kUmSmemBytes = (size_t)kUmStages * kUmStageBytes + 1024;
-constexpr int kUmSpin = 1 << 24;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// shared-memory matrix descriptor: start >> 4, leading byte offset 16 (unused with swizzle),
-// stride byte offset 1024 (next 8-row atom), descriptor version 1, 128-byte swizzle
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-               : "r"(taddr));
-}
 
 // ---- warp-specialised TMA + tcgen05 digit-product kernel ----
 //
@@ -201,29 +181,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // flush warps derive the run schedule from the pair table (no per-step synchronisation).
 constexpr int kWsThreads = 288;
 constexpr int kWsRunSteps = kOzBudget / kUmBK;   // K blocks per run at most (exact FP32 sums)
-
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (int it = 0; it < kUmSpin; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((it & 1023) == 1023 && *abort_flag) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
 
 __global__ void __launch_bounds__(kWsThreads, 1)
     oz_umma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
@@ -243,20 +200,20 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   const int total = npairs * nkb;
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::smem_addr(&tmem_base)),
                  "r"(2 * kUmN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 256) {
     for (int s = 0; s < kUmStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_full[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_empty[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_empty[s])));
     }
     for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_run[b])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_addr(&bar_free[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_run[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(umma::smem_addr(&bar_free[b])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_done)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_done)));
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -269,17 +226,17 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 
   if (warp == 8) {
     if (lane == 0) {
-      const uint32_t sbase = smem_addr(smem);
+      const uint32_t sbase = umma::smem_addr(smem);
       int lp = 0, lkb = 0;
       auto issue_load = [&](int stage) {
-        const uint32_t bar = smem_addr(&bar_full[stage]);
+        const uint32_t bar = umma::smem_addr(&bar_full[stage]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kUmStageBytes)
                      : "memory");
         const uint32_t dA = sbase + (uint32_t)stage * kUmStageBytes, dB = dA + kUmTileBytes;
 #pragma unroll
         for (int at = 0; at < kUmBK / kUmAtomK; ++at) {
-          tma_load_3d(dA + at * kUmAtomBytes, &mapA, lkb * kUmBK + at * kUmAtomK, m0, (int)c_pairs.s[lp], bar);
-          tma_load_3d(dB + at * kUmAtomBytes, &mapB, lkb * kUmBK + at * kUmAtomK, n0, (int)c_pairs.t[lp], bar);
+          umma::tma_load_3d(dA + at * kUmAtomBytes, &mapA, lkb * kUmBK + at * kUmAtomK, m0, (int)c_pairs.s[lp], bar);
+          umma::tma_load_3d(dB + at * kUmAtomBytes, &mapB, lkb * kUmBK + at * kUmAtomK, n0, (int)c_pairs.t[lp], bar);
         }
         if (++lkb == nkb) {
           lkb = 0;
@@ -293,12 +250,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       bool run_first = true;
       for (int step = 0; step < total && ok; ++step) {
         const int stage = step % kUmStages;
-        if (!mbar_wait_or_abort(smem_addr(&bar_full[stage]), (uint32_t)((step / kUmStages) & 1), abort_flag)) {
+        if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[stage]), (uint32_t)((step / kUmStages) & 1), abort_flag)) {
           ok = false;
           break;
         }
         if (run_first && run >= 2 &&
-            !mbar_wait_or_abort(smem_addr(&bar_free[run & 1]), (uint32_t)(((run >> 1) - 1) & 1), abort_flag)) {
+            !umma::mbar_wait_or_abort(umma::smem_addr(&bar_free[run & 1]), (uint32_t)(((run >> 1) - 1) & 1), abort_flag)) {
           ok = false;
           break;
         }
@@ -309,14 +266,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         for (int kk = 0; kk < kUmBK / 16; ++kk) {
           // atom kk / 4, 32-byte K step kk % 4 inside it
           const uint32_t off = (uint32_t)(kk / 4) * kUmAtomBytes + (uint32_t)(kk % 4) * 32;
-          const uint64_t da = umma_desc_sw128(a0 + off), db = umma_desc_sw128(b0 + off);
+          const uint64_t da = umma::desc_sw128(a0 + off), db = umma::desc_sw128(b0 + off);
           const uint32_t accum = (run_first && kk == 0) ? 0u : 1u;
           asm volatile(
               "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
               "l"(da), "l"(db), "r"(idesc), "r"(accum));
         }
-        umma_commit(smem_addr(&bar_empty[stage]));
+        umma::commit(umma::smem_addr(&bar_empty[stage]));
         ++steps_in_run;
         int np_ = cp, nkb_ = ckb + 1;
         if (nkb_ == nkb) {
@@ -325,7 +282,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         }
         const bool run_ends = np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || steps_in_run >= kWsRunSteps;
         if (run_ends) {
-          umma_commit(smem_addr(&bar_run[run & 1]));
+          umma::commit(umma::smem_addr(&bar_run[run & 1]));
           ++run;
           run_first = true;
           steps_in_run = 0;
@@ -334,7 +291,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         }
         const int nxt = step + kUmStages - 1;
         if (nxt < total) {
-          if (step >= 1 && !mbar_wait_or_abort(smem_addr(&bar_empty[(step - 1) % kUmStages]),
+          if (step >= 1 && !umma::mbar_wait_or_abort(umma::smem_addr(&bar_empty[(step - 1) % kUmStages]),
                                                (uint32_t)(((step - 1) / kUmStages) & 1), abort_flag)) {
             ok = false;
             break;
@@ -345,7 +302,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         ckb = nkb_;
       }
       if (!ok) *abort_flag = 1;
-      umma_commit(smem_addr(&bar_done));   // every MMA issued so far
+      umma::commit(umma::smem_addr(&bar_done));   // every MMA issued so far
     }
     __syncwarp();
   } else {
@@ -362,7 +319,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       const int level_steps = (q - p) * nkb;
       const double sc = c_pairs.scale[p];
       for (int done = 0; done < level_steps && ok; done += kWsRunSteps, ++run) {
-        if (!mbar_wait_or_abort(smem_addr(&bar_run[run & 1]), (uint32_t)((run >> 1) & 1), abort_flag)) {
+        if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_run[run & 1]), (uint32_t)((run >> 1) & 1), abort_flag)) {
           ok = false;
           break;
         }
@@ -370,19 +327,19 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           uint32_t v[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)((run & 1) * kUmN) + col_base + (uint32_t)(32 * h), v);
+          umma::tmem_ld32(tmem + lane_base + (uint32_t)((run & 1) * kUmN) + col_base + (uint32_t)(32 * h), v);
           asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
           for (int j = 0; j < 32; ++j) acc64[32 * h + j] = fma((double)__uint_as_float(v[j]), sc, acc64[32 * h + j]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_free[run & 1])) : "memory");
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_addr(&bar_free[run & 1])) : "memory");
       }
       p = q;
     }
     if (!ok) *abort_flag = 1;
-    if (!mbar_wait_or_abort(smem_addr(&bar_done), 0, abort_flag)) ok = false;
+    if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_done), 0, abort_flag)) ok = false;
     // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
     __syncwarp();
     const bool good = ok && !*abort_flag;
@@ -416,9 +373,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kUmN));
 }
 
-// Tensor maps of the digit slices: [slice][rows_pad][k_pad] bfloat16 seen as a 3-D tensor
-// (k innermost), box 64 x 128 x 1 (one swizzle atom) with the 128-byte swizzle the MMA
-// descriptors expect.
+}  // namespace
+
+namespace umma {
+
+namespace {
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -433,25 +392,31 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-qdwhp_status slice_map(CUtensorMap* map, const unsigned short* base, int rows_pad, int k_pad) {
+}  // namespace
+
+qdwhp_status slice_map(CUtensorMap* map, const unsigned short* base, int nslices, int rows_pad, int k_pad) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (enc == nullptr) {
     set_error_message("cuTensorMapEncodeTiled is not available from the driver");
     return QDWHP_ERR_CUDA;
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)kOzS};
+  const cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)nslices};
   const cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * k_pad * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)kUmAtomK, 128u, 1u};
+  const cuuint32_t box[3] = {(cuuint32_t)kAtomK, 128u, 1u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
-    set_error_message("cuTensorMapEncodeTiled rejected a digit-slice tensor map");
+    set_error_message("cuTensorMapEncodeTiled rejected a bfloat16 slice tensor map");
     return QDWHP_ERR_CUDA;
   }
   return QDWHP_OK;
 }
+
+}  // namespace umma
+
+namespace {
 
 qdwhp_status launch_umma_ws(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
                             const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta,
@@ -461,8 +426,8 @@ qdwhp_status launch_umma_ws(cudaStream_t st, int64_t m, int64_t n, int kp, int m
     return cudaFuncSetAttribute(oz_umma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
   }));
   CUtensorMap mapA, mapB;
-  QDWHP_TRY(slice_map(&mapA, Asl, mp, kp));
-  QDWHP_TRY(slice_map(&mapB, Bsl, np, kp));
+  QDWHP_TRY(umma::slice_map(&mapA, Asl, kOzS, mp, kp));
+  QDWHP_TRY(umma::slice_map(&mapB, Bsl, kOzS, np, kp));
   dim3 grid(np / kUmN, mp / 128);
   oz_umma_ws_kernel<<<grid, kWsThreads, kUmSmemBytes, st>>>(mapA, mapB, (int)m, (int)n, kp, ea, eb, alpha, beta, C,
                                                             ldc, (int)uplo, diag_add, err);

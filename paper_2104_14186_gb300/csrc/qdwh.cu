@@ -375,6 +375,24 @@ QDWHP_API qdwhp_status qdwhp_gemm_f64_emulated(int transa, int transb, int64_t m
                     FULL, 0.0, workspace, ws_bytes);
 }
 
+QDWHP_API size_t qdwhp_gemm_f32_bf16x6_workspace_bytes(int64_t m, int64_t n, int64_t k) {
+  return gemm_bf16x6_ws_bytes(m, n, k);
+}
+
+QDWHP_API qdwhp_status qdwhp_gemm_f32_bf16x6(int transa, int transb, int64_t m, int64_t n, int64_t k, float alpha,
+                                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                                             float* C, int64_t ldc, void* workspace, size_t ws_bytes, void* stream) {
+  if (m < 0 || n < 0 || k < 0) return QDWHP_ERR_ARG;
+  if (m == 0 || n == 0) return QDWHP_OK;
+  const int64_t rowsA = transa ? k : m, rowsB = transb ? n : k;
+  if (C == nullptr || ldc < m || lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB))
+    return QDWHP_ERR_ARG;
+  if (k > 0 && (A == nullptr || B == nullptr)) return QDWHP_ERR_ARG;
+  if (k > 0 && (workspace == nullptr || ((uintptr_t)workspace & 15) != 0)) return QDWHP_ERR_ARG;
+  return gemm_bf16x6((cudaStream_t)stream, transa != 0, transb != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                     FULL, 0.0f, workspace, ws_bytes);
+}
+
 QDWHP_API size_t qdwhp_potrf_workspace_bytes(int64_t n) {
   Arena ar;
   ar.dry = true;

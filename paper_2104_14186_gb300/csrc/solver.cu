@@ -174,6 +174,8 @@ struct EigWs {
   int dc_nodes = 0;      // splits of the last divide-and-conquer solve
   char* emu = nullptr;   // emulated FP64 products: their scratch
   size_t emu_bytes = 0;
+  char* f32tc = nullptr; // FP32 products of the reduced-precision steps on the tensor cores: their scratch
+  size_t f32tc_bytes = 0;
 };
 
 void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
@@ -194,6 +196,10 @@ void carve_eig(Arena& ar, int64_t n, const qdwhp_opts& o, EigWs& w) {
   if (emulated_products(o)) {
     w.emu_bytes = gemm_ozaki_ws_bytes(n, n, n);
     w.emu = ar.take<char>(w.emu_bytes);
+  }
+  if (fp32_steps(o)) {
+    w.f32tc_bytes = gemm_bf16x6_ws_bytes(n, n, n);
+    w.f32tc = ar.take<char>(w.f32tc_bytes);
   }
 }
 
@@ -243,6 +249,7 @@ qdwhp_status eig_impl(const double* A, int64_t n, int64_t lda, const qdwhp_opts&
   carve_eig(ar, n, o, w);
   if (!ar.ok()) return QDWHP_ERR_NOMEM;
   EmulationScope emu_scope(w.emu, w.emu_bytes);
+  Fp32TensorScope f32_scope(w.f32tc, w.f32tc_bytes);
   Timer timer(st);
   HostScalars hs;
   qdwhp_info inf;
@@ -445,6 +452,8 @@ struct SvdWs {
   double* At = nullptr;   // transposed input when m < n
   char* emu = nullptr;    // emulated FP64 products: their scratch
   size_t emu_bytes = 0;
+  char* f32tc = nullptr;  // FP32 products of the reduced-precision steps on the tensor cores
+  size_t f32tc_bytes = 0;
 };
 
 void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
@@ -465,6 +474,11 @@ void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, b
     const int64_t d = std::max(m, n);
     w.emu_bytes = gemm_ozaki_ws_bytes(d, d, d);
     w.emu = ar.take<char>(w.emu_bytes);
+  }
+  if (fp32_steps(o)) {
+    const int64_t d = std::max(m, n);
+    w.f32tc_bytes = gemm_bf16x6_ws_bytes(d, d, d);
+    w.f32tc = ar.take<char>(w.f32tc_bytes);
   }
 }
 
@@ -751,6 +765,7 @@ QDWHP_API qdwhp_status qdwhp_svd(const double* A, int64_t m, int64_t n, int64_t 
   carve_svd(ar, mm, nn, *opts, w, m < n);
   if (!ar.ok()) return QDWHP_ERR_NOMEM;
   EmulationScope emu_scope(w.emu, w.emu_bytes);
+  Fp32TensorScope f32_scope(w.f32tc, w.f32tc_bytes);
   if (m >= n) return svd_impl(A, m, n, lda, kk, *opts, sigma, U, ldu, V, ldv, w, info, st);
   // m < n: solve on A^T (n x m) and swap the roles of U and V (Section 4.2).
   QDWHP_TRY(transpose(st, m, n, A, lda, w.At, n));

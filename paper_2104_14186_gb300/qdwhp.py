@@ -118,6 +118,9 @@ SIGNATURES = {
     "qdwhp_gemm_f64_emulated": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P,
                                           C.c_size_t, P]),
     "qdwhp_gemm_f64": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P]),
+    "qdwhp_gemm_f32_bf16x6_workspace_bytes": (C.c_size_t, [I64, I64, I64]),
+    "qdwhp_gemm_f32_bf16x6": (C.c_int, [C.c_int, C.c_int, I64, I64, I64, C.c_float, P, I64, P, I64, C.c_float, P,
+                                        I64, P, C.c_size_t, P]),
     "qdwhp_potrf_workspace_bytes": (C.c_size_t, [I64]),
     "qdwhp_potrf_f64": (C.c_int, [I64, P, I64, P, C.c_size_t, C.POINTER(C.c_int), P]),
     "qdwhp_qr_workspace_bytes": (C.c_size_t, [I64, I64]),
@@ -517,6 +520,25 @@ def gemm_f64_emulated(A: torch.Tensor, B: torch.Tensor, transa=False, transb=Fal
     st = lib().qdwhp_gemm_f64_emulated(int(transa), int(transb), m, n, k, alpha, _ptr(Ac), A.shape[0], _ptr(Bc),
                                        B.shape[0], beta, _ptr(Ct), m, _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "qdwhp_gemm_f64_emulated")
+    return Ct.t()
+
+
+def gemm_f32_bf16x6(A: torch.Tensor, B: torch.Tensor, transa=False, transb=False, alpha=1.0, beta=0.0,
+                    Cmat: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """C = alpha op(A) op(B) + beta C in FP32 through qdwhp_gemm_f32_bf16x6 (three BF16 slices per
+    operand on the tensor cores); logical row-major float32 CUDA tensors in and out."""
+    if A.dtype != torch.float32 or B.dtype != torch.float32 or not A.is_cuda or not B.is_cuda:
+        raise ValueError("expected float32 CUDA tensors")
+    Ac, Bc = A.t().contiguous(), B.t().contiguous()
+    m = A.shape[1] if transa else A.shape[0]
+    k = A.shape[0] if transa else A.shape[1]
+    n = B.shape[0] if transb else B.shape[1]
+    Ct = (torch.zeros(n, m, dtype=torch.float32, device=A.device) if Cmat is None else Cmat.t().contiguous())
+    need = lib().qdwhp_gemm_f32_bf16x6_workspace_bytes(m, n, k)
+    ws = workspace(max(need, 1), A.device)
+    st = lib().qdwhp_gemm_f32_bf16x6(int(transa), int(transb), m, n, k, alpha, _ptr(Ac), A.shape[0], _ptr(Bc),
+                                     B.shape[0], beta, _ptr(Ct), m, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "qdwhp_gemm_f32_bf16x6")
     return Ct.t()
 
 
