@@ -334,6 +334,8 @@ def run_ours(args):
         if args.precision == "mixed":
             line["fp64_products"] = line["roofline"]
         line[key] = bf16x6_roofline(Q, prof_total_ms, bf16 if bf16 else 1.9e3)
+    if args.precision == "fp64" and not args.no_variants:
+        line["variants"] = precision_variants(Q, A, k, p, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
         oracle_solve(p.A, k)
@@ -345,6 +347,41 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def precision_variants(Q, A, k, p, dev, flush, stream, steps=3, warmup=2):
+    """The same workload in the other precision modes (a few timed solves each, after the
+    headline's timed region): emulated FP64 products, and FP32 Cholesky steps + emulated
+    products + 6 FP64 refinement steps on Q2 (both at the plain-FP64 tolerances), with their
+    accuracy against sigma* and the residuals."""
+    import torch
+    out = {}
+    sig_true = torch.from_numpy(p.sigma[:k]).to(dev)
+    nA = torch.linalg.norm(A)
+    for name, opts in (("emulated", {"precision": Q.FP64_EMULATED}),
+                       ("mixed-emulated", {"precision": Q.MIXED_EMULATED, "refine_steps": 6})):
+        o = Q.default_opts(**opts)
+        ws = Q.workspace(Q.lib().qdwhp_svd_workspace_bytes(M, N, __import__("ctypes").byref(o)), dev)
+        for _ in range(warmup):
+            r = Q.svd(A, k=k, ws=ws, **opts)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = Q.svd(A, k=k, ws=ws, **opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        out[name] = {"value": 1e3 / t, "unit": UNIT, "ms_per_step": t, "steps": steps, "options": {
+                         kk: int(v) for kk, v in opts.items()},
+                     "accuracy": {"sigma_err": (torch.max(torch.abs(r.sigma - sig_true)) / sig_true[0]).item(),
+                                  "residV": (torch.linalg.norm(A @ r.V - r.U * r.sigma[None, :]) / nA).item(),
+                                  "residU": (torch.linalg.norm(A.T @ r.U - r.V * r.sigma[None, :]) / nA).item()}}
+        del ws
+    return out
 
 
 def precision_code(Q, name):
@@ -641,6 +678,8 @@ def run_batched(args):
             autotune.save(res, args.tune)
         autotune.apply(res)
         tuning = {"table": res["table"], "path": args.tune}
+    if args.count is None:
+        args.count = 512
     sizes = I.batch_sizes(args.count, 4000)
     As = [I.eig_uniform_device(int(n), 4000 + i, 0.10)[0] for i, n in enumerate(sizes)]
     prec = precision_code(Q, args.precision)
@@ -669,9 +708,80 @@ def run_batched(args):
                       "max_lam_err": worst_lam, "max_resid": worst_res, "tuning": tuning}), flush=True)
 
 
+def serve_input(I, r):
+    """One request's matrix, generated on the GPU at its arrival (butterfly orthogonal factors,
+    known spectrum)."""
+    if r["kind"] == "eig":
+        return I.eig_butterfly_device(r["n"], r["seed"], r["fraction"])
+    return I.svd_butterfly_device(r["m"], r["n"], r["seed"], r["fraction"])
+
+
+def serve_once(Q, I, reqs, arrivals, prec_name, args, sample_every=40):
+    """Submits every request at its arrival time (its input drawn on the GPU then), releases
+    completed ones as it goes, and returns latency statistics and the sampled results."""
+    import numpy as np
+    import torch
+    prec = precision_code(Q, prec_name)
+    extra = {"precision": prec}
+    svd_extra = dict(extra, refine_steps=args.refine if prec_name.startswith("mixed") else 0)
+    q = Q.Queue(args.budget_gb << 30, max_slots=args.concurrency)
+    inflight, lat, done_t, first_t, samples = {}, [], [], None, []
+
+    def reap(block=False):
+        for rid in list(inflight):
+            st = q.poll(rid) if not block else 0
+            if block:
+                q.wait(rid, 3600000)
+            elif st == Q.QDWHP_PENDING:
+                continue
+            t_sub, _, t_done = q.times(rid)
+            lat.append(t_done - t_sub)
+            done_t.append(t_done)
+            i, A, spec, k = inflight.pop(rid)
+            if i % sample_every == 0:
+                res = q.wait(rid, 0)
+                samples.append((reqs[i]["kind"], A, spec, k, res))
+            q.release(rid)
+
+    torch.cuda.synchronize()
+    start = time.perf_counter()
+    for i, (r, ta) in enumerate(zip(reqs, arrivals)):
+        delay = start + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        A, spec, k = serve_input(I, r)
+        rid = q.submit_eig(A, k, **extra) if r["kind"] == "eig" else q.submit_svd(A, k, **svd_extra)
+        first_t = first_t if first_t is not None else q.times(rid)[0]
+        inflight[rid] = (i, A, spec, k)
+        reap()
+    reap(block=True)
+    q.close()
+    worst = {"lam_err": 0.0, "sigma_err": 0.0, "resid": 0.0}
+    for kind, A, spec, k, res in samples:
+        if kind == "eig":
+            true = torch.from_numpy(np.sort(spec)[::-1][:k].copy()).to(A.device)
+            worst["lam_err"] = max(worst["lam_err"], torch.max(torch.abs(res.lam - true)).item())
+            rr = torch.linalg.norm(A @ res.V - res.V * res.lam[None, :]) / torch.linalg.norm(A)
+        else:
+            true = torch.from_numpy(spec[:k].copy()).to(A.device)
+            worst["sigma_err"] = max(worst["sigma_err"], torch.max(torch.abs(res.sigma - true)).item())
+            rr = max(torch.linalg.norm(A @ res.V - res.U * res.sigma[None, :]),
+                     torch.linalg.norm(A.T @ res.U - res.V * res.sigma[None, :])) / torch.linalg.norm(A)
+        worst["resid"] = max(worst["resid"], rr.item())
+    return {"precision": prec_name, "solves_per_s": len(lat) / (max(done_t) - first_t),
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "max_ms": 1e3 * float(np.max(lat)), "wall_s": max(done_t) - first_t,
+            "checked": len(samples), "worst_sampled": worst}
+
+
 def run_serve(args):
     """Poisson-arrival stream of mixed EIG / SVD requests through the qdwhp queue (continuous
-    batching, HBM-budget admission); p50 / p99 latency and solves/s."""
+    batching, HBM-budget admission): 2000 requests by default, EIG n in [128, 8192], SVD n in
+    [128, 4096] with m in [n, 2n] and sigma log-spaced to 1e-10, fractions 1-20 %.  The arrival
+    rate is 80 % of the calibrated capacity of --rate-from (its first 48 requests submitted at
+    once), and every precision of --precisions sees the same arrivals.  Reports p50 / p99
+    latency (completion - submission) and solves/s, and the worst error of every 40th result
+    against its known spectrum."""
     import numpy as np
     import torch
 
@@ -680,52 +790,36 @@ def run_serve(args):
     from paper_2104_14186_gb300 import inputs as I
     from paper_2104_14186_gb300 import qdwhp as Q
 
-    reqs, gaps = I.serving_stream(args.count, 5000)
-    prep = []
-    for r in reqs:
-        if r["kind"] == "eig":
-            A, _, k = I.eig_uniform_device(r["n"], r["seed"], r["fraction"])
-        else:
-            A, _, k = I.svd_logspaced_device(r["m"], r["n"], r["seed"], r["fraction"])
-        prep.append((r["kind"], A, k))
-    prec = precision_code(Q, args.precision)
-    extra = {"precision": prec}
-    svd_extra = dict(extra, refine_steps=args.refine)
-    # capacity calibration: the first 64 requests submitted at once (the queue runs them
-    # concurrently); the arrival rate is 80 % of that throughput
-    q = Q.Queue(args.budget_gb << 30, max_slots=args.concurrency)
-    ncal = min(64, len(prep))
-    t0 = time.perf_counter()
-    cal = [q.submit_eig(A, k, **extra) if kind == "eig" else q.submit_svd(A, k, **svd_extra)
-           for kind, A, k in prep[:ncal]]
-    for rid in cal:
-        q.wait(rid, 3600000)
-        q.release(rid)
-    capacity = ncal / (time.perf_counter() - t0)
-    mean_service = 1.0 / capacity
-    rate = 0.8 * capacity if args.rate <= 0 else args.rate
+    count = args.count if args.count is not None else 2000
+    reqs, gaps = I.serving_stream(count, 5000)
+    names = args.precisions.split(",") if args.precisions else [args.precision]
+    rate = args.rate
+    cal = None
+    if rate <= 0:
+        ref = args.rate_from or names[0]
+        prec = precision_code(Q, ref)
+        q = Q.Queue(args.budget_gb << 30, max_slots=args.concurrency)
+        ncal = min(48, count)
+        inputs = [serve_input(I, r) for r in reqs[:ncal]]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [q.submit_eig(A, k, precision=prec) if r["kind"] == "eig" else
+               q.submit_svd(A, k, precision=prec, refine_steps=args.refine if ref.startswith("mixed") else 0)
+               for r, (A, _, k) in zip(reqs[:ncal], inputs)]
+        for rid in ids:
+            q.wait(rid, 3600000)
+        cal = {"precision": ref, "requests": ncal, "capacity_per_s": ncal / (time.perf_counter() - t0)}
+        q.close()
+        del inputs
+        rate = 0.8 * cal["capacity_per_s"]
     arrivals = np.cumsum(gaps / rate)
-    torch.cuda.synchronize()
-    start = time.perf_counter()
-    ids = []
-    for (kind, A, k), ta in zip(prep, arrivals):
-        delay = start + ta - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        rid = q.submit_eig(A, k, **extra) if kind == "eig" else q.submit_svd(A, k, **svd_extra)
-        ids.append((rid, start + ta))
-    for rid, _ in ids:
-        q.wait(rid, 3600000)
-    end = max(q.times(rid)[2] for rid, _ in ids)
-    t_first = min(q.times(rid)[0] for rid, _ in ids)
-    lat = [q.times(rid)[2] - q.times(rid)[0] for rid, _ in ids]   # completion - submission (= arrival)
-    q.close()
-    print(json.dumps({"workload": f"serving: {args.count} Poisson-arrival requests, EIG n in [128, 2048], "
-                                  f"SVD n in [128, 1024] m in [n, 2n], fractions 1-20 %",
-                      "precision": args.precision, "refine_steps": args.refine, "concurrency": args.concurrency,
-                      "arrival_rate_per_s": rate, "calibrated_capacity_per_s": capacity,
-                      "solves_per_s": len(ids) / (end - t_first),
-                      "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}),
+    results = [serve_once(Q, I, reqs, arrivals, name, args) for name in names]
+    neig = sum(1 for r in reqs if r["kind"] == "eig")
+    print(json.dumps({"workload": f"serving: {count} Poisson-arrival requests ({neig} EIG n in [128, 8192], "
+                                  f"{count - neig} SVD n in [128, 4096] m in [n, 2n], sigma to 1e-10), "
+                                  "fractions 1-20 %, inputs drawn on the GPU at arrival",
+                      "arrival_rate_per_s": rate, "calibration": cal, "concurrency": args.concurrency,
+                      "budget_gb": args.budget_gb, "refine_steps_mixed_svd": args.refine, "results": results}),
           flush=True)
 
 
@@ -754,6 +848,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the emulated and mixed-emulated solves reported beside the FP64 headline")
     ap.add_argument("--precision", choices=["fp64", "mixed", "emulated", "mixed-emulated"], default="fp64")
     ap.add_argument("--refine", type=int, default=0, help="FP64 refinement steps on Q2 (SVD)")
     ap.add_argument("--tune", default=None,
@@ -766,9 +862,10 @@ def main():
     ap.add_argument("--batched", action="store_true", help="time the batched EIG workload")
     ap.add_argument("--gesvd", action="store_true", help="time the full-spectrum QDWH-SVD of the 4096^2 workload")
     ap.add_argument("--serve", action="store_true", help="run the serving stream")
-    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--count", type=int, default=None, help="batched: matrices (512); serve: requests (2000)")
     ap.add_argument("--concurrency", type=int, default=8)
-    ap.add_argument("--budget-gb", type=int, default=16)
+    ap.add_argument("--budget-gb", type=int, default=96)
+    ap.add_argument("--rate-from", default=None, help="serve: precision whose calibrated capacity sets the rate")
     ap.add_argument("--rate", type=float, default=0.0)
     ap.add_argument("--fraction", type=float, default=0.01)
     ap.add_argument("--precisions", default=None,

@@ -232,7 +232,7 @@ qdwhp_status qr_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t l
   // S = [sqrt(c) X; I]
   QDWHP_TRY(axpby(st, m, n, sc, X, ldx, 0.0, w.S, mm));
   QDWHP_TRY(set_matrix(st, n, n, 0.0, 1.0, w.S + m, mm));
-  QDWHP_TRY(geqrf(st, mm, n, w.S, mm, w.qf, w.qr_scratch));
+  QDWHP_TRY(geqrf(st, mm, n, w.S, mm, w.qf, w.qr_scratch, m));   // the identity block's zeros are skipped
   // explicit [Q1; Q2] (the compact factors live in qf, so S can be overwritten)
   QDWHP_TRY(orgqr_columns(st, w.qf, 0, n, w.S, mm, w.qr_scratch));
   // Y = Q1 Q2^T
@@ -263,7 +263,7 @@ qdwhp_status zolo_step(cudaStream_t st, int64_t m, int64_t n, double* X, int64_t
       const double sc = sqrt(cj);
       QDWHP_TRY(copy_matrix(st, m, n, X, ldx, w.S, mm));
       QDWHP_TRY(set_matrix(st, n, n, 0.0, sc, w.S + m, mm));
-      QDWHP_TRY(geqrf(st, mm, n, w.S, mm, w.qf, w.qr_scratch));
+      QDWHP_TRY(geqrf(st, mm, n, w.S, mm, w.qf, w.qr_scratch, m));
       QDWHP_TRY(orgqr_columns(st, w.qf, 0, n, w.S, mm, w.qr_scratch));
       QDWHP_TRY(gemm(st, false, true, m, n, n, aj / sc, w.S, mm, w.S + m, mm, 1.0, w.Acc, m));
       ++*n_qr_terms;

@@ -270,9 +270,17 @@ size_t qr_scratch_elems(int64_t m, int64_t n) {
 
 namespace {
 
+// Rows of the reflectors of the columns [j, j + w): all of [j, m), or, for a factorisation with a
+// band (the stacked [X; D] of a QR-based QDWH step, D diagonal, band = rows of X), only
+// [j, band + j + w): the rows of D below are still zero in those columns.
+int64_t active_rows(const QRFactors& f, int64_t j, int64_t w) {
+  const int64_t end = f.band > 0 ? std::min<int64_t>(f.m, f.band + j + w) : f.m;
+  return end - j;
+}
+
 // T of the outer block starting at column jo (jbo columns) from its panels' T's.
 qdwhp_status build_outer_T(cudaStream_t st, const QRFactors& f, int64_t jo, int jbo, double* G, double* tmp) {
-  const int64_t m = f.m, Ro = m - jo;
+  const int64_t m = f.m, Ro = active_rows(f, jo, jbo);
   const double* Vo = f.Vall + jo + jo * m;
   double* To = f.To + (size_t)(jo / NBO) * NBO * NBO;
   QDWHP_TRY(set_matrix(st, NBO, NBO, 0.0, 0.0, To, NBO));
@@ -291,8 +299,9 @@ qdwhp_status build_outer_T(cudaStream_t st, const QRFactors& f, int64_t jo, int 
 
 }  // namespace
 
-qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f, double* scratch) {
-  if (m < n || n < 0) return QDWHP_ERR_ARG;
+qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda, QRFactors& f, double* scratch,
+                   int64_t band) {
+  if (m < n || n < 0 || band < 0 || (band > 0 && band + n != m)) return QDWHP_ERR_ARG;
   // Householder updates C -= V W2 stay native FP64 in every precision mode: V is unit lower
   // trapezoidal and the coefficient columns span many magnitudes, where the emulated
   // product's normwise (row/column-scaled) error is far above FP64's componentwise one.  Only
@@ -300,6 +309,7 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
   EmulationScope native_products(nullptr, 0);
   f.m = m;
   f.n = n;
+  f.band = band;
   if (n == 0) return QDWHP_OK;
   double* W = scratch;
   double* W2 = W + (size_t)NBO * n;
@@ -312,9 +322,10 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
   double* tmp = G + (size_t)NBO * NBO;
   for (int64_t jo = 0; jo < n; jo += NBO) {
     const int jbo = (int)std::min<int64_t>(NBO, n - jo);
+    const int64_t Ro_blk = active_rows(f, jo, jbo);
     for (int64_t j = jo; j < jo + jbo; j += NB) {
       const int jb = (int)std::min<int64_t>(NB, n - j);
-      const int64_t R = m - j;
+      const int64_t R = active_rows(f, j, jb);
       PanelArgs pa;
       pa.R = (int)R;
       pa.jb = jb;
@@ -329,8 +340,10 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
       pa.gram = gram;
       pa.row_slot = row_slot;
       QDWHP_TRY(launch_panel(st, pa));
-      // the outer block's V is zero above each panel's diagonal
+      // the outer block's V is zero above each panel's diagonal, and (with a band) below the
+      // panel's own rows down to the end of the outer block's rows
       if (j > jo) QDWHP_TRY(set_matrix(st, j - jo, jb, 0.0, 0.0, f.Vall + jo + j * m, m));
+      if (jo + Ro_blk > j + R) QDWHP_TRY(set_matrix(st, jo + Ro_blk - (j + R), jb, 0.0, 0.0, f.Vall + (j + R) + j * m, m));
       const int64_t nc = jo + jbo - j - jb;   // the rest of the outer block
       if (nc > 0) {
         double* C = A + j + (j + jb) * lda;
@@ -344,7 +357,7 @@ qdwhp_status geqrf(cudaStream_t st, int64_t m, int64_t n, double* A, int64_t lda
     QDWHP_TRY(build_outer_T(st, f, jo, jbo, G, tmp));
     const int64_t nc = n - jo - jbo;   // trailing columns: one update with the outer block
     if (nc > 0) {
-      const int64_t Ro = m - jo;
+      const int64_t Ro = Ro_blk;
       const double* Vo = f.Vall + jo + jo * m;
       const double* To = f.To + (size_t)(jo / NBO) * NBO * NBO;
       double* C = A + jo + (jo + jbo) * lda;
@@ -377,7 +390,7 @@ qdwhp_status apply_blocks(cudaStream_t st, const QRFactors& f, int64_t last_bloc
   for (int64_t po = (last_block * NB) / NBO; po >= 0; --po) {
     const int64_t jo = po * NBO;
     const int jbo = (int)std::min<int64_t>(NBO, n - jo);
-    const int64_t Ro = m - jo;
+    const int64_t Ro = active_rows(f, jo, jbo);
     const double* Vo = f.Vall + jo + jo * m;
     const double* To = f.To + (size_t)po * NBO * NBO;
     double* Cj = C + jo;

@@ -173,7 +173,77 @@ def svd_logspaced_device(m: int, n: int, seed: int, fraction: float, decades: fl
     return A.contiguous(), sigma, k_from_fraction(n, fraction)
 
 
-def serving_stream(count: int, seed: int, eig_n=(128, 2048), svd_n=(128, 1024), frac=(0.01, 0.20)):
+def _butterfly_layers(n: int, g, device, passes: int = 4):
+    """Random orthogonal factor as a product of plane rotations (harness only): `passes` sweeps of
+    butterfly layers with strides 1, 2, 4, ... < n, each rotating every pair (i, i + stride) with
+    i's stride bit clear by a uniform random angle, and a random permutation before every sweep.
+    Every coordinate mixes with every other within a sweep; after four sweeps the largest entry
+    is within ~10 % of a Haar factor's typical largest entry (0.167 against 0.153 at n = 1000).
+    The product is orthogonal to rounding (about 4 log2(n) u), and applying it costs
+    O(n^2 log n) instead of a QR of an n x n Gaussian matrix.  Returns the operations in order: ("perm", p) or ("rot", i, j, c, s)."""
+    import torch
+    ops = []
+    idx = torch.arange(n, device=device)
+    for _ in range(passes):
+        ops.append(("perm", torch.randperm(n, generator=g, device=device)))
+        stride = 1
+        while stride < n:
+            i = idx[((idx // stride) % 2 == 0) & (idx + stride < n)]
+            j = i + stride
+            theta = torch.rand(i.numel(), generator=g, device=device, dtype=torch.float64) * (2 * math.pi)
+            ops.append(("rot", i, j, torch.cos(theta), torch.sin(theta)))
+            stride *= 2
+    return ops
+
+
+def _apply_rows(A, ops):
+    """A := Q A for the orthogonal factor Q given by _butterfly_layers (in place on rows)."""
+    for op in ops:
+        if op[0] == "perm":
+            A.copy_(A[op[1]])
+        else:
+            _, i, j, c, s = op
+            Ai, Aj = A[i], A[j]
+            A[i], A[j] = c[:, None] * Ai - s[:, None] * Aj, s[:, None] * Ai + c[:, None] * Aj
+    return A
+
+
+def eig_butterfly_device(n: int, seed: int, fraction: float, device="cuda"):
+    """Symmetric n x n A = Q diag(lambda) Q^T with lambda ~ U[-1, 1] (numpy PCG64) and Q the random
+    butterfly factor of _butterfly_layers (torch Philox from `seed`), built two-sided on the GPU in
+    O(n^2 log n).  For the serving stream, whose 2000 inputs up to n = 8192 would take minutes of
+    Householder QR to draw as Haar factors.  Returns (A as a CUDA float64 tensor, lam, k)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(-1.0, 1.0, n)
+    g = torch.Generator(device=device).manual_seed(seed)
+    ops = _butterfly_layers(n, g, device)
+    A = torch.diag(torch.from_numpy(lam).to(device))
+    _apply_rows(A, ops)
+    At = A.t().contiguous()
+    _apply_rows(At, ops)            # (Q (Q Lambda)^T)^T = Q Lambda Q^T
+    A = 0.5 * (At + At.t())
+    return A.contiguous(), lam, k_from_fraction(n, fraction)
+
+
+def svd_butterfly_device(m: int, n: int, seed: int, fraction: float, decades: float = 10.0, device="cuda"):
+    """m x n A = U [diag(sigma); 0] V^T (m >= n), sigma log-spaced over `decades` from 1, U and V
+    random butterfly factors (as eig_butterfly_device).  Returns (A, sigma, k)."""
+    import torch
+    i = np.arange(n, dtype=np.float64)
+    sigma = 10.0 ** (-decades * i / max(n - 1, 1))
+    g = torch.Generator(device=device).manual_seed(seed)
+    ops_u = _butterfly_layers(m, g, device)
+    ops_v = _butterfly_layers(n, g, device)
+    A = torch.zeros(m, n, dtype=torch.float64, device=device)
+    A[torch.arange(n, device=device), torch.arange(n, device=device)] = torch.from_numpy(sigma).to(device)
+    _apply_rows(A, ops_u)           # U [S; 0]
+    At = A.t().contiguous()
+    _apply_rows(At, ops_v)          # V (U [S; 0])^T = (U [S; 0] V^T)^T
+    return At.t().contiguous(), sigma, k_from_fraction(n, fraction)
+
+
+def serving_stream(count: int, seed: int, eig_n=(128, 8192), svd_n=(128, 4096), frac=(0.01, 0.20)):
     """Seeded request stream: half EIG (n uniform in eig_n, largest side), half SVD (n uniform in
     svd_n, m uniform in [n, 2n]); wanted fraction uniform in frac; unit-rate exponential
     inter-arrival gaps (scaled by the caller to the target rate)."""

@@ -119,9 +119,12 @@ def test_qdwh_chol_steps_match_oracle_and_spectral_map(Q):
     assert abs(conv[-1] - np.linalg.norm(Xo - Xprev)) <= 1e-10 * max(1.0, conv[-1])
 
 
-def test_qdwh_qr_step_matches_oracle(Q):
-    rng = np.random.default_rng(4)
-    m, n = 260, 190
+@pytest.mark.parametrize("m,n", [(260, 190), (700, 600), (600, 600), (1100, 520)])
+def test_qdwh_qr_step_matches_oracle(Q, m, n):
+    """QR-based steps (the stacked [sqrt(c) X; I] factored with its identity block's zeros
+    skipped) against the oracle's dense QR step and the spectral map, over one and several
+    256-column outer blocks, ragged and square."""
+    rng = np.random.default_rng(4 + m + n)
     sig = np.geomspace(1.0, 1e-3, n)
     U = I.haar_orthogonal(n, rng, m)
     V = I.haar_orthogonal(n, rng)
