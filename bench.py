@@ -813,7 +813,10 @@ def run_serve(args):
         del inputs
         rate = 0.8 * cal["capacity_per_s"]
     arrivals = np.cumsum(gaps / rate)
-    results = [serve_once(Q, I, reqs, arrivals, name, args) for name in names]
+    results = []
+    for name in names:
+        results.append(serve_once(Q, I, reqs, arrivals, name, args))
+        print(json.dumps({"partial": True, "arrival_rate_per_s": rate, "result": results[-1]}), flush=True)
     neig = sum(1 for r in reqs if r["kind"] == "eig")
     print(json.dumps({"workload": f"serving: {count} Poisson-arrival requests ({neig} EIG n in [128, 8192], "
                                   f"{count - neig} SVD n in [128, 4096] m in [n, 2n], sigma to 1e-10), "
