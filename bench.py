@@ -694,6 +694,20 @@ def run_batched(args):
         assert all(s == 0 for s in sts), sts
     fl = sum(3 * (n ** 3 + n ** 3 / 3 + 2 * n ** 3) + 4 / 3 * n ** 3 for n in sizes)
     t = statistics.median(times)
+    # one-at-a-time baseline: the same problems solved one after another on one stream
+    sequential = None
+    if args.sequential:
+        o = Q.default_opts(precision=prec, zolo_r=args.zolo)
+        ws = Q.workspace(max(Q.lib().qdwhp_eig_workspace_bytes(int(n), __import__("ctypes").byref(o)) for n in sizes))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for A in As:
+            Q.eig(A, fraction=0.10, ws=ws, precision=prec, zolo_r=args.zolo)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        sequential = {"solves_per_s": args.count / ts, "ms_per_batch": 1e3 * ts,
+                      "batching_gain": ts / t}
+        del ws
     # accuracy of every result against the constructed spectra (outside the timed region)
     import numpy as np
     worst_lam, worst_res = 0.0, 0.0
@@ -705,7 +719,8 @@ def run_batched(args):
     print(json.dumps({"workload": f"batched QDWHpartial-EIG: {args.count} matrices, n in [64, 1024], top 10 %",
                       "precision": args.precision, "zolo_r": args.zolo, "concurrency": args.concurrency,
                       "solves_per_s": args.count / t, "ms_per_batch": 1e3 * t, "alg_tflops_lower_bound": fl / t / 1e12,
-                      "max_lam_err": worst_lam, "max_resid": worst_res, "tuning": tuning}), flush=True)
+                      "max_lam_err": worst_lam, "max_resid": worst_res, "tuning": tuning,
+                      "one_at_a_time": sequential}), flush=True)
 
 
 def serve_input(I, r):
@@ -869,6 +884,8 @@ def main():
     ap.add_argument("--concurrency", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=96)
     ap.add_argument("--rate-from", default=None, help="serve: precision whose calibrated capacity sets the rate")
+    ap.add_argument("--sequential", action="store_true",
+                    help="batched: also time the same problems one after another on one stream")
     ap.add_argument("--rate", type=float, default=0.0)
     ap.add_argument("--fraction", type=float, default=0.01)
     ap.add_argument("--precisions", default=None,
