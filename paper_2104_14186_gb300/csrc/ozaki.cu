@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t bar_full[kUmStages], bar_empty[kUmStages];
   __shared__ __align__(8) uint64_t bar_run[2], bar_free[2], bar_done;
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_zero;
   const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kUmN;
   if (uplo == LOWER && m0 + 128 <= n0) return;   // tile strictly above the diagonal
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_done)));
     s_abort = 0;
+    s_zero = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -243,7 +244,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           ++lp;
         }
       };
-      for (int st = 0; st < kUmStages - 1 && st < total; ++st) issue_load(st);
+      // steps [consumed, loaded) have a copy in flight whose "full" phase nobody has waited for
+      int loaded = 0, consumed = 0;
+      for (int st = 0; st < kUmStages - 1 && st < total; ++st) {
+        issue_load(st);
+        loaded = st + 1;
+      }
       const uint32_t idesc =
           (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUmN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
       int cp = 0, ckb = 0, steps_in_run = 0, run = 0;
@@ -254,6 +260,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           ok = false;
           break;
         }
+        consumed = step + 1;
         if (run_first && run >= 2 &&
             !umma::mbar_wait_or_abort(umma::smem_addr(&bar_free[run & 1]), (uint32_t)(((run >> 1) - 1) & 1), abort_flag)) {
           ok = false;
@@ -297,12 +304,21 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             break;
           }
           issue_load(nxt % kUmStages);
+          loaded = nxt + 1;
         }
         cp = np_;
         ckb = nkb_;
       }
-      if (!ok) *abort_flag = 1;
+      if (!ok) {
+        *abort_flag = 1;
+        // copies still in flight land before the CTA's shared memory is released (bounded)
+        for (int b = consumed; b < loaded; ++b)
+          umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[b % kUmStages]), (uint32_t)((b / kUmStages) & 1),
+                                   &s_zero);
+      }
       umma::commit(umma::smem_addr(&bar_done));   // every MMA issued so far
+      // the tensor memory is freed below only after those MMAs are done (bounded)
+      umma::mbar_wait_or_abort(umma::smem_addr(&bar_done), 0, &s_zero);
     }
     __syncwarp();
   } else {
