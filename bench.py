@@ -301,8 +301,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPES[args.precision],
-        "data": "synthetic", "config": dict(workload_config(k), precision=args.precision, refine_steps=args.refine,
-                                                  polar="zolo-pd r=%d" % args.zolo if args.zolo else "qdwh"),
+        "data": "synthetic", "config": workload_config(k),
+        "mode": {"precision": args.precision, "refine_steps": args.refine,
+                 "polar": "zolo-pd r=%d" % args.zolo if args.zolo else "qdwh"},
         "accuracy": acc,
         "tflops": fl / (total_ms / args.steps / 1e3) / 1e12,
         "tflops_frac_of_fp64_peak": fl / (total_ms / args.steps / 1e3) / 1e12 / peak,
