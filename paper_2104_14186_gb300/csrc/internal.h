@@ -1,6 +1,7 @@
 // Internal host-side interfaces shared by the library's translation units.
 #pragma once
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -18,17 +19,18 @@ class PerDeviceOnce {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return set();
+    if (done_[dev].load(std::memory_order_acquire)) return cudaSuccess;   // every later launch: no lock
     std::lock_guard<std::mutex> lk(mu_);
-    if (done_[dev]) return cudaSuccess;
+    if (done_[dev].load(std::memory_order_relaxed)) return cudaSuccess;
     e = set();
-    if (e == cudaSuccess) done_[dev] = true;
+    if (e == cudaSuccess) done_[dev].store(true, std::memory_order_release);
     return e;
   }
 
  private:
   static constexpr int kMaxDevices = 64;
   std::mutex mu_;
-  bool done_[kMaxDevices] = {};
+  std::atomic<bool> done_[kMaxDevices] = {};
 };
 
 enum Uplo { FULL = 0, LOWER = 1 };
