@@ -107,6 +107,20 @@ def test_emulated_svd(Q, m, n, frac, seed):
     assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-13, mt
 
 
+@pytest.mark.parametrize("m,n,frac,seed", [(1500, 1000, 0.20, 3), (2000, 1200, 0.15, 4)])
+def test_emulated_svd_with_a_qr_based_step(Q, m, n, frac, seed):
+    """The serving stream's SVD shape: sigma over 10 decades and 15-20 % wanted put s near 1e-2,
+    so the schedule starts with a QR-based step (c_0 > 100), whose reductions run emulated."""
+    q = I.svd_logspaced(m, n, seed, frac, decades=10.0)
+    r = Q.svd(dev(q.A), k=q.k, precision=Q.FP64_EMULATED)
+    assert r.info["it_qr"] >= 1
+    mt = O.svd_metrics(q.A, r.sigma.cpu().numpy(), r.U.cpu().numpy(), r.V.cpu().numpy(), q.sigma[: q.k])
+    print(f"{m}x{n} {frac}: {mt}")
+    assert mt["sigma_err"] <= 1e-12, mt
+    assert mt["orthU"] <= 5e-15 * m and mt["orthV"] <= 5e-15 * m, mt
+    assert mt["residV"] <= 1e-13 and mt["residU"] <= 1e-13, mt
+
+
 def test_mixed_emulated_svd_refined_meets_fp64_tolerances(Q):
     """FP32 Cholesky steps, emulated FP64 products elsewhere and 6 FP64 subspace-refinement
     steps: the SVD workload (4096 x 4096, top 5 %) at the plain-FP64 tolerances."""
