@@ -61,4 +61,14 @@ struct DcStats {
 qdwhp_status sym_eig_dc(cudaStream_t st, int64_t n, double lo, double hi, uint64_t seed, bool vectors,
                         int jacobi_max_sweeps, double* lam, double* V, int64_t ldv, DcWs& w, DcStats* stats);
 
+// ---- gesvd.cu ----
+// All singular triplets of the n x n R by QDWH-SVD (polar factor, divide-and-conquer eigensolver
+// of H = U_p^T R, U = U_p V), for the reduced problem of the partial SVD: sigma (n) descending,
+// U (n x n, ld ldu; may be the storage of R, which is read only before U is written) and V
+// (n x n, ld ldv).  `ws` holds gesvd_square_ws_bytes(n) bytes; *sweeps gets the largest Jacobi
+// sweep count of the eigensolver's leaves.
+size_t gesvd_square_ws_bytes(int64_t n);
+qdwhp_status gesvd_square(cudaStream_t st, int64_t n, const double* R, int64_t ldr, double* sigma, double* U,
+                          int64_t ldu, double* V, int64_t ldv, void* ws, size_t ws_bytes, int* sweeps);
+
 }  // namespace qdwhp

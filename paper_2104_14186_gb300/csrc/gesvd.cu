@@ -167,6 +167,27 @@ bool precision_ok(int32_t p) { return p == QDWHP_FP64 || p == QDWHP_FP64_EMULATE
 
 }  // namespace
 
+size_t gesvd_square_ws_bytes(int64_t n) {
+  Arena ar;
+  ar.dry = true;
+  GesvdWs w;
+  carve_gesvd(ar, n, n, false, false, w);
+  return ar.used;
+}
+
+qdwhp_status gesvd_square(cudaStream_t st, int64_t n, const double* R, int64_t ldr, double* sigma, double* U,
+                          int64_t ldu, double* V, int64_t ldv, void* ws, size_t ws_bytes, int* sweeps) {
+  Arena ar{(char*)ws, ws_bytes};
+  GesvdWs w;
+  carve_gesvd(ar, n, n, false, false, w);
+  if (!ar.ok()) return QDWHP_ERR_NOMEM;
+  qdwhp_gesvd_info inf;
+  memset(&inf, 0, sizeof(inf));
+  QDWHP_TRY(gesvd_impl(R, n, n, ldr, sigma, U, ldu, V, ldv, w, &inf, st));
+  if (sweeps) *sweeps = inf.jacobi_sweeps;
+  return QDWHP_OK;
+}
+
 }  // namespace qdwhp
 
 using namespace qdwhp;

@@ -60,6 +60,12 @@ constexpr int64_t kKrylovMaxCols = 2048;
 // (below it the block's Ritz-value bound captures fewer unwanted eigenvalues): kSlqProbes start
 // vectors, kSlqSteps Lanczos steps each, kSlqZ standard errors of margin.
 constexpr int64_t kSlqMinN = 1024;
+// The SVD's reduced problem (the SVD of R from A Q2 = Q_C R) goes to one-sided Jacobi up to this
+// order and to QDWH-SVD above it: a Jacobi sweep rotates every column about ell times, and the
+// rounding of ~10 sweeps of those rotations left ~50 u per column in the singular values and
+// vectors at ell ~ 1000 (a 3910 x 3733 SVD at k = 623: residual 1.2e-13 against the oracle's
+// 5e-15), where QDWH-SVD's Rayleigh-quotient eigenvalues of H stay at the rounding level.
+constexpr int64_t kSvdJacobiMax = 512;
 constexpr int kSlqProbes = 16;
 constexpr int kSlqSteps = 64;
 constexpr double kSlqZ = 3.0;
@@ -454,6 +460,8 @@ struct SvdWs {
   size_t emu_bytes = 0;
   char* f32tc = nullptr;  // FP32 products of the reduced-precision steps on the tensor cores
   size_t f32tc_bytes = 0;
+  char* rr = nullptr;     // QDWH-SVD of a reduced problem of order > kSvdJacobiMax: its scratch
+  size_t rr_bytes = 0;
 };
 
 void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, bool need_transpose) {
@@ -479,6 +487,10 @@ void carve_svd(Arena& ar, int64_t m, int64_t n, const qdwhp_opts& o, SvdWs& w, b
     const int64_t d = std::max(m, n);
     w.f32tc_bytes = gemm_bf16x6_ws_bytes(d, d, d);
     w.f32tc = ar.take<char>(w.f32tc_bytes);
+  }
+  if (n > kSvdJacobiMax) {
+    w.rr_bytes = gesvd_square_ws_bytes(n);
+    w.rr = ar.take<char>(w.rr_bytes);
   }
 }
 
@@ -548,6 +560,7 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   int retries = 0;
   int64_t ell = 0;
   int count = 0;
+  bool rr_unit = false;   // the reduced SVD came from QDWH-SVD (unit U columns) rather than Jacobi
   for (;;) {
     const bool zolo = o.zolo_r > 0;
     if (zolo) {
@@ -612,11 +625,17 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
       QDWHP_TRY(gemm(st, false, false, m, ell, n, 1.0, A, lda, Q2, n, 0.0, w.C, m));
       QDWHP_TRY(geqrf(st, m, ell, w.C, m, w.q.qf, w.q.qr_scratch));
       QDWHP_TRY(copy_upper(st, ell, w.C, m, w.W, ell));
-      QDWHP_TRY(jacobi_onesided(st, ell, ell, w.W, ell, w.Vj, ell, o.jacobi_max_sweeps, kJacobiTight, w.c.jst,
-                                &hs.jst, &sweeps, &conv));
-      if (!conv) return QDWHP_ERR_NOT_CONVERGED;
+      rr_unit = ell > kSvdJacobiMax && w.rr != nullptr;
+      if (rr_unit) {
+        // R = U_R Sigma V_R^T by QDWH-SVD: W := U_R (unit columns), Vj := V_R, vals := sigma
+        QDWHP_TRY(gesvd_square(st, ell, w.W, ell, w.c.vals, w.W, ell, w.Vj, ell, w.rr, w.rr_bytes, &sweeps));
+      } else {
+        QDWHP_TRY(jacobi_onesided(st, ell, ell, w.W, ell, w.Vj, ell, o.jacobi_max_sweeps, kJacobiTight, w.c.jst,
+                                  &hs.jst, &sweeps, &conv));
+        if (!conv) return QDWHP_ERR_NOT_CONVERGED;
+        QDWHP_TRY(column_norms(st, ell, ell, w.W, ell, w.c.vals));
+      }
       inf.jacobi_sweeps = sweeps;
-      QDWHP_TRY(column_norms(st, ell, ell, w.W, ell, w.c.vals));
       // Step 7: sigma >= s alpha, descending.
       QDWHP_TRY(select_sort(st, ell, w.c.vals, -1.0, -s * alpha, w.c.order, w.c.ints + 1));
       QDWHP_TRY(sync_read(st, hs.ints, w.c.ints, sizeof(int) * 4));
@@ -628,11 +647,12 @@ qdwhp_status svd_impl(const double* A, int64_t m, int64_t n, int64_t lda, int64_
   }
   if (count < k) return QDWHP_ERR_COUNT;
   // Step 8: U1 = Q_C [W_sel Sigma_sel^{-1}; 0] with the Jacobi-rotated columns of R (which
-  // stay orthogonal to high relative accuracy even for small sigma), V1 = Q2 V~1 with the
-  // selected rotation columns rescaled to unit norm (rotation rounding drifts their norms).
+  // stay orthogonal to high relative accuracy even for small sigma), or Q_C [U_R,sel; 0] from
+  // QDWH-SVD; V1 = Q2 V~1 with the selected columns rescaled to unit norm (rotation rounding
+  // drifts their norms).
   double* Vsel = w.X;               // ell x k
   QDWHP_TRY(gather_values(st, k, w.c.vals, w.c.order, sigma));
-  QDWHP_TRY(gather_columns(st, ell, k, w.W, ell, w.c.order, w.c.vals, U, ldu));
+  QDWHP_TRY(gather_columns(st, ell, k, w.W, ell, w.c.order, rr_unit ? nullptr : w.c.vals, U, ldu));
   if (m > ell) QDWHP_TRY(set_matrix(st, m - ell, k, 0.0, 0.0, U + ell, ldu));
   QDWHP_TRY(ormqr_left(st, w.q.qf, U, k, ldu, w.q.qr_scratch));
   QDWHP_TRY(gather_columns(st, ell, k, w.Vj, ell, w.c.order, nullptr, Vsel, ell));

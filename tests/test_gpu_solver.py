@@ -127,6 +127,25 @@ def test_svd_small_threshold_takes_qr_step(Q):
     check_svd(q, r)
 
 
+@pytest.mark.parametrize("m,n,frac,seed,prec", [(1800, 1500, 0.25, 7, "fp64"), (2000, 1400, 0.30, 8, "fp64"),
+                                                  (1800, 1500, 0.25, 7, "emulated")])
+def test_svd_large_reduced_problem(Q, m, n, frac, seed, prec):
+    """A reduced problem of order ell > 512 (here 531 and 556, sigma log-spaced over 10 decades,
+    as in the serving stream's SVD requests) is solved by QDWH-SVD on the device instead of the
+    one-sided Jacobi: the FP64 tolerances hold and the residuals stay within 10x the oracle's
+    (the Jacobi rotations on ell > 500 columns left residuals near 1e-13)."""
+    q = I.svd_logspaced(m, n, seed, frac, decades=10.0)
+    precision = Q.FP64 if prec == "fp64" else Q.FP64_EMULATED
+    r = Q.svd(dev(q.A), k=q.k, precision=precision)
+    ref = O.qdwhp_svd(q.A, O.SvdOptions(k=q.k))
+    assert r.info["ell"] > 512 and ref.ell > 512
+    mt = check_svd(q, r, ref)
+    mo = O.svd_metrics(q.A, ref.sigma, ref.U, ref.V)
+    assert mt["residV"] <= 10 * mo["residV"] + 1e-14, (mt, mo)
+    print(f"{m}x{n} k={q.k} ell {r.info['ell']} ({prec}): residV {mt['residV']:.1e} residU {mt['residU']:.1e} "
+          f"(oracle {mo['residV']:.1e} {mo['residU']:.1e})")
+
+
 def test_nonfinite_input_is_reported(Q):
     p = I.eig_uniform(64, 1, 0.1)
     A = p.A.copy()
