@@ -407,7 +407,7 @@ def emulated_roofline(Q, total_ms, bf16_peak):
     fp64_flops = sum((r[1] * (r[1] + 1) * r[2]) if r[3] else 2.0 * r[0] * r[1] * r[2] for r in recs)
     bf16_flops = OZ_PAIRS * fp64_flops
     achieved = bf16_flops / (ms / 1e3) / 1e12
-    return {"kernel": "oz_umma_ws_kernel (FP64 products as 60 exact BF16 digit products, tcgen05.mma kind::f16, "
+    return {"kernel": "oz_umma_kernel (FP64 products as 60 exact BF16 digit products in 2x2 digit blocks, tcgen05.mma kind::f16, "
                       "FP32 sums in TMEM)",
             "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
             "frac": achieved / bf16_peak, "traffic": None,
@@ -499,7 +499,7 @@ def run_kernel_gemm(args):
     if emulated:
         bf16_peak = peaks.get("bf16_tflops", 1.9e3)
         bf16_tf = OZ_PAIRS * 2.0 * n ** 3 / (statistics.median(ms) / 1e3) / 1e12
-        print(json.dumps({"kernel": "oz split + oz_umma_ws_kernel via qdwhp_gemm_f64_emulated", "m": n, "n": n, "k": n,
+        print(json.dumps({"kernel": "oz split + oz_umma_kernel via qdwhp_gemm_f64_emulated", "m": n, "n": n, "k": n,
                           "ms_median": statistics.median(ms), "fp64_equivalent_tflops": tf,
                           "vs_fp64_peak": tf / peak, "bf16_tflops": bf16_tf, "bf16_peak": bf16_peak,
                           "bf16_frac": bf16_tf / bf16_peak}), flush=True)

@@ -68,7 +68,7 @@ qdwhp_status gemm(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n, int64
 size_t gemm_splitk_ws_elems(int64_t m, int64_t n);
 
 // ---- ozaki.cu ----
-// FP64 GEMM emulated on the BF16 tensor cores (Ozaki splitting: 9 six-bit digits per entry,
+// FP64 GEMM emulated on the BF16 tensor cores (Ozaki splitting: 9 balanced six-bit digits per entry,
 // the 60 digit pairs with s + t <= 12, exact in FP32, FP64 accumulation).  Same operation as gemm(); needs
 // gemm_ozaki_ws_bytes(m, n, k) bytes of scratch (16-byte aligned).
 size_t gemm_ozaki_ws_bytes(int64_t m, int64_t n, int64_t k);

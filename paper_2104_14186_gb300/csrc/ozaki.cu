@@ -6,58 +6,48 @@
 // FP64 pipe is ~1/600 of its BF16 tensor rate.
 //
 // Each row i of op(A) is scaled by 2^-e_i (e_i: binary exponent of the row's largest
-// magnitude, so every entry lies in (-1, 1)) and rounded to a 54-bit fixed-point integer,
-// written in base 2^6 as 9 signed digits D_1..D_9 (|D| <= 63: exact in bfloat16).
-// Columns of op(B) are split the same way with exponents f_j.  Then
-//     C_ij = 2^(e_i + f_j) sum_{s,t} 2^(-6 (s + t)) (D^A_s D^B_t)_ij ,
-// where every digit product D^A_s D^B_t is an exact integer matrix product: each term is
-// < 2^12 in magnitude, so a sum over K <= 4096 terms stays below 2^24 and is exact in the
-// FP32 accumulators of the tensor cores (bf16 x bf16 -> f32).  Each such product is scaled
-// by its power of two and added into FP64 accumulators.  The pairs with s + t <= 12 are
-// kept (60 of the 81).  The dropped pairs are a bias, not noise, where the digit products
-// share a sign (a sum of squares): at most 6 K 63^2 2^-78 2^(e_i + f_j), below the K u
-// 2^(e_i + f_j) rounding bound of an FP64 dot product of length K (one level fewer would put
-// 64 times more bias on Gram diagonals).  Pairs
-// of one level s + t share the scale 2^(-6 (s + t)), so they share an FP32 accumulator as
-// long as it holds at most 4224 digit products (exact); it is flushed into FP64 when the
-// level changes or the budget would be exceeded.
+// magnitude, so every entry lies in (-1, 1)) and rounded to a 53-bit fixed-point integer X,
+// written in base 2^6 as 9 balanced signed digits D_1..D_9 (|D| <= 32: exact in bfloat16):
+// X = sum_s D_s 2^(6 (9 - s)), so the entry is 2^(e_i + 1) sum_s D_s 2^(-6 s).  Columns of op(B)
+// are split the same way with exponents f_j.  Then
+//     C_ij = 2^(e_i + f_j + 2) sum_{s,t} 2^(-6 (s + t)) (D^A_s D^B_t)_ij ,
+// where every digit product D^A_s D^B_t is an exact integer matrix product: each term is at
+// most 2^10 in magnitude, so a sum of up to 2^14 terms stays within 2^24 and is exact in the
+// FP32 accumulators of the tensor cores (bf16 x bf16 -> f32).  Each such sum is scaled by its
+// power of two and added into FP64 accumulators.  The pairs with s + t <= 12 are kept (60 of
+// the 81).  The dropped pairs are a bias, not noise, where the digit products share a sign (a
+// sum of squares): at most 6 K 2^10 2^-78 2^(e_i + f_j + 2), far below the K u 2^(e_i + f_j)
+// rounding bound of an FP64 dot product of length K.  The 53-bit rounding of an entry is at
+// most 2^-54 2^(e_i + 1) <= 2^-53 times its row's largest magnitude.  Pairs of one level s + t
+// share the scale 2^(-6 (s + t)), so they share an FP32 accumulator while it holds at most 2^14
+// digit products per entry; the schedule (oz_schedule.h) flushes it into FP64 before that.
 //
 // Layout: digit slices are stored as [slice][row][k_pad] bfloat16 with K contiguous (op(A)
-// rows, op(B) columns), zero-padded to 128-row, 128-deep blocks; the product kernel (TMA +
-// tcgen05, below) streams a (slice pair, K block) sequence through a 3-stage ring in shared
-// memory.
+// rows, op(B) columns), zero-padded to 128-row blocks and 64-deep K steps; the product kernel
+// (TMA + tcgen05, below) runs the schedule's 2 x 2 digit blocks, each K step loading up to two
+// op(A) and two op(B) digit tiles into one stage of a 3-stage ring in shared memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <map>
+#include <memory>
 #include <mutex>
 
 #include "internal.h"
+#include "oz_schedule.h"
 #include "umma.cuh"
 
 namespace qdwhp {
 
 namespace {
 
-constexpr int kOzS = 9;          // digits per entry
 constexpr int kOzBeta = 6;       // bits per digit
-constexpr int kOzT = 12;         // keep digit pairs with s + t <= kOzT (1-based)
-constexpr int kOzBudget = 4224;  // FP32 exactness: at most this many digit products (each
-                                 // < 2^12 in magnitude) in one accumulator: 4224 * 63^2 < 2^24
 constexpr int kOzBM = 128, kOzBN = 128;   // row padding of the op(A) and op(B) digit slices
-constexpr int kOzKPad = 128;              // K padding of the digit slices (one K block)
+constexpr int kOzKPad = kOzStepK;         // K padding of the digit slices (one K step)
 constexpr int kExpEmpty = -2000000000;   // no entry seen yet (row of zeros)
 constexpr int kExpNonfinite = 1 << 20;   // a NaN or Inf in the row
-
-struct PairTable {
-  int npairs;
-  unsigned char s[kOzS * kOzS];
-  unsigned char t[kOzS * kOzS];
-  unsigned char lev[kOzS * kOzS];
-  double scale[kOzS * kOzS];
-};
-__constant__ PairTable c_pairs;
 
 // ---- splitting ----
 
@@ -102,7 +92,7 @@ __global__ void oz_exp_kernel(int rows, int k, const double* X, int64_t ld, int 
 }
 
 __device__ __forceinline__ unsigned short bf16_bits_of_small_int(int d) {
-  // |d| <= 63: exactly representable; round-to-nearest conversion is exact
+  // |d| <= 32: exactly representable; round-to-nearest conversion is exact
   const __nv_bfloat16 h = __int2bfloat16_rn(d);
   return *reinterpret_cast<const unsigned short*>(&h);
 }
@@ -132,86 +122,81 @@ __global__ void oz_split_kernel(int rows, int k, int rows_pad, int k_pad, const 
     if (r >= rows_pad || l >= k_pad) continue;
     const double v = tile[rr][tx];
     int e = (r < rows) ? exps[r] : kExpEmpty;
-    long long X54 = 0;
+    long long X53 = 0;
     if (e != kExpEmpty && e != kExpNonfinite && v != 0.0) {
-      // |v| 2^-e < 1; scaled by 2^54 it is exact, and rounding to an integer loses < 2^-55
-      X54 = llrint(ldexp(v, 54 - e));
+      // |v| 2^-e < 1; scaled by 2^53 it is below 2^53; rounding to an integer moves it by <= 1/2
+      X53 = llrint(ldexp(v, 53 - e));
     }
-    const unsigned long long U = (unsigned long long)(X54 < 0 ? -X54 : X54);
-    const int sgn = X54 < 0 ? -1 : 1;
+    const unsigned long long U = (unsigned long long)(X53 < 0 ? -X53 : X53);
+    const int sgn = X53 < 0 ? -1 : 1;
     unsigned short* o = out + (size_t)r * k_pad + l;
+    // balanced digits, least significant first: a 6-bit group of 32 or more becomes group - 64
+    // with a carry into the next group; the top group (bits 48..52, < 32) takes the last carry
+    int carry = 0;
 #pragma unroll
-    for (int s = 0; s < kOzS; ++s) {
-      const int d = (int)((U >> (kOzBeta * (kOzS - 1 - s))) & ((1u << kOzBeta) - 1));
+    for (int s = kOzS - 1; s >= 1; --s) {
+      int d = (int)((U >> (kOzBeta * (kOzS - 1 - s))) & ((1u << kOzBeta) - 1)) + carry;
+      carry = d >= 32 ? 1 : 0;
+      d -= 64 * carry;
       o[(size_t)s * slice] = bf16_bits_of_small_int(sgn * d);
     }
+    o[0] = bf16_bits_of_small_int(sgn * ((int)(U >> (kOzBeta * (kOzS - 1))) + carry));
   }
 }
 
-// ---- the digit-product GEMM ----
-
-// ---- tcgen05 (UMMA) digit-product kernel ----
+// ---- the digit-product kernel (TMA + tcgen05, warp-specialised, schedule-driven) ----
 //
-// The 60 exact digit products run on the 5th-generation tensor cores as
-// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16).  Both operands are
-// read from shared memory through matrix descriptors: K-major, 128-byte swizzle, i.e. 8-row
-// atoms of 1024 bytes with 16-byte chunk c of row r stored at chunk c ^ (r % 8), which is the
-// layout the TMA engine writes for a 64 x 128 box with the 128-byte swizzle.  The FP32 sums live
-// in tensor memory (two 128-column accumulators), and every mbarrier wait is bounded: on a
-// timeout the tile is written as NaN and err is set.
-constexpr int kUmN = 128;
-constexpr int kUmAtomK = umma::kAtomK;                           // K of one 128-byte swizzle atom row
-constexpr int kUmBK = 128;                                      // K per stage: two atoms per operand
-constexpr int kUmStages = 3;
-constexpr uint32_t kUmAtomBytes = 128 * kUmAtomK * 2;           // 16 KB: 128 rows x 64 K
-constexpr uint32_t kUmTileBytes = 128 * kUmBK * 2;              // 32 KB per operand and stage
-constexpr uint32_t kUmStageBytes = 2 * kUmTileBytes;
-constexpr size_t kUmSmemBytes = (size_t)kUmStages * kUmStageBytes + 1024;
-
-// ---- warp-specialised TMA + tcgen05 digit-product kernel ----
+// One CTA computes a 128 x 128 tile of C.  The digit products run on the 5th-generation tensor
+// cores as tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = N = 128, K = 16), both operands read
+// from shared memory through matrix descriptors: K-major, 128-byte swizzle, i.e. 8-row atoms of
+// 1024 bytes with 16-byte chunk c of row r stored at chunk c ^ (r % 8), which is the layout the
+// TMA engine writes for a 64 x 128 box with the 128-byte swizzle.
 //
-// Warp 8 (one thread) feeds a 3-stage ring (128-deep K per stage) with TMA (cp.async.bulk.tensor, 128-byte swizzle
-// written by the copy engine, each stage's "full" mbarrier counting the bytes) and issues the
-// MMAs of a stage as soon as it is full; each stage's MMAs commit to its "empty" mbarrier, which
-// releases the stage to the next copy.  A level run (digit pairs of one level, at most 4224
-// digit products per accumulator) accumulates into one of two 128-column TMEM buffers and commits to that buffer's
-// "run done" mbarrier.  Warps 0-7 only flush: for each run they wait on "run done", read the
-// FP32 sums (tcgen05.ld), add them into their FP64 registers and arrive on the buffer's "free"
-// mbarrier, which the issuing thread waits on before reusing the buffer two runs later.  The
-// flush warps derive the run schedule from the pair table (no per-step synchronisation).
-constexpr int kWsThreads = 288;
-constexpr int kWsRunSteps = kOzBudget / kUmBK;   // K blocks per run at most (exact FP32 sums)
+// Warp 8 (one thread) walks the schedule (oz_schedule.h): for every K step of an item it loads
+// the item's digit tiles (op(A) digits into tile slots 0-1, op(B) digits into 2-3 of a 64 KB
+// stage; the stage's "full" mbarrier counts the bytes) and, once the stage is full, issues the
+// item's pair products into their tensor-memory slots (four 128-column FP32 accumulators); the
+// stage's MMAs commit to its "empty" mbarrier, which releases it to the next copy.  After an
+// item it commits the "ready" mbarrier of every slot the schedule flushes there, and before
+// writing a reused slot it waits on the slot's "free" mbarrier.  Warps 0-7 only flush: for each
+// flush of the schedule they wait on the slot's "ready", read its FP32 sums (tcgen05.ld), add
+// them times 2^(-6 level) into their FP64 registers and arrive on "free".  Every wait is
+// bounded: on a timeout the tile is written as NaN and err is set.
+constexpr int kOzThreads = 288;
+constexpr int kOzStages = 3;
+constexpr uint32_t kOzTileBytes = umma::kAtomBytes;        // 16 KB: 128 rows x 64 K of one digit
+constexpr uint32_t kOzStageBytes = 4 * kOzTileBytes;       // op(A) tiles 0-1, op(B) tiles 2-3
+constexpr size_t kOzSmemBytes = (size_t)kOzStages * kOzStageBytes + 1024;
+constexpr int kOzTmemCols = kOzSlots * 128;
 
-__global__ void __launch_bounds__(kWsThreads, 1)
-    oz_umma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-                      int k_pad, const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta,
-                      double* C, int64_t ldc, int uplo, double diag_add, int* err) {
-  extern __shared__ unsigned char ws_smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)ws_smem_raw + 1023) & ~(uintptr_t)1023);
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_umma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ OzSchedule sch, int M, int N, int kb0, const int* __restrict__ ea,
+                   const int* __restrict__ eb, double alpha, double beta, double* C, int64_t ldc, int uplo,
+                   double diag_add, int* err) {
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t bar_full[kUmStages], bar_empty[kUmStages];
-  __shared__ __align__(8) uint64_t bar_run[2], bar_free[2], bar_done;
+  __shared__ __align__(8) uint64_t bar_full[kOzStages], bar_empty[kOzStages];
+  __shared__ __align__(8) uint64_t bar_ready[kOzSlots], bar_free[kOzSlots], bar_done;
   __shared__ int s_abort, s_zero;
-  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kUmN;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
   if (uplo == LOWER && m0 + 128 <= n0) return;   // tile strictly above the diagonal
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nkb = k_pad / kUmBK;
-  const int npairs = c_pairs.npairs;
-  const int total = npairs * nkb;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(umma::smem_addr(&tmem_base)),
-                 "r"(2 * kUmN));
+                 "r"(kOzTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 256) {
-    for (int s = 0; s < kUmStages; ++s) {
+    for (int s = 0; s < kOzStages; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_empty[s])));
     }
-    for (int b = 0; b < 2; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_run[b])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(umma::smem_addr(&bar_free[b])));
+    for (int x = 0; x < kOzSlots; ++x) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_ready[x])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(umma::smem_addr(&bar_free[x])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(umma::smem_addr(&bar_done)));
     s_abort = 0;
@@ -228,92 +213,94 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   if (warp == 8) {
     if (lane == 0) {
       const uint32_t sbase = umma::smem_addr(smem);
-      int lp = 0, lkb = 0;
+      int total = 0;
+      for (int it = 0; it < sch.nitems; ++it) total += oz_item_steps(sch, it);
+      int li = 0, lks = 0;   // the next step to load: item li, its step lks
       auto issue_load = [&](int stage) {
+        const int at = sch.atile[li], bt = sch.btile[li];
+        const bool a2 = (at >> 4) != 0xF, b2 = (bt >> 4) != 0xF;
         const uint32_t bar = umma::smem_addr(&bar_full[stage]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kUmStageBytes)
-                     : "memory");
-        const uint32_t dA = sbase + (uint32_t)stage * kUmStageBytes, dB = dA + kUmTileBytes;
-#pragma unroll
-        for (int at = 0; at < kUmBK / kUmAtomK; ++at) {
-          umma::tma_load_3d(dA + at * kUmAtomBytes, &mapA, lkb * kUmBK + at * kUmAtomK, m0, (int)c_pairs.s[lp], bar);
-          umma::tma_load_3d(dB + at * kUmAtomBytes, &mapB, lkb * kUmBK + at * kUmAtomK, n0, (int)c_pairs.t[lp], bar);
-        }
-        if (++lkb == nkb) {
-          lkb = 0;
-          ++lp;
+        const uint32_t bytes = (uint32_t)(2 + (a2 ? 1 : 0) + (b2 ? 1 : 0)) * kOzTileBytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        const int kc = (kb0 + sch.chunk[li] * sch.clen + lks) * kOzStepK;
+        const uint32_t d = sbase + (uint32_t)stage * kOzStageBytes;
+        umma::tma_load_3d(d, &mapA, kc, m0, at & 15, bar);
+        if (a2) umma::tma_load_3d(d + kOzTileBytes, &mapA, kc, m0, at >> 4, bar);
+        umma::tma_load_3d(d + 2 * kOzTileBytes, &mapB, kc, n0, bt & 15, bar);
+        if (b2) umma::tma_load_3d(d + 3 * kOzTileBytes, &mapB, kc, n0, bt >> 4, bar);
+        if (++lks == oz_item_steps(sch, li)) {
+          lks = 0;
+          ++li;
         }
       };
       // steps [consumed, loaded) have a copy in flight whose "full" phase nobody has waited for
       int loaded = 0, consumed = 0;
-      for (int st = 0; st < kUmStages - 1 && st < total; ++st) {
+      for (int st = 0; st < kOzStages - 1 && st < total; ++st) {
         issue_load(st);
         loaded = st + 1;
       }
-      const uint32_t idesc =
-          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUmN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-      int cp = 0, ckb = 0, steps_in_run = 0, run = 0;
-      bool run_first = true;
+      const uint32_t idesc = umma::idesc_bf16_f32(128, 128);
+      int ci = 0, cks = 0, fp = 0;
+      uint32_t nf = 0;   // flushes committed per slot, 8 bits each
       for (int step = 0; step < total && ok; ++step) {
-        const int stage = step % kUmStages;
-        if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[stage]), (uint32_t)((step / kUmStages) & 1), abort_flag)) {
+        const int stage = step % kOzStages;
+        if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[stage]), (uint32_t)((step / kOzStages) & 1), abort_flag)) {
           ok = false;
           break;
         }
         consumed = step + 1;
-        if (run_first && run >= 2 &&
-            !umma::mbar_wait_or_abort(umma::smem_addr(&bar_free[run & 1]), (uint32_t)(((run >> 1) - 1) & 1), abort_flag)) {
-          ok = false;
-          break;
+        if (cks == 0) {
+          // reused slots: their last flush has read them out
+          const int wm = sch.ctl[ci] & 15;
+          for (int x = 0; x < kOzSlots && ok; ++x)
+            if ((wm >> x) & 1) {
+              const uint32_t cnt = (nf >> (8 * x)) & 255u;
+              if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_free[x]), (cnt - 1u) & 1u, abort_flag)) ok = false;
+            }
+          if (!ok) break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = sbase + (uint32_t)stage * kUmStageBytes, b0 = a0 + kUmTileBytes;
-        const uint32_t dcol = tmem + (uint32_t)((run & 1) * kUmN);
+        const uint32_t st_base = sbase + (uint32_t)stage * kOzStageBytes;
 #pragma unroll
-        for (int kk = 0; kk < kUmBK / 16; ++kk) {
-          // atom kk / 4, 32-byte K step kk % 4 inside it
-          const uint32_t off = (uint32_t)(kk / 4) * kUmAtomBytes + (uint32_t)(kk % 4) * 32;
-          const uint64_t da = umma::desc_sw128(a0 + off), db = umma::desc_sw128(b0 + off);
-          const uint32_t accum = (run_first && kk == 0) ? 0u : 1u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-              "l"(da), "l"(db), "r"(idesc), "r"(accum));
+        for (int p = 0; p < 4; ++p) {
+          const int pc = sch.pair[ci][p];
+          if (!(pc & 0x80)) continue;
+          const uint32_t a0 = st_base + (uint32_t)(pc & 1) * kOzTileBytes;
+          const uint32_t b0 = st_base + (uint32_t)(2 + ((pc >> 1) & 1)) * kOzTileBytes;
+          const uint32_t dcol = tmem + (uint32_t)(((pc >> 2) & 3) * 128);
+          const bool fresh = (pc & 0x10) && cks == 0;
+#pragma unroll
+          for (int kk = 0; kk < kOzStepK / 16; ++kk)   // 32-byte K steps inside the swizzle atom
+            umma::mma_bf16(dcol, umma::desc_sw128(a0 + kk * 32), umma::desc_sw128(b0 + kk * 32), idesc,
+                           (fresh && kk == 0) ? 0u : 1u);
         }
         umma::commit(umma::smem_addr(&bar_empty[stage]));
-        ++steps_in_run;
-        int np_ = cp, nkb_ = ckb + 1;
-        if (nkb_ == nkb) {
-          nkb_ = 0;
-          ++np_;
+        if (++cks == oz_item_steps(sch, ci)) {
+          const int nfl = (sch.ctl[ci] >> 4) & 7;
+          for (int f = 0; f < nfl; ++f) {
+            const int x = sch.flush[fp++] & 3;
+            umma::commit(umma::smem_addr(&bar_ready[x]));
+            nf += 1u << (8 * x);
+          }
+          cks = 0;
+          ++ci;
         }
-        const bool run_ends = np_ >= npairs || c_pairs.lev[np_] != c_pairs.lev[cp] || steps_in_run >= kWsRunSteps;
-        if (run_ends) {
-          umma::commit(umma::smem_addr(&bar_run[run & 1]));
-          ++run;
-          run_first = true;
-          steps_in_run = 0;
-        } else {
-          run_first = false;
-        }
-        const int nxt = step + kUmStages - 1;
+        const int nxt = step + kOzStages - 1;
         if (nxt < total) {
-          if (step >= 1 && !umma::mbar_wait_or_abort(umma::smem_addr(&bar_empty[(step - 1) % kUmStages]),
-                                               (uint32_t)(((step - 1) / kUmStages) & 1), abort_flag)) {
+          if (step >= 1 && !umma::mbar_wait_or_abort(umma::smem_addr(&bar_empty[(step - 1) % kOzStages]),
+                                                     (uint32_t)(((step - 1) / kOzStages) & 1), abort_flag)) {
             ok = false;
             break;
           }
-          issue_load(nxt % kUmStages);
+          issue_load(nxt % kOzStages);
           loaded = nxt + 1;
         }
-        cp = np_;
-        ckb = nkb_;
       }
       if (!ok) {
         *abort_flag = 1;
         // copies still in flight land before the CTA's shared memory is released (bounded)
         for (int b = consumed; b < loaded; ++b)
-          umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[b % kUmStages]), (uint32_t)((b / kUmStages) & 1),
+          umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[b % kOzStages]), (uint32_t)((b / kOzStages) & 1),
                                    &s_zero);
       }
       umma::commit(umma::smem_addr(&bar_done));   // every MMA issued so far
@@ -322,41 +309,38 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     __syncwarp();
   } else {
-    // flush warps: row (warp % 4) * 32 + lane, columns (warp / 4) * 64 + [0, 64)
+    // flush warps: row (warp % 4) * 32 + lane, columns (warp / 4) * 64 + [0, 64) of every slot
     double acc64[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) acc64[j] = 0.0;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t col_base = (uint32_t)((warp >> 2) * 64);
-    int run = 0;
-    for (int p = 0; p < npairs && ok;) {
-      int q = p;
-      while (q < npairs && c_pairs.lev[q] == c_pairs.lev[p]) ++q;   // pairs [p, q) share a level
-      const int level_steps = (q - p) * nkb;
-      const double sc = c_pairs.scale[p];
-      for (int done = 0; done < level_steps && ok; done += kWsRunSteps, ++run) {
-        if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_run[run & 1]), (uint32_t)((run >> 1) & 1), abort_flag)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t v[32];
-          umma::tmem_ld32(tmem + lane_base + (uint32_t)((run & 1) * kUmN) + col_base + (uint32_t)(32 * h), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc64[32 * h + j] = fma((double)__uint_as_float(v[j]), sc, acc64[32 * h + j]);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_addr(&bar_free[run & 1])) : "memory");
+    uint32_t nfw = 0;   // flushes done per slot, 8 bits each
+    for (int j = 0; j < sch.nflush && ok; ++j) {
+      const int fl = sch.flush[j], x = fl & 3, lev = fl >> 2;
+      const uint32_t cnt = (nfw >> (8 * x)) & 255u;
+      if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_ready[x]), cnt & 1u, abort_flag)) {
+        ok = false;
+        break;
       }
-      p = q;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const double sc = __longlong_as_double((long long)(1023 - kOzBeta * lev) << 52);   // 2^(-6 lev), exact
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        umma::tmem_ld32(tmem + lane_base + (uint32_t)(x * 128) + col_base + (uint32_t)(32 * h), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc64[32 * h + c] = fma((double)__uint_as_float(v[c]), sc, acc64[32 * h + c]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_addr(&bar_free[x])) : "memory");
+      nfw += 1u << (8 * x);
     }
     if (!ok) *abort_flag = 1;
     if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_done), 0, abort_flag)) ok = false;
-    // epilogue: C = alpha 2^(e_i + f_j) acc + beta C (+ diag_add on the diagonal)
+    // epilogue: C = alpha 2^(e_i + f_j + 2) acc + beta C (+ diag_add on the diagonal)
     __syncwarp();
     const bool good = ok && !*abort_flag;
     const int i = m0 + (warp & 3) * 32 + lane;
@@ -373,7 +357,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         } else if (e_i == kExpEmpty || f_j == kExpEmpty) {
           v = 0.0;
         } else {
-          v = alpha * ldexp(acc64[c], e_i + f_j);
+          v = alpha * ldexp(acc64[c], e_i + f_j + 2);
         }
         double* cptr = C + i + (int64_t)j * ldc;
         if (beta != 0.0) v = fma(beta, *cptr, v);
@@ -386,7 +370,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kUmN));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzTmemCols));
 }
 
 }  // namespace
@@ -434,52 +418,48 @@ qdwhp_status slice_map(CUtensorMap* map, const unsigned short* base, int nslices
 
 namespace {
 
-qdwhp_status launch_umma_ws(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
-                            const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta,
-                            double* C, int64_t ldc, Uplo uplo, double diag_add, int* err) {
+// Schedules by number of K steps, built once per size and kept for the process.
+const OzSchedule* schedule_for(int nsteps) {
+  static std::mutex mu;
+  static std::map<int, std::unique_ptr<OzSchedule>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(nsteps);
+  if (it != cache.end()) return it->second.get();
+  std::unique_ptr<OzSchedule> s(new OzSchedule);
+  if (!oz_build_schedule(nsteps, s.get())) return nullptr;
+  return (cache[nsteps] = std::move(s)).get();
+}
+
+qdwhp_status launch_oz(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, int np, const unsigned short* Asl,
+                       const unsigned short* Bsl, const int* ea, const int* eb, double alpha, double beta, double* C,
+                       int64_t ldc, Uplo uplo, double diag_add, int* err) {
   static PerDeviceOnce attr;
   QDWHP_CUDA_TRY(attr.run([] {
-    return cudaFuncSetAttribute(oz_umma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmSmemBytes);
+    return cudaFuncSetAttribute(oz_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmemBytes);
   }));
   CUtensorMap mapA, mapB;
   QDWHP_TRY(umma::slice_map(&mapA, Asl, kOzS, mp, kp));
   QDWHP_TRY(umma::slice_map(&mapB, Bsl, kOzS, np, kp));
-  dim3 grid(np / kUmN, mp / 128);
-  oz_umma_ws_kernel<<<grid, kWsThreads, kUmSmemBytes, st>>>(mapA, mapB, (int)m, (int)n, kp, ea, eb, alpha, beta, C,
-                                                            ldc, (int)uplo, diag_add, err);
-  QDWHP_LAUNCH_CHECK();
+  const dim3 grid(np / 128, mp / 128);
+  const int nsteps = kp / kOzStepK;
+  // K beyond one schedule's reach: later launches add onto C
+  for (int kb0 = 0; kb0 < nsteps; kb0 += kOzMaxSteps) {
+    const int ns = nsteps - kb0 < kOzMaxSteps ? nsteps - kb0 : kOzMaxSteps;
+    const OzSchedule* sch = schedule_for(ns);
+    if (sch == nullptr) {
+      set_error_message("no digit-product schedule for this K");
+      return QDWHP_ERR_ARG;
+    }
+    const bool first = kb0 == 0;
+    oz_umma_kernel<<<grid, kOzThreads, kOzSmemBytes, st>>>(mapA, mapB, *sch, (int)m, (int)n, kb0, ea, eb, alpha,
+                                                           first ? beta : 1.0, C, ldc, (int)uplo,
+                                                           first ? diag_add : 0.0, err);
+    QDWHP_LAUNCH_CHECK();
+  }
   return QDWHP_OK;
 }
 
 int ceil_to(int64_t a, int b) { return (int)(((a + b - 1) / b) * b); }
-
-PerDeviceOnce g_pairs_once;
-
-qdwhp_status upload_pairs() {
-  const cudaError_t e = g_pairs_once.run([] {
-    PairTable t;
-    memset(&t, 0, sizeof(t));
-    int p = 0;
-    // most significant pairs first (any order is exact in FP32; FP64 adds in this order)
-    for (int lev = 2; lev <= kOzT; ++lev)
-      for (int s = 1; s <= kOzS; ++s) {
-        const int tt = lev - s;
-        if (tt < 1 || tt > kOzS) continue;
-        t.s[p] = (unsigned char)(s - 1);
-        t.t[p] = (unsigned char)(tt - 1);
-        t.lev[p] = (unsigned char)lev;
-        t.scale[p] = ldexp(1.0, -kOzBeta * lev);
-        ++p;
-      }
-    t.npairs = p;
-    return cudaMemcpyToSymbol(c_pairs, &t, sizeof(t));
-  });
-  if (e != cudaSuccess) {
-    set_last_error(e, "upload of the digit-pair table", __FILE__, __LINE__);
-    return QDWHP_ERR_CUDA;
-  }
-  return QDWHP_OK;
-}
 
 }  // namespace
 
@@ -497,7 +477,6 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
   if (m > (1 << 24) || n > (1 << 24) || k > (1 << 24)) return QDWHP_ERR_ARG;
   if (k == 0) return gemm(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, uplo, diag_add);
   if (ws == nullptr || ws_bytes < gemm_ozaki_ws_bytes(m, n, k)) return QDWHP_ERR_NOMEM;
-  QDWHP_TRY(upload_pairs());
   const int mp = ceil_to(m, kOzBM), np = ceil_to(n, kOzBN), kp = ceil_to(k, kOzKPad);
   unsigned short* Asl = (unsigned short*)ws;
   unsigned short* Bsl = Asl + (size_t)kOzS * mp * kp;
@@ -522,7 +501,7 @@ qdwhp_status gemm_ozaki(cudaStream_t st, bool ta, bool tb, int64_t m, int64_t n,
     const double shape[5] = {(double)m, (double)n, (double)k, (double)(uplo == LOWER), -1.0};
     prof_slot = gemm_prof_start(st, flops, shape);
   }
-  QDWHP_TRY(launch_umma_ws(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add, err));
+  QDWHP_TRY(launch_oz(st, m, n, kp, mp, np, Asl, Bsl, ea, eb, alpha, beta, C, ldc, uplo, diag_add, err));
   if (prof_slot >= 0) gemm_prof_stop(st, prof_slot);
   return QDWHP_OK;
 }

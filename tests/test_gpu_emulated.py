@@ -1,8 +1,8 @@
 """FP64 products emulated on the BF16 tensor cores (Ozaki splitting), through the C ABI.
 
 The emulated GEMM is checked against its definition (the numpy FP64 product) with the
-scheme's error bound: the inputs are rounded to 54 bits relative to the largest entry of
-each row of op(A) and column of op(B), digit pairs below 2^-66 of those are dropped, and the
+scheme's error bound: the inputs are rounded to 53 bits relative to the largest entry of
+each row of op(A) and column of op(B), digit pairs below 2^-70 of those are dropped, and the
 60 exact partial products are summed in FP64.  The solvers in QDWHP_FP64_EMULATED mode must
 meet the plain-FP64 tolerances: |lambda - lambda*| <= 1e-12 ||A||_2,
 ||V^T V - I||_F <= 5e-15 n, residuals <= 1e-13."""
@@ -65,6 +65,46 @@ def test_emulated_gemm_within_bound(Q, m, n, k, ta, tb):
     # and it agrees with the native FP64 product to FP64 accuracy, normwise
     nat = Q.gemm_f64(dev(A), dev(B), ta, tb, alpha=1.5, beta=-0.5, Cmat=dev(C0)).cpu().numpy()
     assert np.linalg.norm(got - nat) <= 1e-14 * np.linalg.norm(np.abs(opA) @ np.abs(opB))
+
+
+def test_emulated_gemm_exact_on_integers_with_digit_carries(Q):
+    """Integer entries below 2^20 whose 6-bit groups are 63 or 32 (every balanced digit carries,
+    the top digit reaches its bound 32): the digits hold them exactly and no kept pair is
+    dropped, so the emulated product equals the exact integer product."""
+    rng = np.random.default_rng(11)
+    m, k, n = 200, 300, 136
+    pool = np.array([2 ** 20 - 1, 2 ** 19 + 2 ** 13 - 1, 0b100000_100000_100000, 2 ** 18 + 1, 63, 32])
+    A = (rng.choice(pool, (m, k)) * rng.choice([-1, 1], (m, k))).astype(np.int64)
+    B = (rng.choice(pool, (k, n)) * rng.choice([-1, 1], (k, n))).astype(np.int64)
+    A[:, 0] = 2 ** 20 - 1                     # every row's largest entry: all ones
+    exact = A @ B                             # |entries| < 300 * 2^40: exact in int64 and FP64
+    got = Q.gemm_f64_emulated(dev(A.astype(np.float64)), dev(B.astype(np.float64))).cpu().numpy()
+    assert np.array_equal(got, exact.astype(np.float64))
+
+
+def test_emulated_gemm_all_ones_mantissas(Q):
+    """Entries +-(1 - 2^-53) 2^p: the 53-bit integer of a row's largest entry is 2^53 - 1, so every
+    6-bit group is 63 and the carry reaches the top digit."""
+    rng = np.random.default_rng(12)
+    m, k, n = 160, 520, 140
+    A = rng.choice([-1.0, 1.0], (m, k)) * (1 - 2.0 ** -53) * 2.0 ** rng.integers(-3, 1, (m, k))
+    B = rng.choice([-1.0, 1.0], (k, n)) * (1 - 2.0 ** -53) * 2.0 ** rng.integers(-3, 1, (k, n))
+    got = Q.gemm_f64_emulated(dev(A), dev(B)).cpu().numpy()
+    ref = A @ B
+    assert np.all(np.abs(got - ref) <= emulation_bound(A, B, 1.0, 0.0, np.zeros_like(ref)))
+
+
+def test_emulated_gemm_k_beyond_one_launch(Q):
+    """K = 66000 exceeds one digit-product schedule (65536 deep): the product runs as two
+    launches, the second adding onto C."""
+    rng = np.random.default_rng(13)
+    m, k, n = 130, 66000, 128
+    A = rng.standard_normal((m, k))
+    B = rng.standard_normal((k, n))
+    C0 = rng.standard_normal((m, n))
+    got = Q.gemm_f64_emulated(dev(A), dev(B), alpha=1.5, beta=-0.5, Cmat=dev(C0)).cpu().numpy()
+    ref = 1.5 * A @ B - 0.5 * C0
+    assert np.all(np.abs(got - ref) <= emulation_bound(A, B, 1.5, -0.5, C0))
 
 
 def test_emulated_gemm_zero_and_nonfinite_rows(Q):
