@@ -857,10 +857,10 @@ def run_single(args):
     p = make_problem(SEED)
     A = torch.from_numpy(np.ascontiguousarray(p.A)).cuda()
     launches0 = Q.launch_count()
-    r = Q.svd(A, k=p.k)
+    r = Q.svd(A, k=p.k, precision=precision_code(Q, args.precision))
     torch.cuda.synchronize()
-    print(json.dumps({"single_solve": True, "launches": Q.launch_count() - launches0, "ell": r.info["ell"],
-                      "ms": r.info["ms_total"]}), flush=True)
+    print(json.dumps({"single_solve": True, "precision": args.precision, "launches": Q.launch_count() - launches0,
+                      "ell": r.info["ell"], "ms": r.info["ms_total"]}), flush=True)
 
 
 def main():

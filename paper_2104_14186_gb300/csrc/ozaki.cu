@@ -150,37 +150,46 @@ __global__ void oz_split_kernel(int rows, int k, int rows_pad, int k_pad, const 
 // cores as tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = N = 128, K = 16), both operands read
 // from shared memory through matrix descriptors: K-major, 128-byte swizzle, i.e. 8-row atoms of
 // 1024 bytes with 16-byte chunk c of row r stored at chunk c ^ (r % 8), which is the layout the
-// TMA engine writes for a 64 x 128 box with the 128-byte swizzle.
+// TMA engine writes for a 64 x 128 box with the 128-byte swizzle.  (32-deep steps with the
+// 64-byte swizzle fit seven 32 KB stages, but ran the 4096^3 product a third slower.)
 //
-// Warp 8 (one thread) walks the schedule (oz_schedule.h): for every K step of an item it loads
-// the item's digit tiles (op(A) digits into tile slots 0-1, op(B) digits into 2-3 of a 64 KB
-// stage; the stage's "full" mbarrier counts the bytes) and, once the stage is full, issues the
-// item's pair products into their tensor-memory slots (four 128-column FP32 accumulators); the
-// stage's MMAs commit to its "empty" mbarrier, which releases it to the next copy.  After an
-// item it commits the "ready" mbarrier of every slot the schedule flushes there, and before
-// writing a reused slot it waits on the slot's "free" mbarrier.  Warps 0-7 only flush: for each
-// flush of the schedule they wait on the slot's "ready", read its FP32 sums (tcgen05.ld), add
+// Two threads walk the schedule (oz_schedule.h).  Warp 9 (one thread) loads, for every K step of
+// an item, the item's digit tiles (op(A) digits into tile slots 0-1, op(B) digits into 2-3 of a 64 KB
+// stage; the stage's "full" mbarrier counts the bytes) as soon as the stage's "empty" mbarrier
+// says the MMAs of its previous step are done.  Warp 8 (one thread), once a stage is full, issues the item's
+// pair products into their tensor-memory slots (four 128-column FP32 accumulators) and commits
+// them to the stage's "empty" mbarrier; it never waits on its own MMAs (a single thread that
+// also refilled the ring had to, so the copy latency and the MMA time added up: 9.6 against
+// 7.5 ms for the 4096^3 product).  After an item it
+// commits the "ready" mbarrier of every slot the schedule flushes there, and before writing a
+// reused slot it waits on the slot's "free" mbarrier.  Warps 0-7 only flush: for each
+// flush of the schedule they wait (sleeping between polls) on the slot's "ready", read its FP32 sums (tcgen05.ld), add
 // them times 2^(-6 level) into their FP64 registers and arrive on "free".  Every wait is
 // bounded: on a timeout the tile is written as NaN and err is set.
-constexpr int kOzThreads = 288;
+constexpr int kOzThreads = 320;
 constexpr int kOzStages = 3;
-constexpr uint32_t kOzTileBytes = umma::kAtomBytes;        // 16 KB: 128 rows x 64 K of one digit
+constexpr uint32_t kOzTileBytes = 128 * kOzStepK * 2;      // 16 KB: 128 rows x 64 K of one digit
 constexpr uint32_t kOzStageBytes = 4 * kOzTileBytes;       // op(A) tiles 0-1, op(B) tiles 2-3
 constexpr size_t kOzSmemBytes = (size_t)kOzStages * kOzStageBytes + 1024;
 constexpr int kOzTmemCols = kOzSlots * 128;
+constexpr int kOzGroupM = 8;   // tile rows per band of the tile order (152 resident CTAs: 8 x 19 tiles)
 
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_umma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const __grid_constant__ OzSchedule sch, int M, int N, int kb0, const int* __restrict__ ea,
-                   const int* __restrict__ eb, double alpha, double beta, double* C, int64_t ldc, int uplo,
-                   double diag_add, int* err) {
+                   const __grid_constant__ OzSchedule sch, int M, int N, int ntm, int ntn, int kb0,
+                   const int* __restrict__ ea, const int* __restrict__ eb, double alpha, double beta, double* C,
+                   int64_t ldc, int uplo, double diag_add, int* err) {
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t bar_full[kOzStages], bar_empty[kOzStages];
   __shared__ __align__(8) uint64_t bar_ready[kOzSlots], bar_free[kOzSlots], bar_done;
   __shared__ int s_abort, s_zero;
-  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
+  // tile order: bands of kOzGroupM tile rows, column by column inside a band, so that the CTAs
+  // resident at one time share their op(A) and op(B) digit tiles in L2
+  const int band = (int)blockIdx.x / (kOzGroupM * ntn), local = (int)blockIdx.x - band * kOzGroupM * ntn;
+  const int gm = min(kOzGroupM, ntm - band * kOzGroupM);
+  const int m0 = (band * kOzGroupM + local % gm) * 128, n0 = (local / gm) * 128;
   if (uplo == LOWER && m0 + 128 <= n0) return;   // tile strictly above the diagonal
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -209,103 +218,96 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const uint32_t tmem = tmem_base;
   volatile int* abort_flag = &s_abort;
   bool ok = true;
+  int issued = 0;   // steps whose copy the producer issued
 
-  if (warp == 8) {
+  if (warp >= 8) {
     if (lane == 0) {
       const uint32_t sbase = umma::smem_addr(smem);
       int total = 0;
       for (int it = 0; it < sch.nitems; ++it) total += oz_item_steps(sch, it);
-      int li = 0, lks = 0;   // the next step to load: item li, its step lks
-      auto issue_load = [&](int stage) {
-        const int at = sch.atile[li], bt = sch.btile[li];
-        const bool a2 = (at >> 4) != 0xF, b2 = (bt >> 4) != 0xF;
-        const uint32_t bar = umma::smem_addr(&bar_full[stage]);
-        const uint32_t bytes = (uint32_t)(2 + (a2 ? 1 : 0) + (b2 ? 1 : 0)) * kOzTileBytes;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-        const int kc = (kb0 + sch.chunk[li] * sch.clen + lks) * kOzStepK;
-        const uint32_t d = sbase + (uint32_t)stage * kOzStageBytes;
-        umma::tma_load_3d(d, &mapA, kc, m0, at & 15, bar);
-        if (a2) umma::tma_load_3d(d + kOzTileBytes, &mapA, kc, m0, at >> 4, bar);
-        umma::tma_load_3d(d + 2 * kOzTileBytes, &mapB, kc, n0, bt & 15, bar);
-        if (b2) umma::tma_load_3d(d + 3 * kOzTileBytes, &mapB, kc, n0, bt >> 4, bar);
-        if (++lks == oz_item_steps(sch, li)) {
-          lks = 0;
-          ++li;
-        }
-      };
-      // steps [consumed, loaded) have a copy in flight whose "full" phase nobody has waited for
-      int loaded = 0, consumed = 0;
-      for (int st = 0; st < kOzStages - 1 && st < total; ++st) {
-        issue_load(st);
-        loaded = st + 1;
-      }
-      const uint32_t idesc = umma::idesc_bf16_f32(128, 128);
-      int ci = 0, cks = 0, fp = 0;
-      uint32_t nf = 0;   // flushes committed per slot, 8 bits each
-      for (int step = 0; step < total && ok; ++step) {
-        const int stage = step % kOzStages;
-        if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[stage]), (uint32_t)((step / kOzStages) & 1), abort_flag)) {
-          ok = false;
-          break;
-        }
-        consumed = step + 1;
-        if (cks == 0) {
-          // reused slots: their last flush has read them out
-          const int wm = sch.ctl[ci] & 15;
-          for (int x = 0; x < kOzSlots && ok; ++x)
-            if ((wm >> x) & 1) {
-              const uint32_t cnt = (nf >> (8 * x)) & 255u;
-              if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_free[x]), (cnt - 1u) & 1u, abort_flag)) ok = false;
-            }
-          if (!ok) break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t st_base = sbase + (uint32_t)stage * kOzStageBytes;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const int pc = sch.pair[ci][p];
-          if (!(pc & 0x80)) continue;
-          const uint32_t a0 = st_base + (uint32_t)(pc & 1) * kOzTileBytes;
-          const uint32_t b0 = st_base + (uint32_t)(2 + ((pc >> 1) & 1)) * kOzTileBytes;
-          const uint32_t dcol = tmem + (uint32_t)(((pc >> 2) & 3) * 128);
-          const bool fresh = (pc & 0x10) && cks == 0;
-#pragma unroll
-          for (int kk = 0; kk < kOzStepK / 16; ++kk)   // 32-byte K steps inside the swizzle atom
-            umma::mma_bf16(dcol, umma::desc_sw128(a0 + kk * 32), umma::desc_sw128(b0 + kk * 32), idesc,
-                           (fresh && kk == 0) ? 0u : 1u);
-        }
-        umma::commit(umma::smem_addr(&bar_empty[stage]));
-        if (++cks == oz_item_steps(sch, ci)) {
-          const int nfl = (sch.ctl[ci] >> 4) & 7;
-          for (int f = 0; f < nfl; ++f) {
-            const int x = sch.flush[fp++] & 3;
-            umma::commit(umma::smem_addr(&bar_ready[x]));
-            nf += 1u << (8 * x);
-          }
-          cks = 0;
-          ++ci;
-        }
-        const int nxt = step + kOzStages - 1;
-        if (nxt < total) {
-          if (step >= 1 && !umma::mbar_wait_or_abort(umma::smem_addr(&bar_empty[(step - 1) % kOzStages]),
-                                                     (uint32_t)(((step - 1) / kOzStages) & 1), abort_flag)) {
+      if (warp == 9) {
+        // producer: step j goes to stage j % kOzStages once the MMAs of step j - kOzStages are done
+        int li = 0, lks = 0;   // the next step to load: item li, its step lks
+        for (int j = 0; j < total; ++j) {
+          const int stage = j % kOzStages;
+          if (j >= kOzStages && !umma::mbar_wait_or_abort(umma::smem_addr(&bar_empty[stage]),
+                                                          (uint32_t)((j / kOzStages - 1) & 1), abort_flag)) {
             ok = false;
             break;
           }
-          issue_load(nxt % kOzStages);
-          loaded = nxt + 1;
+          const int at = sch.atile[li], bt = sch.btile[li];
+          const bool a2 = (at >> 4) != 0xF, b2 = (bt >> 4) != 0xF;
+          const uint32_t bar = umma::smem_addr(&bar_full[stage]);
+          const uint32_t bytes = (uint32_t)(2 + (a2 ? 1 : 0) + (b2 ? 1 : 0)) * kOzTileBytes;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+          const int kc = (kb0 + sch.chunk[li] * sch.clen + lks) * kOzStepK;
+          const uint32_t d = sbase + (uint32_t)stage * kOzStageBytes;
+          umma::tma_load_3d(d, &mapA, kc, m0, at & 15, bar);
+          if (a2) umma::tma_load_3d(d + kOzTileBytes, &mapA, kc, m0, at >> 4, bar);
+          umma::tma_load_3d(d + 2 * kOzTileBytes, &mapB, kc, n0, bt & 15, bar);
+          if (b2) umma::tma_load_3d(d + 3 * kOzTileBytes, &mapB, kc, n0, bt >> 4, bar);
+          issued = j + 1;
+          if (++lks == oz_item_steps(sch, li)) {
+            lks = 0;
+            ++li;
+          }
         }
+        if (!ok) *abort_flag = 1;
+      } else {
+        // MMA issuer: never waits on its own MMAs, so the tensor pipe is fed as far ahead as the
+        // copies allow
+        const uint32_t idesc = umma::idesc_bf16_f32(128, 128);
+        int ci = 0, cks = 0, fp = 0;
+        uint32_t nf = 0;   // flushes committed per slot, 8 bits each
+        for (int step = 0; step < total && ok; ++step) {
+          const int stage = step % kOzStages;
+          if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[stage]), (uint32_t)((step / kOzStages) & 1),
+                                        abort_flag)) {
+            ok = false;
+            break;
+          }
+          if (cks == 0) {
+            // reused slots: their last flush has read them out
+            const int wm = sch.ctl[ci] & 15;
+            for (int x = 0; x < kOzSlots && ok; ++x)
+              if ((wm >> x) & 1) {
+                const uint32_t cnt = (nf >> (8 * x)) & 255u;
+                if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_free[x]), (cnt - 1u) & 1u, abort_flag)) ok = false;
+              }
+            if (!ok) break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t st_base = sbase + (uint32_t)stage * kOzStageBytes;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const int pc = sch.pair[ci][p];
+            if (!(pc & 0x80)) continue;
+            const uint32_t a0 = st_base + (uint32_t)(pc & 1) * kOzTileBytes;
+            const uint32_t b0 = st_base + (uint32_t)(2 + ((pc >> 1) & 1)) * kOzTileBytes;
+            const uint32_t dcol = tmem + (uint32_t)(((pc >> 2) & 3) * 128);
+            const bool fresh = (pc & 0x10) && cks == 0;
+#pragma unroll
+            for (int kk = 0; kk < kOzStepK / 16; ++kk)   // 32-byte K steps inside the 128-byte rows
+              umma::mma_bf16(dcol, umma::desc_sw128(a0 + kk * 32), umma::desc_sw128(b0 + kk * 32), idesc,
+                             (fresh && kk == 0) ? 0u : 1u);
+          }
+          umma::commit(umma::smem_addr(&bar_empty[stage]));
+          if (++cks == oz_item_steps(sch, ci)) {
+            const int nfl = (sch.ctl[ci] >> 4) & 7;
+            for (int f = 0; f < nfl; ++f) {
+              const int x = sch.flush[fp++] & 3;
+              umma::commit(umma::smem_addr(&bar_ready[x]));
+              nf += 1u << (8 * x);
+            }
+            cks = 0;
+            ++ci;
+          }
+        }
+        if (!ok) *abort_flag = 1;
+        umma::commit(umma::smem_addr(&bar_done));   // every MMA issued so far
+        // the tensor memory is freed below only after those MMAs are done (bounded)
+        umma::mbar_wait_or_abort(umma::smem_addr(&bar_done), 0, &s_zero);
       }
-      if (!ok) {
-        *abort_flag = 1;
-        // copies still in flight land before the CTA's shared memory is released (bounded)
-        for (int b = consumed; b < loaded; ++b)
-          umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[b % kOzStages]), (uint32_t)((b / kOzStages) & 1),
-                                   &s_zero);
-      }
-      umma::commit(umma::smem_addr(&bar_done));   // every MMA issued so far
-      // the tensor memory is freed below only after those MMAs are done (bounded)
-      umma::mbar_wait_or_abort(umma::smem_addr(&bar_done), 0, &s_zero);
     }
     __syncwarp();
   } else {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     for (int j = 0; j < sch.nflush && ok; ++j) {
       const int fl = sch.flush[j], x = fl & 3, lev = fl >> 2;
       const uint32_t cnt = (nfw >> (8 * x)) & 255u;
-      if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_ready[x]), cnt & 1u, abort_flag)) {
+      if (!umma::mbar_wait_sleep_or_abort(umma::smem_addr(&bar_ready[x]), cnt & 1u, abort_flag)) {
         ok = false;
         break;
       }
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       nfw += 1u << (8 * x);
     }
     if (!ok) *abort_flag = 1;
-    if (!umma::mbar_wait_or_abort(umma::smem_addr(&bar_done), 0, abort_flag)) ok = false;
+    if (!umma::mbar_wait_sleep_or_abort(umma::smem_addr(&bar_done), 0, abort_flag)) ok = false;
     // epilogue: C = alpha 2^(e_i + f_j + 2) acc + beta C (+ diag_add on the diagonal)
     __syncwarp();
     const bool good = ok && !*abort_flag;
@@ -371,6 +373,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzTmemCols));
+  if (warp == 9 && lane == 0 && *abort_flag) {
+    // after a give-up anywhere in the CTA: the last copy into each stage lands before the CTA's
+    // shared memory is released (bounded)
+    for (int j = issued > kOzStages ? issued - kOzStages : 0; j < issued; ++j)
+      umma::mbar_wait_or_abort(umma::smem_addr(&bar_full[j % kOzStages]), (uint32_t)((j / kOzStages) & 1), &s_zero);
+  }
 }
 
 }  // namespace
@@ -440,7 +448,8 @@ qdwhp_status launch_oz(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, in
   CUtensorMap mapA, mapB;
   QDWHP_TRY(umma::slice_map(&mapA, Asl, kOzS, mp, kp));
   QDWHP_TRY(umma::slice_map(&mapB, Bsl, kOzS, np, kp));
-  const dim3 grid(np / 128, mp / 128);
+  const int ntm = mp / 128, ntn = np / 128;
+  const dim3 grid((unsigned)(ntm * ntn));
   const int nsteps = kp / kOzStepK;
   // K beyond one schedule's reach: later launches add onto C
   for (int kb0 = 0; kb0 < nsteps; kb0 += kOzMaxSteps) {
@@ -451,7 +460,7 @@ qdwhp_status launch_oz(cudaStream_t st, int64_t m, int64_t n, int kp, int mp, in
       return QDWHP_ERR_ARG;
     }
     const bool first = kb0 == 0;
-    oz_umma_kernel<<<grid, kOzThreads, kOzSmemBytes, st>>>(mapA, mapB, *sch, (int)m, (int)n, kb0, ea, eb, alpha,
+    oz_umma_kernel<<<grid, kOzThreads, kOzSmemBytes, st>>>(mapA, mapB, *sch, (int)m, (int)n, ntm, ntn, kb0, ea, eb, alpha,
                                                            first ? beta : 1.0, C, ldc, (int)uplo,
                                                            first ? diag_add : 0.0, err);
     QDWHP_LAUNCH_CHECK();

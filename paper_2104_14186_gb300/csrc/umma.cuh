@@ -72,6 +72,25 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
   return false;
 }
 
+// The same for waiters off the critical path: sleeps ~100 ns after each failed poll, so that
+// the warp takes no issue slots from the threads that feed the tensor cores; at most kSpinSleep
+// polls (about half a second or more).
+constexpr int kSpinSleep = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_sleep_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (int it = 0; it < kSpinSleep; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 63 && *abort_flag) return false;
+    __nanosleep(100);
+  }
+  return false;
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint32_t bar) {
   asm volatile(
