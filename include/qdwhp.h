@@ -404,10 +404,11 @@ QDWHP_API qdwhp_status qdwhp_qdwh_steps_f64(int64_t m, int64_t n, double* X, int
  *   qdwhp_last_error_message() and nothing launched.
  *   Scratch: a 4 MB array in the library's own device memory, held by every GPU that
  *   loads the library until the process exits.  The first call on a device looks up
- *   that array's device address (with the device current); make that first call
- *   before any stream capture.  All calls share the one array, so calls that
- *   overlap on the GPU (other streams, other host threads) race: serialise them.
- *   Synchronises `stream` to read the result flag.
+ *   that array's device address (with the device current).  All calls share the one
+ *   array, so calls that overlap on the GPU (other streams, other host threads) race:
+ *   serialise them.
+ *   Every call synchronises `stream` to read the result flag, so the entry point cannot
+ *   be used inside a stream capture at all.
  */
 #define QDWHP_POTRF_NOALLOC_MAX_N 4096
 QDWHP_API qdwhp_status qdwhp_potrf_f64_noalloc(int64_t n, double* Z, int64_t ldz, int* info_host, void* stream);
