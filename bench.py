@@ -399,7 +399,7 @@ def emulated_roofline(Q, total_ms, bf16_peak):
     """Roofline of the emulated-product kernel from the per-GEMM records (split slot -1):
     its own arithmetic is BF16 tensor work, 60 digit products of each FP64 product.  The
     count is algorithmic (the unpadded shape; n(n+1)k for a lower SYRK), not what the
-    128 x 128 x 128-padded tiles issue."""
+    128 x 128 x 64-padded tiles issue."""
     recs = [r for r in Q.profile_records() if r[4] < 0]
     if not recs:
         return None
