@@ -153,19 +153,21 @@ __global__ void oz_split_kernel(int rows, int k, int rows_pad, int k_pad, const 
 // TMA engine writes for a 64 x 128 box with the 128-byte swizzle.  (32-deep steps with the
 // 64-byte swizzle fit seven 32 KB stages, but ran the 4096^3 product a third slower.)
 //
-// Two threads walk the schedule (oz_schedule.h).  Warp 9 (one thread) loads, for every K step of
-// an item, the item's digit tiles (op(A) digits into tile slots 0-1, op(B) digits into 2-3 of a 64 KB
-// stage; the stage's "full" mbarrier counts the bytes) as soon as the stage's "empty" mbarrier
-// says the MMAs of its previous step are done.  Warp 8 (one thread), once a stage is full, issues the item's
-// pair products into their tensor-memory slots (four 128-column FP32 accumulators) and commits
-// them to the stage's "empty" mbarrier; it never waits on its own MMAs (a single thread that
-// also refilled the ring had to, so the copy latency and the MMA time added up: 9.6 against
-// 7.5 ms for the 4096^3 product).  After an item it
-// commits the "ready" mbarrier of every slot the schedule flushes there, and before writing a
-// reused slot it waits on the slot's "free" mbarrier.  Warps 0-7 only flush: for each
-// flush of the schedule they wait (sleeping between polls) on the slot's "ready", read its FP32 sums (tcgen05.ld), add
-// them times 2^(-6 level) into their FP64 registers and arrive on "free".  Every wait is
-// bounded: on a timeout the tile is written as NaN and err is set.
+// Two threads walk the schedule (oz_schedule.h).
+// * Warp 9 (one thread) copies, for every K step of an item, the item's digit tiles into a
+//   64 KB stage (op(A) digits into tile slots 0-1, op(B) digits into 2-3; the stage's "full"
+//   mbarrier counts the bytes) as soon as the stage's "empty" mbarrier says the MMAs of its
+//   previous step are done.
+// * Warp 8 (one thread), once a stage is full, issues the item's pair products into their
+//   tensor-memory slots (four 128-column FP32 accumulators) and commits them to the stage's
+//   "empty" mbarrier.  It never waits on its own MMAs: a single thread that also refilled the
+//   ring had to, so copy latency and MMA time added up (9.6 against 7.5 ms for the 4096^3
+//   product).  After an item it commits the "ready" mbarrier of every slot the schedule
+//   flushes there; before writing a reused slot it waits on that slot's "free" mbarrier.
+// * Warps 0-7 only flush: for each flush of the schedule they wait (sleeping between polls)
+//   on the slot's "ready", read its FP32 sums (tcgen05.ld), add them times 2^(-6 level) into
+//   their FP64 registers and arrive on "free".
+// Every wait is bounded: on a timeout the tile is written as NaN and err is set.
 constexpr int kOzThreads = 320;
 constexpr int kOzStages = 3;
 constexpr uint32_t kOzTileBytes = 128 * kOzStepK * 2;      // 16 KB: 128 rows x 64 K of one digit
