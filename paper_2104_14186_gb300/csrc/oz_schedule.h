@@ -50,6 +50,10 @@ struct OzSchedule {
   uint8_t flush[kOzMaxFlush];    // slot | level << 2, in issue order
 };
 
+// kernel parameters are limited to 4 KB on the classic path; the two tensor maps and the
+// scalars take about 0.4 KB of it
+static_assert(sizeof(OzSchedule) <= 3584, "the digit-pair schedule must fit in a kernel parameter block");
+
 QDWHP_OZ_HD inline int oz_item_steps(const OzSchedule& s, int it) {
   const int left = s.nsteps - s.chunk[it] * s.clen;
   return left < s.clen ? left : s.clen;
