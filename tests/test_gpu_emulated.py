@@ -2,8 +2,9 @@
 
 The emulated GEMM is checked against its definition (the numpy FP64 product) with the
 scheme's error bound: the inputs are rounded to 53 bits relative to the largest entry of
-each row of op(A) and column of op(B), digit pairs below 2^-70 of those are dropped, and the
-60 exact partial products are summed in FP64.  The solvers in QDWHP_FP64_EMULATED mode must
+each row of op(A) and column of op(B), the digit pairs with s + t > 12 (each term at most 2^-64
+of the row maximum times the column maximum) are dropped, and the 60 exact partial products
+are summed in FP64.  The solvers in QDWHP_FP64_EMULATED mode must
 meet the plain-FP64 tolerances: |lambda - lambda*| <= 1e-12 ||A||_2,
 ||V^T V - I||_F <= 5e-15 n, residuals <= 1e-13."""
 
