@@ -70,6 +70,18 @@ def test_workspace_sizes_grow(lib):
     assert lib.qdwhp_svd_workspace_bytes(200, 300, C.byref(o)) > lib.qdwhp_svd_workspace_bytes(300, 200, C.byref(o))
 
 
+def test_svd_workspace_holds_the_reduced_route_above_512(lib):
+    """Above order 512 the partial SVD's reduced problem (order ell <= n) may go to QDWH-SVD,
+    so the workspace must also hold that solver's scratch for a square problem of order n."""
+    from paper_2104_14186_gb300 import qdwhp as Q
+    o = Q.default_opts()
+    for n in (513, 1024, 3000):
+        svd = lib.qdwhp_svd_workspace_bytes(n, n, C.byref(o))
+        assert svd > lib.qdwhp_gesvd_workspace_bytes(n, n, 0), n
+    # at or below 512 the one-sided Jacobi handles every reduced problem: no such scratch
+    assert lib.qdwhp_svd_workspace_bytes(512, 512, C.byref(o)) < lib.qdwhp_gesvd_workspace_bytes(512, 512, 0)
+
+
 def test_argument_errors_return_before_any_launch(lib):
     from paper_2104_14186_gb300 import qdwhp as Q
     o = Q.default_opts()
